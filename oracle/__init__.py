@@ -1,0 +1,224 @@
+"""FP64 CPU oracle for the split-step Crank-Nicolson Gross-Pitaevskii step.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the tests, the package smoke
+check and the benchmark's CPU-baseline leg may import this module.  It wraps
+``gp_oracle.c`` (plain C, FP64, textbook Thomas solves over the whole grid in
+the method's order) with numpy arrays; it shares no code with the CUDA path.
+
+Arrays are complex128 with shape ``(nx, ny, nz)`` in C order, i.e. z has
+stride 1, y stride nz and x stride ny*nz (the paper's "Summary of revisions"
+layout of the psi array).  ``d`` is ``(dx, dy, dz)`` and ``omega`` is
+``(gamma, nu, lambda)``.
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against things
+other than itself: dense LU solves, the separable g = 0 fixed point, the
+continuum and Thomas-Fermi limits, the virial relation, unitarity in real
+time, and the O(dt) energy drift of first-order splitting.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gp_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libgporacle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``gp_oracle.c`` into ``libgporacle.so`` next to it (gcc, no
+    fused multiply-add contraction so x86 and Arm give the same bits)."""
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_thomas.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            lib.oracle_gaussian.argtypes = [_ip, _dp, _dp, _dp]
+            lib.oracle_kick.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp,
+                                        ctypes.c_double, ctypes.c_int]
+            lib.oracle_sweep.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int]
+            lib.oracle_renormalize.argtypes = [_ip, _dp, _dp]
+            lib.oracle_step.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int]
+            lib.oracle_observables.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_double, _dp]
+            for f in (lib.oracle_thomas, lib.oracle_gaussian, lib.oracle_kick,
+                      lib.oracle_sweep, lib.oracle_renormalize, lib.oracle_step,
+                      lib.oracle_observables):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+class use_library:
+    """Context manager that points this module at another build of the oracle
+    (used by the mutation test, which compiles copies with planted mistakes)."""
+
+    def __init__(self, path):
+        self.path = path
+        self.saved = None
+
+    def __enter__(self):
+        global _lib
+        _load()
+        with _lock:
+            self.saved = _lib
+            lib = ctypes.CDLL(self.path)
+            for name in ("oracle_thomas", "oracle_gaussian", "oracle_kick", "oracle_sweep",
+                         "oracle_renormalize", "oracle_step", "oracle_observables"):
+                getattr(lib, name).argtypes = getattr(self.saved, name).argtypes
+                getattr(lib, name).restype = ctypes.c_int
+            _lib = lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+        return False
+
+
+def compile_variant(source_text: str, out_path: str) -> str:
+    """Compile C source text with the oracle's flags into ``out_path``."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.run(["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                    src, "-o", out_path, "-lm"], check=True)
+    return out_path
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _ints(v):
+    a = (ctypes.c_int * 3)(*[int(x) for x in v])
+    return ctypes.cast(a, _ip), a
+
+
+def _dbls(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    return a.ctypes.data_as(_dp), a
+
+
+def _field(psi: np.ndarray) -> np.ndarray:
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous or psi.ndim != 3:
+        raise TypeError("oracle fields are C-contiguous complex128 arrays of shape (nx, ny, nz)")
+    return psi
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError("oracle %s failed with code %d" % (what, rc))
+
+
+def thomas(sub, diag, sup, rhs) -> np.ndarray:
+    """Textbook Thomas solve of sub[m] x[m-1] + diag[m] x[m] + sup[m] x[m+1] = rhs[m]."""
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.complex128)) for a in (sub, diag, sup, rhs)]
+    n = arrs[3].shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    ptrs = [a.ctypes.data_as(_dp) for a in arrs]
+    _check(_load().oracle_thomas(n, *ptrs, x.ctypes.data_as(_dp)), "thomas")
+    return x
+
+
+def gaussian(shape, d, omega) -> np.ndarray:
+    """Normalised product-Gaussian initial state, zero on the boundary."""
+    psi = np.zeros(tuple(int(s) for s in shape), dtype=np.complex128)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    po, _c = _dbls(omega)
+    _check(_load().oracle_gaussian(pn, pd, po, psi.ctypes.data_as(_dp)), "gaussian")
+    return psi
+
+
+def kick(psi, d, dt, omega, g, realtime) -> np.ndarray:
+    """In-place potential-plus-nonlinear step (calcnu)."""
+    psi = _field(psi)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    po, _c = _dbls(omega)
+    _check(_load().oracle_kick(pn, pd, psi.ctypes.data_as(_dp), float(dt), po, float(g),
+                               int(bool(realtime))), "kick")
+    return psi
+
+
+def sweep(psi, d, axis, dt, realtime) -> np.ndarray:
+    """In-place CN line solve along ``axis`` (0 = x, 1 = y, 2 = z)."""
+    psi = _field(psi)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    _check(_load().oracle_sweep(pn, pd, psi.ctypes.data_as(_dp), int(axis), float(dt),
+                                int(bool(realtime))), "sweep")
+    return psi
+
+
+def renormalize(psi, d) -> np.ndarray:
+    psi = _field(psi)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    _check(_load().oracle_renormalize(pn, pd, psi.ctypes.data_as(_dp)), "renormalize")
+    return psi
+
+
+def step(psi, d, dt, omega, g, realtime, nsteps=1) -> np.ndarray:
+    """In-place ``nsteps`` split-step CN steps (kick, x, y, z [, renorm])."""
+    psi = _field(psi)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    po, _c = _dbls(omega)
+    _check(_load().oracle_step(pn, pd, psi.ctypes.data_as(_dp), float(dt), po, float(g),
+                               int(bool(realtime)), int(nsteps)), "step")
+    return psi
+
+
+OBS_KEYS = ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z")
+
+
+def observables(psi, d, omega, g) -> dict:
+    """Norm, chemical potential, energy and rms radii (calcmuen, calcrms)."""
+    psi = _field(psi)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    po, _c = _dbls(omega)
+    out = np.zeros(6, dtype=np.float64)
+    _check(_load().oracle_observables(pn, pd, psi.ctypes.data_as(_dp), po, float(g),
+                                      out.ctypes.data_as(_dp)), "observables")
+    return dict(zip(OBS_KEYS, (float(v) for v in out)))
+
+
+def run_imag_until(psi, d, dt, omega, g, mu_tol, check_every=10, max_steps=100000):
+    """Imaginary-time propagation with the stop rule |mu(n) - mu(n-K)| < tol,
+    checked every K steps (reading R6).  Returns (steps taken, last mu)."""
+    mu_prev = observables(psi, d, omega, g)["mu"]
+    steps = 0
+    while steps < max_steps:
+        step(psi, d, dt, omega, g, False, check_every)
+        steps += check_every
+        mu = observables(psi, d, omega, g)["mu"]
+        if abs(mu - mu_prev) < mu_tol:
+            return steps, mu
+        mu_prev = mu
+    return steps, mu_prev

@@ -1,0 +1,390 @@
+/*
+ * gp_oracle.c -- plain FP64 CPU oracle for the split-step Crank-Nicolson (CN)
+ * propagation of the 3D Gross-Pitaevskii (GP) equation in a fully anisotropic
+ * harmonic trap.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  It is the parity authority for the
+ * CUDA path and shares no code, header, table or constant with it.  Only the
+ * tests, the package smoke check and the benchmark's CPU-baseline leg load it.
+ * It is deliberately slow: every stage runs over the whole grid in the order
+ * the method states, every line solve is the textbook Thomas algorithm with
+ * its own per-line elimination, and complex numbers are C99 `double complex`.
+ *
+ * Source of the method.  The paper ("New version program summary", fields
+ * "Solution method" and "Method of solution" of program summaries (i) and
+ * (ii)) states that the time-dependent GP equation is discretised in space
+ * and time and propagated over small time steps by the split-step CN method,
+ * in imaginary time (stationary states) or real time (dynamics).  Its
+ * "Summary of revisions" names the numerical stages: calcnu (potential and
+ * nonlinear step), calclux / calcluy / calcluz (CN line solves along x, y and
+ * z), renormalisation and norm, calcrms (rms radii) and calcmuen (chemical
+ * potential and energy), and fixes the wavefunction layout: one 1D array in
+ * which z has stride 1, y stride Nz and x stride Ny*Nz.  The paper prints no
+ * equation; the readings of the method taken here, numbered as they are
+ * cited elsewhere in this repository, are:
+ *
+ *   R1  i dpsi/dt = [-(1/2) lap + V + g |psi|^2] psi,
+ *       V = (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2) / 2,  int |psi|^2 = 1,
+ *       so that at g = 0 the ground-state chemical potential is
+ *       (gamma + nu + lambda) / 2.
+ *   R2  nodes x_i = (i - (N-1)/2) d, i = 0..N-1 (trap centred in the box).
+ *   R3  Dirichlet boundary: psi = 0 on the outermost nodes of every axis;
+ *       boundary values are never read by a line solve and are written 0.
+ *   R4  observables are rectangle sums with forward-difference links
+ *       (the exact discrete Rayleigh quotient of the CN Laplacian).
+ *   R5  first-order (Lie) splitting: kick, then x, y, z sweeps, each with
+ *       the full dt; imaginary time then renormalises.
+ *
+ * Imaginary time uses t -> -i tau, so the kick is exp(-dt (V + g|psi|^2))
+ * and each sweep is CN for dpsi/dtau = (1/2) d^2 psi / dx^2; real time uses
+ * the kick exp(-i dt (V + g|psi|^2)) and CN for i dpsi/dt = -(1/2) d^2 psi/dx^2.
+ * With c = dt / (4 d^2) (imaginary time) or c = i dt / (4 d^2) (real time),
+ * the CN line equation at interior node m is
+ *     -c phi[m-1] + (1 + 2c) phi[m] - c phi[m+1]
+ *         = c psi[m-1] + (1 - 2c) psi[m] + c psi[m+1].
+ *
+ * Every entry point returns 0 on success, -1 on bad arguments, -2 when an
+ * allocation fails, -3 on a zero pivot.  Arrays of complex values are passed
+ * as interleaved (re, im) doubles.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+
+typedef double complex cplx;
+
+#define ORACLE_OK 0
+#define ORACLE_EARG (-1)
+#define ORACLE_ENOMEM (-2)
+#define ORACLE_EPIVOT (-3)
+
+/* Offset of node (i, j, k): z stride 1, y stride Nz, x stride Ny*Nz
+ * (paper, "Summary of revisions", layout of the psi array). */
+static size_t site(const int n[3], int i, int j, int k)
+{
+    return ((size_t)i * (size_t)n[1] + (size_t)j) * (size_t)n[2] + (size_t)k;
+}
+
+/* Node coordinate along one axis (reading R2). */
+static double node_coord(int idx, int n, double d)
+{
+    return ((double)idx - 0.5 * (double)(n - 1)) * d;
+}
+
+static int valid_grid(const int n[3], const double d[3])
+{
+    for (int a = 0; a < 3; a++) {
+        if (n[a] < 3 || !(d[a] > 0.0) || !isfinite(d[a]))
+            return 0;
+    }
+    return 1;
+}
+
+static size_t n_sites(const int n[3])
+{
+    return (size_t)n[0] * (size_t)n[1] * (size_t)n[2];
+}
+
+/* Harmonic trap V = (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2) / 2 (reading R1). */
+static double trap(const int n[3], const double d[3], const double omega[3],
+                   int i, int j, int k)
+{
+    double x = node_coord(i, n[0], d[0]);
+    double y = node_coord(j, n[1], d[1]);
+    double z = node_coord(k, n[2], d[2]);
+    return 0.5 * (omega[0] * omega[0] * x * x + omega[1] * omega[1] * y * y +
+                  omega[2] * omega[2] * z * z);
+}
+
+/*
+ * Textbook Thomas algorithm for a tridiagonal system
+ *     sub[m] x[m-1] + diag[m] x[m] + sup[m] x[m+1] = rhs[m],  m = 0..len-1,
+ * with x[-1] = x[len] = 0 (sub[0] and sup[len-1] are ignored).  Forward
+ * elimination builds the modified super-diagonal cp and right-hand side dp;
+ * back substitution recovers x.  No pivoting (the CN matrices here are
+ * strictly diagonally dominant).
+ */
+static int thomas_solve(int len, const cplx *sub, const cplx *diag, const cplx *sup,
+                        const cplx *rhs, cplx *x)
+{
+    if (len < 1)
+        return ORACLE_EARG;
+    cplx *cp = malloc((size_t)len * sizeof(cplx));
+    cplx *dp = malloc((size_t)len * sizeof(cplx));
+    if (!cp || !dp) {
+        free(cp);
+        free(dp);
+        return ORACLE_ENOMEM;
+    }
+    int rc = ORACLE_OK;
+    cplx den = diag[0];
+    if (den == 0.0) {
+        rc = ORACLE_EPIVOT;
+        goto out;
+    }
+    cp[0] = (len > 1 ? sup[0] : 0.0) / den;
+    dp[0] = rhs[0] / den;
+    for (int m = 1; m < len; m++) {
+        den = diag[m] - sub[m] * cp[m - 1];
+        if (den == 0.0) {
+            rc = ORACLE_EPIVOT;
+            goto out;
+        }
+        cp[m] = (m < len - 1 ? sup[m] : 0.0) / den;
+        dp[m] = (rhs[m] - sub[m] * dp[m - 1]) / den;
+    }
+    x[len - 1] = dp[len - 1];
+    for (int m = len - 2; m >= 0; m--)
+        x[m] = dp[m] - cp[m] * x[m + 1];
+out:
+    free(cp);
+    free(dp);
+    return rc;
+}
+
+int oracle_thomas(int len, const double *sub, const double *diag, const double *sup,
+                  const double *rhs, double *x)
+{
+    if (!sub || !diag || !sup || !rhs || !x)
+        return ORACLE_EARG;
+    return thomas_solve(len, (const cplx *)sub, (const cplx *)diag, (const cplx *)sup,
+                        (const cplx *)rhs, (cplx *)x);
+}
+
+/*
+ * Initial state: the product Gaussian prod_a (omega_a/pi)^(1/4)
+ * exp(-omega_a x_a^2 / 2), zero on the boundary nodes (R3), normalised so
+ * that dV * sum |psi|^2 = 1.  This is the g = 0 continuum ground state of
+ * the reading R1.
+ */
+int oracle_gaussian(const int n[3], const double d[3], const double omega[3], double *psi_ri)
+{
+    if (!n || !d || !omega || !psi_ri || !valid_grid(n, d))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    double sum = 0.0;
+    for (int i = 0; i < n[0]; i++)
+        for (int j = 0; j < n[1]; j++)
+            for (int k = 0; k < n[2]; k++) {
+                double v = 0.0;
+                int edge = (i == 0 || i == n[0] - 1 || j == 0 || j == n[1] - 1 ||
+                            k == 0 || k == n[2] - 1);
+                if (!edge) {
+                    double x = node_coord(i, n[0], d[0]);
+                    double y = node_coord(j, n[1], d[1]);
+                    double z = node_coord(k, n[2], d[2]);
+                    v = pow(omega[0] / M_PI, 0.25) * exp(-0.5 * omega[0] * x * x) *
+                        pow(omega[1] / M_PI, 0.25) * exp(-0.5 * omega[1] * y * y) *
+                        pow(omega[2] / M_PI, 0.25) * exp(-0.5 * omega[2] * z * z);
+                }
+                psi[site(n, i, j, k)] = v;
+                sum += v * v;
+            }
+    double dv = d[0] * d[1] * d[2];
+    double scale = 1.0 / sqrt(dv * sum);
+    for (size_t s = 0; s < n_sites(n); s++)
+        psi[s] *= scale;
+    return ORACLE_OK;
+}
+
+/*
+ * Potential-plus-nonlinear step (calcnu): at every node, with rho = |psi|^2
+ * taken before the step,
+ *   imaginary time: psi <- exp(-dt (V + g rho)) psi,
+ *   real time:      psi <- exp(-i dt (V + g rho)) psi.
+ */
+int oracle_kick(const int n[3], const double d[3], double *psi_ri, double dt,
+                const double omega[3], double g, int realtime)
+{
+    if (!n || !d || !omega || !psi_ri || !valid_grid(n, d) || !isfinite(dt))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    for (int i = 0; i < n[0]; i++)
+        for (int j = 0; j < n[1]; j++)
+            for (int k = 0; k < n[2]; k++) {
+                size_t s = site(n, i, j, k);
+                double rho = creal(psi[s] * conj(psi[s]));
+                double arg = dt * (trap(n, d, omega, i, j, k) + g * rho);
+                if (realtime)
+                    psi[s] *= cexp(-I * arg);
+                else
+                    psi[s] *= exp(-arg);
+            }
+    return ORACLE_OK;
+}
+
+/*
+ * CN line solve along one axis (calclux, calcluy, calcluz): for every line
+ * along `axis`, build the right-hand side c psi[m-1] + (1-2c) psi[m] +
+ * c psi[m+1] at the interior nodes m = 1..N-2 (boundary nodes count as 0,
+ * R3), solve the tridiagonal system (-c, 1+2c, -c) with the Thomas
+ * algorithm, and write the solution back with zeros on the two boundary
+ * nodes.
+ */
+int oracle_sweep(const int n[3], const double d[3], double *psi_ri, int axis, double dt,
+                 int realtime)
+{
+    if (!n || !d || !psi_ri || !valid_grid(n, d) || axis < 0 || axis > 2 || !isfinite(dt))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    const int len = n[axis];
+    const int m_int = len - 2;
+    const cplx c = (realtime ? I : 1.0) * dt / (4.0 * d[axis] * d[axis]);
+
+    cplx *sub = malloc((size_t)m_int * sizeof(cplx));
+    cplx *diag = malloc((size_t)m_int * sizeof(cplx));
+    cplx *sup = malloc((size_t)m_int * sizeof(cplx));
+    cplx *rhs = malloc((size_t)m_int * sizeof(cplx));
+    cplx *sol = malloc((size_t)m_int * sizeof(cplx));
+    cplx *line = malloc((size_t)len * sizeof(cplx));
+    int rc = ORACLE_OK;
+    if (!sub || !diag || !sup || !rhs || !sol || !line) {
+        rc = ORACLE_ENOMEM;
+        goto out;
+    }
+    for (int m = 0; m < m_int; m++) {
+        sub[m] = -c;
+        diag[m] = 1.0 + 2.0 * c;
+        sup[m] = -c;
+    }
+
+    /* The two axes that label the lines, and the strides of all three. */
+    const size_t stride[3] = {(size_t)n[1] * (size_t)n[2], (size_t)n[2], 1};
+    const int a1 = (axis == 0) ? 1 : 0;
+    const int a2 = (axis == 2) ? 1 : 2;
+    for (int p = 0; p < n[a1]; p++) {
+        for (int q = 0; q < n[a2]; q++) {
+            size_t base = (size_t)p * stride[a1] + (size_t)q * stride[a2];
+            for (int m = 0; m < len; m++)
+                line[m] = psi[base + (size_t)m * stride[axis]];
+            for (int m = 1; m <= len - 2; m++) {
+                cplx left = (m - 1 >= 1) ? line[m - 1] : 0.0;
+                cplx right = (m + 1 <= len - 2) ? line[m + 1] : 0.0;
+                rhs[m - 1] = c * left + (1.0 - 2.0 * c) * line[m] + c * right;
+            }
+            rc = thomas_solve(m_int, sub, diag, sup, rhs, sol);
+            if (rc != ORACLE_OK)
+                goto out;
+            psi[base] = 0.0;
+            psi[base + (size_t)(len - 1) * stride[axis]] = 0.0;
+            for (int m = 1; m <= len - 2; m++)
+                psi[base + (size_t)m * stride[axis]] = sol[m - 1];
+        }
+    }
+out:
+    free(sub);
+    free(diag);
+    free(sup);
+    free(rhs);
+    free(sol);
+    free(line);
+    return rc;
+}
+
+/* Norm dV * sum |psi|^2 (rectangle rule, R4). */
+static double grid_norm(const int n[3], const double d[3], const cplx *psi)
+{
+    double sum = 0.0;
+    for (size_t s = 0; s < n_sites(n); s++)
+        sum += creal(psi[s] * conj(psi[s]));
+    return d[0] * d[1] * d[2] * sum;
+}
+
+/* Imaginary-time renormalisation psi <- psi / sqrt(norm). */
+int oracle_renormalize(const int n[3], const double d[3], double *psi_ri)
+{
+    if (!n || !d || !psi_ri || !valid_grid(n, d))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    double nrm = grid_norm(n, d, psi);
+    if (!(nrm > 0.0) || !isfinite(nrm))
+        return ORACLE_EARG;
+    double scale = 1.0 / sqrt(nrm);
+    for (size_t s = 0; s < n_sites(n); s++)
+        psi[s] *= scale;
+    return ORACLE_OK;
+}
+
+/*
+ * `nsteps` full split-step CN steps (R5): kick, sweep x, sweep y, sweep z,
+ * and in imaginary time the renormalisation.
+ */
+int oracle_step(const int n[3], const double d[3], double *psi_ri, double dt,
+                const double omega[3], double g, int realtime, int nsteps)
+{
+    if (nsteps < 0)
+        return ORACLE_EARG;
+    for (int s = 0; s < nsteps; s++) {
+        int rc = oracle_kick(n, d, psi_ri, dt, omega, g, realtime);
+        for (int axis = 0; axis < 3 && rc == ORACLE_OK; axis++)
+            rc = oracle_sweep(n, d, psi_ri, axis, dt, realtime);
+        if (rc == ORACLE_OK && !realtime)
+            rc = oracle_renormalize(n, d, psi_ri);
+        if (rc != ORACLE_OK)
+            return rc;
+    }
+    return ORACLE_OK;
+}
+
+/*
+ * Observables (calcrms, calcmuen, norm), reading R4:
+ *   norm = dV sum |psi|^2
+ *   K    = (1/2) dV sum_axes sum_links |psi[m+1] - psi[m]|^2 / d^2
+ *          (all links m = 0..N-2 along each axis)
+ *   P    = dV sum V |psi|^2,   I = dV sum |psi|^4
+ *   mu   = (K + P + g I) / norm,   E = (K + P + g I / 2) / norm
+ *   rms_a = sqrt(dV sum a^2 |psi|^2 / norm)   (no mean subtraction).
+ * out = {norm, mu, energy, rms_x, rms_y, rms_z}.
+ */
+int oracle_observables(const int n[3], const double d[3], const double *psi_ri,
+                       const double omega[3], double g, double out[6])
+{
+    if (!n || !d || !omega || !psi_ri || !out || !valid_grid(n, d))
+        return ORACLE_EARG;
+    const cplx *psi = (const cplx *)psi_ri;
+    double s_rho = 0.0, s_v = 0.0, s_rho2 = 0.0, s_x2 = 0.0, s_y2 = 0.0, s_z2 = 0.0;
+    double links[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n[0]; i++)
+        for (int j = 0; j < n[1]; j++)
+            for (int k = 0; k < n[2]; k++) {
+                cplx p = psi[site(n, i, j, k)];
+                double rho = creal(p * conj(p));
+                double x = node_coord(i, n[0], d[0]);
+                double y = node_coord(j, n[1], d[1]);
+                double z = node_coord(k, n[2], d[2]);
+                s_rho += rho;
+                s_v += trap(n, d, omega, i, j, k) * rho;
+                s_rho2 += rho * rho;
+                s_x2 += x * x * rho;
+                s_y2 += y * y * rho;
+                s_z2 += z * z * rho;
+                if (i + 1 < n[0]) {
+                    cplx df = psi[site(n, i + 1, j, k)] - p;
+                    links[0] += creal(df * conj(df));
+                }
+                if (j + 1 < n[1]) {
+                    cplx df = psi[site(n, i, j + 1, k)] - p;
+                    links[1] += creal(df * conj(df));
+                }
+                if (k + 1 < n[2]) {
+                    cplx df = psi[site(n, i, j, k + 1)] - p;
+                    links[2] += creal(df * conj(df));
+                }
+            }
+    const double dv = d[0] * d[1] * d[2];
+    double norm = dv * s_rho;
+    if (!(norm > 0.0))
+        return ORACLE_EARG;
+    double kin = 0.5 * dv *
+                 (links[0] / (d[0] * d[0]) + links[1] / (d[1] * d[1]) + links[2] / (d[2] * d[2]));
+    double pot = dv * s_v;
+    double inter = dv * s_rho2;
+    out[0] = norm;
+    out[1] = (kin + pot + g * inter) / norm;
+    out[2] = (kin + pot + 0.5 * g * inter) / norm;
+    out[3] = sqrt(dv * s_x2 / norm);
+    out[4] = sqrt(dv * s_y2 / norm);
+    out[5] = sqrt(dv * s_z2 / norm);
+    return ORACLE_OK;
+}
