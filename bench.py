@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Benchmark of the split-step Crank-Nicolson GP step on one GB300 (or N
+independent replicas, one per GPU, under torchrun).
+
+    python bench.py [--steps K] [--warmup W] [--workload real_large]
+    python bench.py --impl reference ...        # the FP64 CPU oracle, timed
+
+A step is one pass of the whole hot path over the grid: the fused kick +
+x line solve, the y line solve, the z line solve with its fused norm, and
+(every 10 steps) the observables reduction that tracks norm and energy
+drift, queued on the device.  Metric: CN site-updates/s (grid sites x steps
+/ seconds).  Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1601_04641_gb300 import inputs  # noqa: E402
+
+METRIC = "CN site-updates/s"
+UNIT = "site-updates/s"
+TRACK_EVERY = 10
+
+WORKLOADS = {
+    # name: (problem factory, precision, field, real time, g used to prepare the start state)
+    "real_large": (inputs.real_large, "f32", "complex", True),
+    "real_medium": (inputs.real_medium, "f64", "complex", True),
+    "imag_small": (inputs.imag_small, "f64", "real", False),
+}
+
+# DRAM bytes (read + write) per launch from `ncu` of each kernel, with the
+# sha256 prefix of the kernel sources they were taken from; a figure whose
+# sources have changed since is reported as null.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1601_04641_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + ",".join(self.FIELDS),
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clocks not sampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        power = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        reasons = set()
+        for r in self.rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        load = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+def gpu_id_for(torch, dev):
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        return "%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        first = vis.split(",")[dev] if vis else str(dev)
+        return first
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_rate(problem, realtime, budget_s, steps=None):
+    """Time the FP64 CPU oracle, as it stands, on a slab of the workload
+    (the full y-z planes, fewer x planes) for about `budget_s` seconds."""
+    import numpy as np
+
+    import oracle
+    nx, ny, nz = problem.shape
+    est_ns = 130.0
+    planes = max(3, min(nx, int(budget_s / (est_ns * 1e-9 * ny * nz * (steps or 2)))))
+    shape = (planes, ny, nz)
+    psi = inputs.random_field(shape, seed=1)
+    oracle.renormalize(psi, problem.d)
+    nsteps = steps or 1
+    t0 = time.perf_counter()
+    oracle.step(psi, problem.d, problem.dt, problem.omega, problem.g, realtime, nsteps)
+    dt = time.perf_counter() - t0
+    if steps is None:
+        # second pass sized to the budget from the first measurement
+        per = dt / (planes * ny * nz)
+        nsteps = max(1, int(budget_s / (per * planes * ny * nz)))
+        t0 = time.perf_counter()
+        oracle.step(psi, problem.d, problem.dt, problem.omega, problem.g, realtime, nsteps)
+        dt = time.perf_counter() - t0
+    sites = planes * ny * nz
+    return {"value": sites * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d %s step(s) of a %dx%dx%d slab of the %dx%dx%d grid, FP64 complex, "
+                      "single-threaded C oracle, %.1f s" % (nsteps, "real-time" if realtime else
+                                                             "imaginary-time", planes, ny, nz,
+                                                             nx, ny, nz, dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    factory, prec, field, realtime = WORKLOADS[args.workload]
+    p = factory()
+    if field == "real":
+        realtime = False
+    per_step_budget = max(0.05, 150.0 / max(1, args.steps + args.warmup))
+    import oracle
+    oracle.build()
+    nx, ny, nz = p.shape
+    planes = max(3, min(nx, int(per_step_budget / (130e-9 * ny * nz))))
+    shape = (planes, ny, nz)
+    psi = inputs.random_field(shape, seed=1)
+    oracle.renormalize(psi, p.d)
+    for _ in range(args.warmup):
+        oracle.step(psi, p.d, p.dt, p.omega, p.g, realtime, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(psi, p.d, p.dt, p.omega, p.g, realtime, 1)
+    el = time.perf_counter() - t0
+    sites = planes * ny * nz
+    value = sites * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p.name, "grid": list(p.shape),
+                       "sample_grid": list(shape), "parallelism": "single-threaded CPU"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: one %s step of a %dx%dx%d slab of the "
+                                       "%dx%dx%d grid, FP64 C oracle" %
+                                       ("real-time" if realtime else "imaginary-time",
+                                        planes, ny, nz, nx, ny, nz)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def prepare(torch, gp, p, realtime):
+    """Start state: the Gaussian relaxed in imaginary time at the preparation
+    nonlinearity, then (real time) the quench to g."""
+    gp.init_gaussian()
+    if realtime:
+        g_prep = p.meta.get("g_prepare", p.g)
+        dt_imag = 0.1 * min(p.d) ** 2
+        gp.set_g(g_prep)
+        gp.set_dt(dt_imag)
+        gp.step_imag(100)
+        gp.set_g(p.g)
+        gp.set_dt(p.dt)
+        psi = gp.get_psi(as_numpy=False)
+        gp.set_psi(psi)
+    torch.cuda.synchronize()
+
+
+def time_workload(torch, name, steps, warmup, dev, with_breakdown=True):
+    from paper_1601_04641_gb300.solver import GP
+    factory, prec, field, realtime = WORKLOADS[name]
+    p = factory()
+    gp = GP(p.shape, p.d, p.dt, p.omega, p.g, prec, field, device=dev)
+    prepare(torch, gp, p, realtime)
+    step = gp.step_real if realtime else gp.step_imag
+    gp.set_tracking(TRACK_EVERY, (steps + warmup) // TRACK_EVERY + 4)
+    stream = gp.stream
+    step(warmup)
+    torch.cuda.synchronize()
+    res = {"problem": p, "gp": gp, "prec": prec, "field": field, "realtime": realtime}
+    res["step"] = step
+    return res
+
+
+def timed_region(torch, res, steps, dist):
+    gp, step = res["gp"], res["step"]
+    stream = gp.stream
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def kernel_breakdown(torch, res, steps):
+    """Average duration of each kernel of the step, from CUDA events recorded
+    between the stages on the launching stream."""
+    gp = res["gp"]
+    rt = res["realtime"]
+    stream = gp.stream
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        ev[s][0].record(stream)
+        for stage in range(3):
+            gp.stage(stage, rt)
+            ev[s][stage + 1].record(stream)
+    torch.cuda.synchronize()
+    names = ["kick_xsweep", "ysweep", "zsweep_norm"]
+    out = {}
+    for stage in range(3):
+        ms = [ev[s][stage].elapsed_time(ev[s][stage + 1]) for s in range(steps)]
+        out[names[stage]] = sum(ms) / len(ms) / 1e3
+    return out
+
+
+def e2e_region(torch, res, steps, dist):
+    """Through the public API with host buffers: psi uploaded from pinned host
+    memory, `steps` steps with the observables read back to the host every 10
+    steps, psi downloaded to pinned host memory -- all inside the timed region."""
+    import numpy as np
+    gp, step = res["gp"], res["step"]
+    host = torch.empty(gp.shape, dtype=gp.psi.dtype, pin_memory=True)
+    host.copy_(gp.psi.cpu())
+    out = torch.empty_like(host).pin_memory()
+    src = host.numpy()
+    dst = out.numpy()
+    gp.set_tracking(0, 0)
+    n_obs = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gp.lib.gp_set_psi(gp.h, src.ctypes.data_as(ctypes.c_void_p), 0)
+    done = 0
+    while done < steps:
+        n = min(TRACK_EVERY, steps - done)
+        step(n)
+        done += n
+        gp.observables()
+        n_obs += 1
+    gp.lib.gp_get_psi(gp.h, dst.ctypes.data_as(ctypes.c_void_p), 0)
+    el = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    nbytes = host.numel() * host.element_size()
+    obs_bytes = 16 * 8 * n_obs
+    return el, nbytes / steps, (nbytes + obs_bytes) / steps
+
+
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    torch.cuda.set_device(local)
+    from paper_1601_04641_gb300 import build as B
+    B.build()
+
+    res = time_workload(torch, args.workload, args.steps, args.warmup, local)
+    p = res["problem"]
+    clocks = ClockSampler(gpu_id_for(torch, local))
+    clocks.start()
+    el = timed_region(torch, res, args.steps, dist)
+    clocks.stop()
+    if dist:
+        t = torch.tensor([el], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    sites = p.sites
+    value = sites * args.steps * world / el
+    launches = 3 * args.steps + (args.steps // TRACK_EVERY)
+    track = res["gp"].tracking()
+
+    kb = kernel_breakdown(torch, res, min(args.steps, 200))
+    top = max(kb, key=kb.get)
+    elem = 8 if res["prec"] == "f32" else 16
+    if res["field"] == "real":
+        elem //= 2
+    alg_bytes = 2 * elem * sites  # each kernel reads and writes psi once
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / kb[top] / 1e9
+    src_hash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get((args.workload, top))
+    traffic = tr[0] if tr and tr[1] == src_hash else None
+
+    e2e_el, h2d, d2h = e2e_region(torch, res, args.steps, dist)
+    if dist:
+        t = torch.tensor([e2e_el], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_el = float(t.item())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": res["prec"], "data": "synthetic",
+        "config": {"workload": p.name, "grid": list(p.shape), "sites": sites,
+                   "psi": {"f32": "complex64", "f64": "complex128"}[res["prec"]]
+                   if res["field"] == "complex" else {"f32": "float32", "f64": "float64"}[res["prec"]],
+                   "reductions": "fp64", "dt": p.dt, "g": p.g, "omega": list(p.omega),
+                   "track_every": TRACK_EVERY,
+                   "l2": "inputs larger than L2 (psi %.0f MB > 129 MB)" % (elem * sites / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel_ms": {k: 1e3 * v for k, v in kb.items()}},
+        "e2e": {"value": sites * args.steps * world / e2e_el, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+        "drift": {"norm": track[-1]["norm"] - track[0]["norm"] if track else None,
+                  "energy_rel": (track[-1]["energy"] - track[0]["energy"]) / track[0]["energy"]
+                  if track else None},
+    }
+    res["gp"].close()
+    if args.also and world == 1:
+        also = {}
+        for name in args.also.split(","):
+            if name and name != args.workload:
+                r2 = time_workload(torch, name, args.also_steps, 3, local)
+                el2 = timed_region(torch, r2, args.also_steps, None)
+                kb2 = kernel_breakdown(torch, r2, min(args.also_steps, 50))
+                also[name] = {"value": r2["problem"].sites * args.also_steps / el2,
+                              "ms_per_step": 1e3 * el2 / args.also_steps, "dtype": r2["prec"],
+                              "kernel_ms": {k: 1e3 * v for k, v in kb2.items()}}
+                r2["gp"].close()
+        line["also"] = also
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_rate(p, res["realtime"], args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="real_large")
+    ap.add_argument("--also", default="real_medium",
+                    help="comma-separated secondary workloads timed after the main one")
+    ap.add_argument("--also-steps", type=int, default=200)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

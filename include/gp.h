@@ -1,0 +1,201 @@
+/*
+ * gp.h -- C ABI of libgpcn: one GB300 GPU advancing the 3D Gross-Pitaevskii
+ * (GP) equation in a fully anisotropic harmonic trap by split-step
+ * Crank-Nicolson (CN) steps, in imaginary time (stationary states) or real
+ * time (dynamics).
+ *
+ * What the calls compute.  The paper (arXiv:1601.04641, "New version program
+ * summary", fields "Solution method" and "Method of solution" of program
+ * summaries (i) imagtime3d and (ii) realtime3d) solves the time-dependent GP
+ * equation by the split-step CN method, discretised in space and time and
+ * propagated over small time steps.  Its "Summary of revisions" names the
+ * stages of one step and the data layout; this library keeps both:
+ *
+ *   calcnu   potential + nonlinear step  psi <- exp(-dt (V + g|psi|^2)) psi
+ *            (imaginary time) or exp(-i dt (V + g|psi|^2)) psi (real time),
+ *            V = (gamma^2 x^2 + nu^2 y^2 + lambda^2 z^2) / 2;
+ *   calclux, calcluy, calcluz
+ *            CN line solves along x, y and z: for c = dt/(4 d^2) (imaginary
+ *            time) or c = i dt/(4 d^2) (real time) every line solves
+ *            -c phi[m-1] + (1+2c) phi[m] - c phi[m+1]
+ *               = c psi[m-1] + (1-2c) psi[m] + c psi[m+1]
+ *            on its interior nodes with psi = 0 on the two end nodes;
+ *   renormalisation (imaginary time) psi <- psi / sqrt(dV sum |psi|^2);
+ *   calcrms, calcmuen  rms radii, chemical potential mu and energy E.
+ *
+ * Layout (paper, "Summary of revisions"): psi is ONE array of nx*ny*nz
+ * elements with z stride 1, y stride nz and x stride ny*nz.  An element is
+ * a double or float (GP_REAL, imaginary time only) or an interleaved
+ * (re, im) pair of doubles or floats (GP_COMPLEX).  Node (i, j, k) sits at
+ * x = (i - (nx-1)/2) dx, y = (j - (ny-1)/2) dy, z = (k - (nz-1)/2) dz.
+ *
+ * Conventions.
+ *  - Every call returns a gp_status; nothing throws across this boundary.
+ *    On error, gp_last_error(h) (or gp_last_error(NULL) for a failed
+ *    create) returns a message valid until the next call on that handle
+ *    from the same thread.
+ *  - Arguments are checked on the host: every n >= 3, spacings and dt > 0
+ *    and finite, trap frequencies >= 0 and finite, g finite.  Otherwise
+ *    GP_ERR_ARG and nothing is launched.
+ *  - Work is queued on the handle's CUDA stream.  Calls that return values
+ *    to the host (gp_observables, gp_get_psi to host memory,
+ *    gp_run_imag_until) synchronise that stream; the step calls do not.
+ *  - The library owns psi unless it was created with gp_create_ext, in
+ *    which case the caller owns the device buffer and must keep it alive
+ *    until gp_destroy.  All other device buffers (CN coefficient tables,
+ *    reduction partials, scalars) are owned by the handle.
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef GPCN_GP_H
+#define GPCN_GP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_handle_s *gp_handle; /* opaque, owned by the library */
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_ARG = 1,       /* invalid argument, nothing done */
+    GP_ERR_CUDA = 2,      /* a CUDA call failed; the handle may be unusable */
+    GP_ERR_NOMEM = 3,     /* a device or host allocation failed */
+    GP_ERR_NONFINITE = 4, /* psi holds NaN or Inf at an observables check */
+    GP_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    GP_ERR_STATE = 6      /* call not valid in the handle's state (e.g. real
+                             time on a GP_REAL field) */
+} gp_status;
+
+typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_precision; /* element precision of psi;
+                                                         reductions are always FP64 */
+typedef enum { GP_COMPLEX = 0, GP_REAL = 1 } gp_field;
+
+typedef struct {
+    int nx, ny, nz;       /* nodes per axis, each >= 3 */
+    double dx, dy, dz;    /* spacings, > 0 */
+} gp_grid;
+
+/* Observables of the current psi (paper, "Summary of revisions": norm,
+ * rms radii from calcrms, chemical potential and energy from calcmuen),
+ * with rectangle sums and forward-difference links:
+ *   norm  = dV sum |psi|^2
+ *   K     = (1/2) dV sum_axes sum_links |psi[m+1]-psi[m]|^2 / d^2
+ *   P     = dV sum V |psi|^2,  I = dV sum |psi|^4
+ *   mu    = (K + P + g I) / norm,  energy = (K + P + g I / 2) / norm
+ *   rms_a = sqrt(dV sum a^2 |psi|^2 / norm). */
+typedef struct {
+    double norm, mu, energy, rms_x, rms_y, rms_z;
+    long long step; /* steps taken since create / the last gp_set_psi */
+    double t;       /* imaginary or real time advanced, sum of dt */
+} gp_obs;
+
+/* Create a solver for one condensate.  grid: nodes and spacings; dt: time
+ * step; gamma, nu, lambda: trap frequencies along x, y, z; g: nonlinearity.
+ * prec / field select the element type of psi (GP_REAL allows imaginary
+ * time only).  cuda_stream: a cudaStream_t to queue work on, or NULL for the
+ * legacy default stream.  psi is allocated on the current CUDA device and
+ * zero-filled.  On success *out holds the handle. */
+gp_status gp_create(gp_handle *out, gp_grid grid, double dt, double gamma, double nu,
+                    double lambda, double g, gp_precision prec, gp_field field,
+                    void *cuda_stream);
+
+/* As gp_create, but psi lives in the caller's device buffer dev_psi of
+ * `bytes` bytes (at least nx*ny*nz elements, 16-byte aligned), which the
+ * caller keeps alive until gp_destroy.  Its contents are kept as they are
+ * (taken as psi with no pending scale). */
+gp_status gp_create_ext(gp_handle *out, gp_grid grid, double dt, double gamma, double nu,
+                        double lambda, double g, gp_precision prec, gp_field field,
+                        void *cuda_stream, void *dev_psi, size_t bytes);
+
+/* Free every buffer the handle owns (not a gp_create_ext psi).  NULL is a no-op. */
+void gp_destroy(gp_handle h);
+
+/* psi <- the product Gaussian prod_a (w_a/pi)^(1/4) exp(-w_a a^2/2), zero on
+ * the boundary nodes, normalised so that dV sum |psi|^2 = 1 (the g = 0
+ * ground state of the continuum problem); resets step and t. */
+gp_status gp_init_gaussian(gp_handle h);
+
+/* Copy psi in (host memory if on_device == 0, device memory otherwise) in
+ * the handle's element type and layout; resets step and t.  The caller
+ * keeps ownership of the source. */
+gp_status gp_set_psi(gp_handle h, const void *psi, int on_device);
+
+/* Copy the current psi out (any pending renormalisation applied). */
+gp_status gp_get_psi(gp_handle h, void *psi, int on_device);
+
+/* Change g (a quench); the CN coefficients do not depend on g. */
+gp_status gp_set_g(gp_handle h, double g);
+
+/* Change dt; rebuilds the CN coefficient tables. */
+gp_status gp_set_dt(gp_handle h, double dt);
+
+/* Queue nsteps imaginary-time steps: kick, x, y and z line solves, then
+ * renormalisation (applied lazily by the next read of psi). */
+gp_status gp_step_imag(gp_handle h, int nsteps);
+
+/* Queue nsteps real-time steps (GP_COMPLEX only): kick, x, y, z line solves. */
+gp_status gp_step_real(gp_handle h, int nsteps);
+
+/* Imaginary-time propagation until |mu(n) - mu(n - check_every)| < mu_tol,
+ * checking every check_every steps, or max_steps.  *steps_taken (may be
+ * NULL) receives the number of steps.  Synchronises at every check. */
+gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max_steps,
+                            int *steps_taken);
+
+/* Compute the observables of the current psi into *out (synchronises).
+ * GP_ERR_NONFINITE if any reduction is NaN or Inf. */
+gp_status gp_observables(gp_handle h, gp_obs *out);
+
+/* Track observables during stepping: after every `every` steps of
+ * gp_step_imag / gp_step_real (counted by the handle's step counter) the
+ * observables reduction is queued on the stream, with no host
+ * synchronisation, into a device history of `capacity` records (the norm
+ * and energy drift of a real-time run).  every = 0 turns tracking off.
+ * Resets the history. */
+gp_status gp_set_tracking(gp_handle h, int every, int capacity);
+
+/* Copy up to max tracked records (oldest first) into out[] and their count
+ * into *count (synchronises).  GP_ERR_NONFINITE if a record is non-finite. */
+gp_status gp_get_tracking(gp_handle h, gp_obs *out, int max, int *count);
+
+/* Run one stage of a step by itself (stage 0: kick + x line solve; 1: y
+ * line solve; 2: z line solve, whose imaginary-time form also sets the
+ * pending renormalisation).  realtime selects the real-time forms.  Stages
+ * 0, 1, 2 in order are exactly one step.  For tests of single stages. */
+gp_status gp_step_stage(gp_handle h, int stage, int realtime);
+
+/* Queue all work on a new stream (a cudaStream_t, NULL for the legacy
+ * default stream). */
+gp_status gp_set_stream(gp_handle h, void *cuda_stream);
+
+/* Block until the handle's queued work is done. */
+gp_status gp_sync(gp_handle h);
+
+/* Window of the windowed back substitution per axis for imaginary (mode 0)
+ * or real (mode 1) time; 0 means the exact two-pass solve is used. */
+gp_status gp_get_window(gp_handle h, int mode, int window[3]);
+
+/* Override the window of every axis and mode: -1 restores the automatic
+ * choice, 0 forces the exact two-pass solve, 4 / 8 / 16 force that window
+ * (GP_ERR_ARG if it is below the smallest window that keeps the truncation
+ * under an eighth of the unit roundoff for this dt). */
+gp_status gp_set_window(gp_handle h, int window);
+
+/* Threads per block of the line-solve kernel of one axis (multiple of 32,
+ * 32..256). */
+gp_status gp_set_threads(gp_handle h, int axis, int threads);
+
+/* Last error message for this handle (or for the calling thread's last
+ * failed create when h is NULL).  Never NULL. */
+const char *gp_last_error(gp_handle h);
+
+/* Library version string. */
+const char *gp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPCN_GP_H */

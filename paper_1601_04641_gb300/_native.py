@@ -1,0 +1,95 @@
+"""ctypes declarations of the C ABI in include/gp.h (libgpcn.so).
+
+Argument marshalling only.  Loading fails loudly when the library has not
+been built: there is no CPU fallback for any of these calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgpcn.so")
+
+GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_NOMEM, GP_ERR_NONFINITE, GP_ERR_TIMEOUT, GP_ERR_STATE = range(7)
+STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_CUDA", 3: "GP_ERR_NOMEM",
+                4: "GP_ERR_NONFINITE", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_STATE"}
+GP_F64, GP_F32 = 0, 1
+GP_COMPLEX, GP_REAL = 0, 1
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("mu", ctypes.c_double), ("energy", ctypes.c_double),
+                ("rms_x", ctypes.c_double), ("rms_y", ctypes.c_double), ("rms_z", ctypes.c_double),
+                ("step", ctypes.c_longlong), ("t", ctypes.c_double)]
+
+
+Handle = ctypes.c_void_p
+_vp = ctypes.c_void_p
+_d = ctypes.c_double
+_i = ctypes.c_int
+
+# name -> (restype, argtypes), in the order of include/gp.h
+SIGNATURES = {
+    "gp_create": (_i, [ctypes.POINTER(Handle), Grid, _d, _d, _d, _d, _d, _i, _i, _vp]),
+    "gp_create_ext": (_i, [ctypes.POINTER(Handle), Grid, _d, _d, _d, _d, _d, _i, _i, _vp, _vp,
+                           ctypes.c_size_t]),
+    "gp_destroy": (None, [Handle]),
+    "gp_init_gaussian": (_i, [Handle]),
+    "gp_set_psi": (_i, [Handle, _vp, _i]),
+    "gp_get_psi": (_i, [Handle, _vp, _i]),
+    "gp_set_g": (_i, [Handle, _d]),
+    "gp_set_dt": (_i, [Handle, _d]),
+    "gp_step_imag": (_i, [Handle, _i]),
+    "gp_step_real": (_i, [Handle, _i]),
+    "gp_run_imag_until": (_i, [Handle, _d, _i, _i, ctypes.POINTER(_i)]),
+    "gp_observables": (_i, [Handle, ctypes.POINTER(Obs)]),
+    "gp_set_tracking": (_i, [Handle, _i, _i]),
+    "gp_get_tracking": (_i, [Handle, ctypes.POINTER(Obs), _i, ctypes.POINTER(_i)]),
+    "gp_step_stage": (_i, [Handle, _i, _i]),
+    "gp_set_stream": (_i, [Handle, _vp]),
+    "gp_sync": (_i, [Handle]),
+    "gp_get_window": (_i, [Handle, _i, ctypes.POINTER(_i)]),
+    "gp_set_window": (_i, [Handle, _i]),
+    "gp_set_threads": (_i, [Handle, _i, _i]),
+    "gp_last_error": (ctypes.c_char_p, [Handle]),
+    "gp_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GPError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+def load():
+    """Load libgpcn.so (built by paper_1601_04641_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libgpcn.so is not built (run paper_1601_04641_gb300.build.build()); "
+                                   "the CUDA path has no fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(status, handle=None):
+    if status != GP_OK:
+        msg = load().gp_last_error(handle)
+        raise GPError(status, msg.decode() if msg else "")

@@ -1,0 +1,731 @@
+// gp_api.cu -- the C ABI of libgpcn (include/gp.h): handle lifetime, host-side
+// argument checks, the FP64 precomputation of the CN recursion coefficients,
+// and the per-step launch sequence (kick + x sweep, y sweep, z sweep + norm).
+#include "gp.h"
+#include "gp_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace gpcn {
+cudaError_t launch_sweep_f32_ir(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+cudaError_t launch_sweep_f32_ic(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+cudaError_t launch_sweep_f32_rt(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+cudaError_t launch_sweep_f64_ir(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+cudaError_t launch_sweep_f64_ic(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+cudaError_t launch_sweep_f64_rt(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+
+cudaError_t launch_sweep(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    if (L.prec == P_F32) {
+        switch (L.form) {
+        case F_IMAG_REAL: return launch_sweep_f32_ir(L, a, s);
+        case F_IMAG_CPLX: return launch_sweep_f32_ic(L, a, s);
+        case F_REALTIME: return launch_sweep_f32_rt(L, a, s);
+        }
+    } else {
+        switch (L.form) {
+        case F_IMAG_REAL: return launch_sweep_f64_ir(L, a, s);
+        case F_IMAG_CPLX: return launch_sweep_f64_ic(L, a, s);
+        case F_REALTIME: return launch_sweep_f64_rt(L, a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace gpcn
+
+using namespace gpcn;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Device scalars of a handle.
+enum Scalar { S_SCALE = 0, S_ONE = 1, S_NORM_SWEEP = 2, S_NORM_INIT = 3, S_COUNT = 8 };
+
+struct CoefSet {
+    size_t off_cp = 0, off_ip = 0;  // byte offsets into the coefficient buffer
+    int window = 0;                  // chosen window (0: exact two-pass)
+    int min_window = 0;              // smallest admissible window (0: none)
+    double cp_max = 0.0;
+};
+
+}  // namespace
+
+struct gp_handle_s {
+    int device = 0;
+    int n[3] = {0, 0, 0};
+    double d[3] = {0, 0, 0};
+    double dt = 0, w[3] = {0, 0, 0}, g = 0;
+    gp_precision prec = GP_F64;
+    gp_field field = GP_COMPLEX;
+    size_t elem = 0, sites = 0, bytes = 0;
+    void *psi = nullptr;
+    bool own_psi = false;
+    cudaStream_t stream = nullptr;
+    char *d_coef = nullptr;
+    size_t coef_bytes = 0;
+    CoefSet coef[2][3];
+    int forced_window = -1;
+    double *d_scal = nullptr;
+    double *d_obs = nullptr;
+    double *d_partials = nullptr;
+    size_t partial_cap = 0;
+    unsigned int *d_counter = nullptr;
+    bool scale_pending = false;
+    long long step = 0;
+    double t = 0;
+    int threads[3] = {128, 128, 128};
+    // observables history queued during stepping
+    int track_every = 0, track_cap = 0, track_count = 0;
+    double *d_track = nullptr;
+    std::vector<long long> track_step;
+    std::vector<double> track_t;
+    std::string err;
+};
+
+namespace {
+
+gp_status fail(gp_handle h, gp_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+#define GP_CK(h, call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((h), GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+gp_status check_args(gp_grid grid, double dt, double gamma, double nu, double lambda, double g,
+                     gp_precision prec, gp_field field) {
+    const int n[3] = {grid.nx, grid.ny, grid.nz};
+    const double d[3] = {grid.dx, grid.dy, grid.dz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 3) return fail(nullptr, GP_ERR_ARG, "every axis needs at least 3 nodes");
+        if (!finite_pos(d[a])) return fail(nullptr, GP_ERR_ARG, "spacings must be finite and > 0");
+    }
+    if ((long long)n[0] * n[1] * n[2] > (1LL << 40))
+        return fail(nullptr, GP_ERR_ARG, "grid too large");
+    if (!finite_pos(dt)) return fail(nullptr, GP_ERR_ARG, "dt must be finite and > 0");
+    const double w[3] = {gamma, nu, lambda};
+    for (double x : w)
+        if (!std::isfinite(x) || x < 0.0)
+            return fail(nullptr, GP_ERR_ARG, "trap frequencies must be finite and >= 0");
+    if (!std::isfinite(g)) return fail(nullptr, GP_ERR_ARG, "g must be finite");
+    if (prec != GP_F64 && prec != GP_F32) return fail(nullptr, GP_ERR_ARG, "unknown precision");
+    if (field != GP_COMPLEX && field != GP_REAL) return fail(nullptr, GP_ERR_ARG, "unknown field");
+    return GP_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int modes_of(gp_handle h) { return h->field == GP_COMPLEX ? 2 : 1; }
+
+// FP64 Thomas coefficients of the CN matrix (-c, 1+2c, -c) on n interior
+// nodes: den[0] = 1+2c, den[t] = 1+2c + c cp[t-1], ip = 1/den, cp = -c ip.
+void thomas_coefficients(std::complex<double> c, int n, std::vector<std::complex<double>> &cp,
+                         std::vector<std::complex<double>> &ip) {
+    cp.assign(n, 0.0);
+    ip.assign(n, 0.0);
+    const std::complex<double> b = 1.0 + 2.0 * c;
+    for (int t = 0; t < n; ++t) {
+        const std::complex<double> den = (t == 0) ? b : b + c * cp[t - 1];
+        ip[t] = 1.0 / den;
+        cp[t] = -c * ip[t];
+    }
+}
+
+// Build and upload the coefficient tables of both modes and all axes, and
+// pick the window of the windowed backward sweep for each.
+gp_status build_coefficients(gp_handle h) {
+    const bool f32 = h->prec == GP_F32;
+    const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+    const double eps = f32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    std::vector<char> host;
+    size_t off = 0;
+    for (int mode = 0; mode < modes_of(h); ++mode) {
+        for (int ax = 0; ax < 3; ++ax) {
+            const int n = h->n[ax] - 2;
+            const size_t esz = (mode == 1 ? 2 : 1) * rsz;
+            CoefSet &cs = h->coef[mode][ax];
+            cs.off_cp = off;
+            off = align_up(off + esz * n, 256);
+            cs.off_ip = off;
+            off = align_up(off + esz * n, 256);
+        }
+    }
+    host.assign(off, 0);
+    for (int mode = 0; mode < modes_of(h); ++mode) {
+        for (int ax = 0; ax < 3; ++ax) {
+            const int n = h->n[ax] - 2;
+            const double kap = h->dt / (4.0 * h->d[ax] * h->d[ax]);
+            const std::complex<double> c = mode == 1 ? std::complex<double>(0.0, kap)
+                                                     : std::complex<double>(kap, 0.0);
+            std::vector<std::complex<double>> cp, ip;
+            thomas_coefficients(c, n, cp, ip);
+            CoefSet &cs = h->coef[mode][ax];
+            cs.cp_max = 0.0;
+            for (int t = 0; t < n - 1; ++t) cs.cp_max = std::max(cs.cp_max, std::abs(cp[t]));
+            cs.min_window = 0;
+            for (int w : {4, 8, 16}) {
+                if (std::pow(cs.cp_max, w + 1) <= eps / 8.0) {
+                    cs.min_window = w;
+                    break;
+                }
+            }
+            cs.window = cs.min_window;
+            for (int t = 0; t < n; ++t) {
+                for (int which = 0; which < 2; ++which) {
+                    const std::complex<double> v = which == 0 ? cp[t] : ip[t];
+                    char *dst = host.data() + (which == 0 ? cs.off_cp : cs.off_ip);
+                    if (mode == 1) {
+                        if (f32) {
+                            float pr[2] = {(float)v.real(), (float)v.imag()};
+                            std::memcpy(dst + t * 2 * rsz, pr, sizeof(pr));
+                        } else {
+                            double pr[2] = {v.real(), v.imag()};
+                            std::memcpy(dst + t * 2 * rsz, pr, sizeof(pr));
+                        }
+                    } else {
+                        if (f32) {
+                            float r = (float)v.real();
+                            std::memcpy(dst + t * rsz, &r, sizeof(r));
+                        } else {
+                            double r = v.real();
+                            std::memcpy(dst + t * rsz, &r, sizeof(r));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (h->d_coef && h->coef_bytes < off) {
+        cudaFree(h->d_coef);
+        h->d_coef = nullptr;
+    }
+    if (!h->d_coef) {
+        if (cudaMalloc(&h->d_coef, off) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, GP_ERR_NOMEM, "cudaMalloc of the coefficient tables failed");
+        }
+        h->coef_bytes = off;
+    }
+    GP_CK(h, cudaMemcpyAsync(h->d_coef, host.data(), off, cudaMemcpyHostToDevice, h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->forced_window >= 0) {
+        for (int mode = 0; mode < modes_of(h); ++mode)
+            for (int ax = 0; ax < 3; ++ax) {
+                CoefSet &cs = h->coef[mode][ax];
+                const bool ok = h->forced_window == 0 ||
+                                (cs.min_window > 0 && h->forced_window >= cs.min_window);
+                cs.window = ok ? h->forced_window : cs.window;
+            }
+    }
+    return GP_OK;
+}
+
+long long sweep_lines(gp_handle h, int ax) {
+    const long long nx = h->n[0], ny = h->n[1], nz = h->n[2];
+    return ax == 0 ? ny * nz : ax == 1 ? nx * nz : nx * ny;
+}
+
+size_t blocks_for(long long items, int threads) { return (size_t)((items + threads - 1) / threads); }
+
+FieldArgs field_args(gp_handle h) {
+    FieldArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = h->psi;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.n[ax] = h->n[ax];
+        a.d[ax] = h->d[ax];
+        a.origin[ax] = -0.5 * (h->n[ax] - 1) * h->d[ax];
+        a.w[ax] = h->w[ax];
+        a.half_w2[ax] = 0.5 * h->w[ax] * h->w[ax];
+    }
+    a.g = h->g;
+    a.scale = h->d_scal + (h->scale_pending ? S_SCALE : S_ONE);
+    a.dV = h->d[0] * h->d[1] * h->d[2];
+    a.partials = h->d_partials;
+    a.counter = h->d_counter;
+    a.out = h->d_obs;
+    a.scale_out = h->d_scal + S_SCALE;
+    a.norm_out = h->d_scal + S_NORM_INIT;
+    a.sites = (long long)h->sites;
+    return a;
+}
+
+constexpr int kNormBlocks = 152 * 4;
+
+gp_status alloc_scratch(gp_handle h) {
+    size_t cap = kNormBlocks;
+    cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32));  // z sweep at >= 32 threads/block
+    FieldArgs fa = field_args(h);
+    cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
+    if (cudaMalloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_scal, S_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_obs, O_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_counter, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, GP_ERR_NOMEM, "cudaMalloc of reduction scratch failed");
+    }
+    h->partial_cap = cap;
+    double init[S_COUNT] = {1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    GP_CK(h, cudaMemcpyAsync(h->d_scal, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+    GP_CK(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int), h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    return GP_OK;
+}
+
+void release(gp_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->own_psi && h->psi) cudaFree(h->psi);
+    cudaFree(h->d_coef);
+    cudaFree(h->d_scal);
+    cudaFree(h->d_obs);
+    cudaFree(h->d_partials);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_track);
+    cudaGetLastError();
+    delete h;
+}
+
+gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, double nu,
+                        double lambda, double g, gp_precision prec, gp_field field, void *stream,
+                        void *dev_psi, size_t bytes) {
+    if (!out) return fail(nullptr, GP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    gp_status st = check_args(grid, dt, gamma, nu, lambda, g, prec, field);
+    if (st != GP_OK) return st;
+    gp_handle h = new (std::nothrow) gp_handle_s();
+    if (!h) return fail(nullptr, GP_ERR_NOMEM, "host allocation failed");
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, GP_ERR_CUDA, "no CUDA device");
+    }
+    h->n[0] = grid.nx;
+    h->n[1] = grid.ny;
+    h->n[2] = grid.nz;
+    h->d[0] = grid.dx;
+    h->d[1] = grid.dy;
+    h->d[2] = grid.dz;
+    h->dt = dt;
+    h->w[0] = gamma;
+    h->w[1] = nu;
+    h->w[2] = lambda;
+    h->g = g;
+    h->prec = prec;
+    h->field = field;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->elem = (prec == GP_F64 ? 8 : 4) * (field == GP_COMPLEX ? 2 : 1);
+    h->sites = (size_t)grid.nx * grid.ny * grid.nz;
+    h->bytes = h->sites * h->elem;
+    if (dev_psi) {
+        if (bytes < h->bytes || (reinterpret_cast<uintptr_t>(dev_psi) & 15u)) {
+            delete h;
+            return fail(nullptr, GP_ERR_ARG, "dev_psi too small or not 16-byte aligned");
+        }
+        h->psi = dev_psi;
+        h->own_psi = false;
+    } else {
+        if (cudaMalloc(&h->psi, h->bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(nullptr, GP_ERR_NOMEM, "cudaMalloc of psi failed");
+        }
+        h->own_psi = true;
+        if (cudaMemsetAsync(h->psi, 0, h->bytes, h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            release(h);
+            return fail(nullptr, GP_ERR_CUDA, "cudaMemsetAsync of psi failed");
+        }
+    }
+    st = alloc_scratch(h);
+    if (st == GP_OK) st = build_coefficients(h);
+    if (st != GP_OK) {
+        g_create_error = h->err;
+        release(h);
+        return st;
+    }
+    *out = h;
+    return GP_OK;
+}
+
+gp_status enter(gp_handle h) {
+    if (!h) return fail(nullptr, GP_ERR_ARG, "NULL handle");
+    if (cudaSetDevice(h->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+    }
+    return GP_OK;
+}
+
+gp_status queue_observables(gp_handle h, double *dst);
+
+// One stage of a step: 0 = kick + x sweep, 1 = y sweep, 2 = z sweep + norm.
+gp_status run_stage(gp_handle h, int stage, bool realtime) {
+    SweepLaunch L;
+    L.prec = h->prec == GP_F32 ? P_F32 : P_F64;
+    L.form = realtime ? F_REALTIME : (h->field == GP_REAL ? F_IMAG_REAL : F_IMAG_CPLX);
+    L.kind = static_cast<Kind>(stage);
+    const int mode = realtime ? 1 : 0;
+    const int ax = stage;
+    const CoefSet &cs = h->coef[mode][ax];
+    L.window = cs.window;
+    L.threads = h->threads[ax];
+    L.contiguous = 0;
+
+    SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const long long nx = h->n[0], ny = h->n[1], nz = h->n[2];
+    a.psi = h->psi;
+    a.cp = h->d_coef + cs.off_cp;
+    a.ip = h->d_coef + cs.off_ip;
+    a.n_lines = sweep_lines(h, ax);
+    if (ax == 0) {
+        a.inner = ny * nz;
+        a.outer_stride = 0;
+        a.stride = ny * nz;
+    } else if (ax == 1) {
+        a.inner = nz;
+        a.outer_stride = ny * nz;
+        a.stride = nz;
+    } else {
+        a.inner = 1;
+        a.outer_stride = nz;
+        a.stride = 1;
+    }
+    a.N = h->n[ax];
+    a.kappa = h->dt / (4.0 * h->d[ax] * h->d[ax]);
+    a.scale = h->d_scal + (h->scale_pending ? S_SCALE : S_ONE);
+    a.dt = h->dt;
+    a.g = h->g;
+    for (int q = 0; q < 3; ++q) {
+        a.half_w2[q] = 0.5 * h->w[q] * h->w[q];
+        a.origin[q] = -0.5 * (h->n[q] - 1) * h->d[q];
+        a.d[q] = h->d[q];
+    }
+    a.nz = (int)nz;
+    a.ny = (int)ny;
+    a.partials = h->d_partials;
+    a.counter = h->d_counter;
+    a.norm_out = h->d_scal + S_NORM_SWEEP;
+    a.scale_out = h->d_scal + S_SCALE;
+    a.dV = h->d[0] * h->d[1] * h->d[2];
+    a.want_scale = realtime ? 0 : 1;
+    if (stage == 2 && blocks_for(a.n_lines, L.threads) > h->partial_cap)
+        return fail(h, GP_ERR_STATE, "z sweep grid exceeds the partials buffer");
+    GP_CK(h, launch_sweep(L, a, h->stream));
+    if (stage == 0) h->scale_pending = false;
+    if (stage == 2 && !realtime) h->scale_pending = true;
+    return GP_OK;
+}
+
+gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
+    if (nsteps < 0) return fail(h, GP_ERR_ARG, "nsteps < 0");
+    if (realtime && h->field != GP_COMPLEX)
+        return fail(h, GP_ERR_STATE, "real-time steps need a GP_COMPLEX field");
+    for (int s = 0; s < nsteps; ++s) {
+        for (int stage = 0; stage < 3; ++stage) {
+            gp_status st = run_stage(h, stage, realtime);
+            if (st != GP_OK) return st;
+        }
+        h->step += 1;
+        h->t += h->dt;
+        if (h->track_every > 0 && h->step % h->track_every == 0 && h->track_count < h->track_cap) {
+            gp_status st = queue_observables(h, h->d_track + (size_t)h->track_count * O_COUNT);
+            if (st != GP_OK) return st;
+            h->track_step.push_back(h->step);
+            h->track_t.push_back(h->t);
+            h->track_count += 1;
+        }
+    }
+    return GP_OK;
+}
+
+gp_status queue_observables(gp_handle h, double *dst) {
+    FieldArgs a = field_args(h);
+    a.out = dst;
+    if ((size_t)observables_blocks(a) * 9 > h->partial_cap)
+        return fail(h, GP_ERR_STATE, "observables grid exceeds the partials buffer");
+    GP_CK(h, launch_observables(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a,
+                                h->stream));
+    return GP_OK;
+}
+
+void fill_obs(const double *o, long long step, double t, gp_obs *out) {
+    out->norm = o[O_NORM];
+    out->mu = o[O_MU];
+    out->energy = o[O_E];
+    out->rms_x = o[O_RMSX];
+    out->rms_y = o[O_RMSY];
+    out->rms_z = o[O_RMSZ];
+    out->step = step;
+    out->t = t;
+}
+
+gp_status observables(gp_handle h, gp_obs *out) {
+    gp_status st = queue_observables(h, h->d_obs);
+    if (st != GP_OK) return st;
+    double o[O_COUNT];
+    GP_CK(h, cudaMemcpyAsync(o, h->d_obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    if (out) fill_obs(o, h->step, h->t, out);
+    if (o[O_FINITE] != 1.0) return fail(h, GP_ERR_NONFINITE, "psi holds NaN or Inf");
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_create(gp_handle *out, gp_grid grid, double dt, double gamma, double nu,
+                    double lambda, double g, gp_precision prec, gp_field field,
+                    void *cuda_stream) {
+    return create_common(out, grid, dt, gamma, nu, lambda, g, prec, field, cuda_stream, nullptr, 0);
+}
+
+gp_status gp_create_ext(gp_handle *out, gp_grid grid, double dt, double gamma, double nu,
+                        double lambda, double g, gp_precision prec, gp_field field,
+                        void *cuda_stream, void *dev_psi, size_t bytes) {
+    if (!dev_psi) return fail(nullptr, GP_ERR_ARG, "dev_psi is NULL");
+    return create_common(out, grid, dt, gamma, nu, lambda, g, prec, field, cuda_stream, dev_psi,
+                         bytes);
+}
+
+void gp_destroy(gp_handle h) { release(h); }
+
+gp_status gp_init_gaussian(gp_handle h) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    FieldArgs a = field_args(h);
+    const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
+    const bool cplx = h->field == GP_COMPLEX;
+    GP_CK(h, launch_gaussian(p, cplx, a, h->stream));
+    GP_CK(h, launch_norm(p, cplx, a, kNormBlocks, h->stream));
+    h->scale_pending = true;
+    h->step = 0;
+    h->t = 0.0;
+    return GP_OK;
+}
+
+gp_status gp_set_psi(gp_handle h, const void *psi, int on_device) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
+    GP_CK(h, cudaMemcpyAsync(h->psi, psi, h->bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             h->stream));
+    if (!on_device) GP_CK(h, cudaStreamSynchronize(h->stream));
+    h->scale_pending = false;
+    h->step = 0;
+    h->t = 0.0;
+    return GP_OK;
+}
+
+gp_status gp_get_psi(gp_handle h, void *psi, int on_device) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
+    FieldArgs a = field_args(h);
+    const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
+    const bool cplx = h->field == GP_COMPLEX;
+    if (on_device) {
+        GP_CK(h, launch_apply_scale(p, cplx, a, psi, h->stream));
+        return GP_OK;
+    }
+    if (h->scale_pending) {  // fold the pending factor into psi (same rounding as the next kick)
+        GP_CK(h, launch_apply_scale(p, cplx, a, h->psi, h->stream));
+        h->scale_pending = false;
+    }
+    GP_CK(h, cudaMemcpyAsync(psi, h->psi, h->bytes, cudaMemcpyDeviceToHost, h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    return GP_OK;
+}
+
+gp_status gp_set_g(gp_handle h, double g) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (!std::isfinite(g)) return fail(h, GP_ERR_ARG, "g must be finite");
+    h->g = g;
+    return GP_OK;
+}
+
+gp_status gp_set_dt(gp_handle h, double dt) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (!finite_pos(dt)) return fail(h, GP_ERR_ARG, "dt must be finite and > 0");
+    h->dt = dt;
+    return build_coefficients(h);
+}
+
+gp_status gp_step_imag(gp_handle h, int nsteps) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    return run_steps(h, nsteps, false);
+}
+
+gp_status gp_step_real(gp_handle h, int nsteps) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    return run_steps(h, nsteps, true);
+}
+
+gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max_steps,
+                            int *steps_taken) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (!(mu_tol > 0.0) || check_every < 1 || max_steps < 0)
+        return fail(h, GP_ERR_ARG, "need mu_tol > 0, check_every >= 1, max_steps >= 0");
+    gp_obs o;
+    st = observables(h, &o);
+    if (st != GP_OK) return st;
+    double mu_prev = o.mu;
+    int taken = 0;
+    while (taken < max_steps) {
+        const int n = std::min(check_every, max_steps - taken);
+        st = run_steps(h, n, false);
+        if (st != GP_OK) break;
+        taken += n;
+        st = observables(h, &o);
+        if (st != GP_OK) break;
+        if (std::fabs(o.mu - mu_prev) < mu_tol) break;
+        mu_prev = o.mu;
+    }
+    if (steps_taken) *steps_taken = taken;
+    return st;
+}
+
+gp_status gp_observables(gp_handle h, gp_obs *out) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (!out) return fail(h, GP_ERR_ARG, "out is NULL");
+    return observables(h, out);
+}
+
+gp_status gp_set_tracking(gp_handle h, int every, int capacity) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (every < 0 || capacity < 0 || (every > 0 && capacity < 1))
+        return fail(h, GP_ERR_ARG, "need every >= 0 and capacity >= 1 when tracking");
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->d_track && capacity > h->track_cap) {
+        cudaFree(h->d_track);
+        h->d_track = nullptr;
+        h->track_cap = 0;
+    }
+    if (every > 0 && !h->d_track) {
+        if (cudaMalloc(&h->d_track, (size_t)capacity * O_COUNT * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, GP_ERR_NOMEM, "cudaMalloc of the tracking history failed");
+        }
+        h->track_cap = capacity;
+    }
+    h->track_every = every;
+    h->track_count = 0;
+    h->track_step.clear();
+    h->track_t.clear();
+    return GP_OK;
+}
+
+gp_status gp_get_tracking(gp_handle h, gp_obs *out, int max, int *count) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (max < 0 || (max > 0 && !out)) return fail(h, GP_ERR_ARG, "bad output buffer");
+    const int n = std::min(max, h->track_count);
+    std::vector<double> buf((size_t)std::max(n, 1) * O_COUNT);
+    if (n > 0)
+        GP_CK(h, cudaMemcpyAsync(buf.data(), h->d_track, (size_t)n * O_COUNT * sizeof(double),
+                                 cudaMemcpyDeviceToHost, h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    bool finite = true;
+    for (int r = 0; r < n; ++r) {
+        fill_obs(buf.data() + (size_t)r * O_COUNT, h->track_step[r], h->track_t[r], out + r);
+        finite = finite && buf[(size_t)r * O_COUNT + O_FINITE] == 1.0;
+    }
+    if (count) *count = h->track_count;
+    if (!finite) return fail(h, GP_ERR_NONFINITE, "a tracked record is non-finite");
+    return GP_OK;
+}
+
+gp_status gp_step_stage(gp_handle h, int stage, int realtime) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (stage < 0 || stage > 2) return fail(h, GP_ERR_ARG, "stage must be 0, 1 or 2");
+    if (realtime && h->field != GP_COMPLEX)
+        return fail(h, GP_ERR_STATE, "real-time stages need a GP_COMPLEX field");
+    return run_stage(h, stage, realtime != 0);
+}
+
+gp_status gp_set_stream(gp_handle h, void *cuda_stream) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return GP_OK;
+}
+
+gp_status gp_sync(gp_handle h) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    return GP_OK;
+}
+
+gp_status gp_get_window(gp_handle h, int mode, int window[3]) {
+    if (!h || !window || mode < 0 || mode > 1) return fail(h, GP_ERR_ARG, "bad arguments");
+    if (mode >= modes_of(h)) return fail(h, GP_ERR_STATE, "no real-time tables on a GP_REAL field");
+    for (int ax = 0; ax < 3; ++ax) window[ax] = h->coef[mode][ax].window;
+    return GP_OK;
+}
+
+gp_status gp_set_window(gp_handle h, int window) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (window != -1 && window != 0 && window != 4 && window != 8 && window != 16)
+        return fail(h, GP_ERR_ARG, "window must be -1 (automatic), 0, 4, 8 or 16");
+    if (window > 0) {
+        for (int mode = 0; mode < modes_of(h); ++mode)
+            for (int ax = 0; ax < 3; ++ax) {
+                const CoefSet &cs = h->coef[mode][ax];
+                if (cs.min_window == 0 || window < cs.min_window)
+                    return fail(h, GP_ERR_ARG, "window too small for the accuracy of this dt");
+            }
+    }
+    for (int mode = 0; mode < modes_of(h); ++mode)
+        for (int ax = 0; ax < 3; ++ax) {
+            CoefSet &cs = h->coef[mode][ax];
+            cs.window = window < 0 ? cs.min_window : window;
+        }
+    h->forced_window = window;
+    return GP_OK;
+}
+
+gp_status gp_set_threads(gp_handle h, int axis, int threads) {
+    if (!h || axis < 0 || axis > 2) return fail(h, GP_ERR_ARG, "bad axis");
+    if (threads < 32 || threads > 256 || threads % 32)
+        return fail(h, GP_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
+    h->threads[axis] = threads;
+    return GP_OK;
+}
+
+const char *gp_last_error(gp_handle h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+const char *gp_version(void) { return "gpcn 0.1 (sm_103a)"; }
+
+}  // extern "C"

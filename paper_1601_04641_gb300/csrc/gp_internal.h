@@ -1,0 +1,97 @@
+// gp_internal.h -- launch descriptors shared by the runtime (gp_api.cu) and
+// the kernel translation units.  Host-visible plain structs only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gpcn {
+
+enum Prec { P_F64 = 0, P_F32 = 1 };
+
+// The three arithmetic forms of a sweep:
+//  IMAG_REAL  imaginary time on a real field   (c real, coefficients real)
+//  IMAG_CPLX  imaginary time on a complex field (c real, coefficients real)
+//  REALTIME   real time on a complex field     (c = i kappa, coefficients complex)
+enum Form { F_IMAG_REAL = 0, F_IMAG_CPLX = 1, F_REALTIME = 2 };
+
+// Which sweep of the step: X carries the fused kick, Z the fused norm.
+enum Kind { K_X = 0, K_Y = 1, K_Z = 2 };
+
+// Arguments of one line-solve launch (all lines of one axis).
+struct SweepArgs {
+    void *psi;             // element array, layout z-fastest
+    const void *cp;        // Thomas multipliers cp[t], t = 0..N-3 (real or complex)
+    const void *ip;        // inverse pivots ip[t]
+    long long n_lines;     // lines of this axis
+    long long inner;       // line L starts at (L / inner) * outer_stride + (L % inner)
+    long long outer_stride;
+    long long stride;      // element stride along the line
+    int N;                 // nodes along the line (interior N - 2)
+    double kappa;          // |c| = dt / (4 d^2)
+    // kick (K_X): site (i, j, k) with i along the line, (j, k) = (L / nz, L % nz)
+    const double *scale;   // pending renormalisation factor applied on load
+    double dt, g;
+    double half_w2[3];     // (gamma^2, nu^2, lambda^2) / 2
+    double origin[3];      // coordinate of node 0 per axis
+    double d[3];           // spacings
+    int nz, ny;
+    // norm (K_Z): block partials, last-block-done counter, outputs
+    double *partials;
+    unsigned int *counter;
+    double *norm_out;      // dV * sum |psi|^2 of the result
+    double *scale_out;     // 1 / sqrt(norm) when want_scale
+    double dV;
+    int want_scale;
+    // exact two-pass solve scratch flag (window 0): dp is staged in psi itself
+};
+
+struct SweepLaunch {
+    Prec prec;
+    Form form;
+    Kind kind;
+    int window;            // 4, 8, 16, or 0 for the exact two-pass solve
+    int threads;           // threads per block
+    int contiguous;        // 1: warp-tiled kernel for the stride-1 axis
+};
+
+cudaError_t launch_sweep(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s);
+// Highest window the templates provide.
+constexpr int kMaxWindow = 16;
+
+// Gaussian initial state (unnormalised) plus its norm partials.
+struct FieldArgs {
+    void *psi;
+    int n[3];
+    double d[3];
+    double origin[3];
+    double w[3];           // trap frequencies
+    double half_w2[3];
+    double g;
+    const double *scale;   // factor applied to psi on read
+    double dV;
+    double *partials;
+    unsigned int *counter;
+    double *out;           // observables: 9 raw sums + 6 derived values
+    double *scale_out;
+    double *norm_out;
+    long long sites;
+};
+
+cudaError_t launch_gaussian(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s);
+cudaError_t launch_norm(Prec p, bool cplx, const FieldArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_observables(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s);
+cudaError_t launch_apply_scale(Prec p, bool cplx, const FieldArgs &a, void *dst, cudaStream_t s);
+
+// Observables output layout in FieldArgs::out.
+enum ObsSlot {
+    O_RHO = 0, O_V, O_RHO2, O_X2, O_Y2, O_Z2, O_LX, O_LY, O_LZ,   // raw sums
+    O_NORM = 9, O_MU, O_E, O_RMSX, O_RMSY, O_RMSZ, O_FINITE,      // derived
+    O_COUNT = 16
+};
+
+int observables_blocks(const FieldArgs &a);
+constexpr int kReduceThreads = 256;
+
+}  // namespace gpcn

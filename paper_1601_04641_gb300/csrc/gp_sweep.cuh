@@ -1,0 +1,349 @@
+// gp_sweep.cuh -- CN line-solve kernels for one axis of the split-step step.
+//
+// Every line along the swept axis solves the CN system (paper, "Summary of
+// revisions": calclux / calcluy / calcluz)
+//     -c phi[t-1] + (1+2c) phi[t] - c phi[t+1] = c psi[t-1] + (1-2c) psi[t] + c psi[t+1]
+// on its n = N-2 interior nodes with zero end nodes, by the Thomas algorithm
+// on precomputed recursion coefficients (inverse pivots ip[t] and
+// multipliers cp[t], built once per dt on the host in FP64):
+//     forward   dp[t] = (r[t] + c dp[t-1]) ip[t]
+//     backward  phi[t] = dp[t] - cp[t] phi[t+1],  phi[n-1] = dp[n-1].
+//
+// One thread owns one line and streams it once from HBM: the forward sweep
+// is exact; the backward sweep is windowed.  dp values are kept in a
+// register ring of B + W entries.  After dp[t0 .. t0+B+W-1] are known, the
+// chunk phi[t0 .. t0+B-1] is recovered by starting the backward recurrence
+// at t0+B+W-1 with phi ~ dp (dropping cp * phi[t0+B+W]) and running it down
+// to t0.  The dropped term reaches phi[t0+B-1] multiplied by W+1 factors
+// |cp| < 1, so the chunk is exact to |cp|_max^(W+1) * max|phi|; the host
+// picks W so that this is below an eighth of the unit roundoff (or uses the
+// exact two-pass form, window 0, which stages dp in psi and reads it back).
+// The last chunk of a line is solved exactly from phi[n-1] = dp[n-1].
+//
+// The x sweep carries the fused potential-plus-nonlinear kick (calcnu),
+// applied to each value as it is loaded, together with the pending
+// renormalisation factor of the previous imaginary-time step; the z sweep
+// carries the fused norm reduction (two-stage, deterministic, FP64 across
+// threads) whose last block writes the next renormalisation factor.
+#pragma once
+
+#include "gp_internal.h"
+
+namespace gpcn {
+
+template <typename R> struct cx;
+template <> struct __align__(8) cx<float> { float re, im; };
+template <> struct __align__(16) cx<double> { double re, im; };
+
+// Read-only loads of coefficient-table entries (uniform across a warp).
+__device__ __forceinline__ float ldc(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ldc(const double *p) { return __ldg(p); }
+__device__ __forceinline__ cx<float> ldc(const cx<float> *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return cx<float>{v.x, v.y};
+}
+__device__ __forceinline__ cx<double> ldc(const cx<double> *p) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return cx<double>{v.x, v.y};
+}
+
+__device__ __forceinline__ float g_exp(float x) { return expf(x); }
+__device__ __forceinline__ double g_exp(double x) { return exp(x); }
+__device__ __forceinline__ void g_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void g_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+
+// Per-thread sum: plain FP64, or FP32 with an error-free two-sum
+// compensation term (Knuth) so that long FP32 sums keep FP64-like accuracy.
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// ------------------------------------------------------------------ forms
+// Imaginary time, real field: c = kappa, coefficients real.
+template <typename R> struct FImagReal {
+    using V = R;
+    using C = R;
+    __device__ __forceinline__ static V zero() { return R(0); }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, R k) {
+        return fma(k, (pm + p1) - R(2) * p0, p0);
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ip) { return fma(k, dprev, r) * ip; }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) { return fma(-cp, phi, dp); }
+    __device__ __forceinline__ static R abs2(V v) { return v * v; }
+    __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
+        V q = p * s;
+        return q * g_exp(-dt * fma(g, q * q, vpot));
+    }
+};
+
+// Imaginary time, complex field: c = kappa real, applied to both parts.
+template <typename R> struct FImagCplx {
+    using V = cx<R>;
+    using C = R;
+    __device__ __forceinline__ static V zero() { return V{R(0), R(0)}; }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, R k) {
+        return V{fma(k, (pm.re + p1.re) - R(2) * p0.re, p0.re),
+                 fma(k, (pm.im + p1.im) - R(2) * p0.im, p0.im)};
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ip) {
+        return V{fma(k, dprev.re, r.re) * ip, fma(k, dprev.im, r.im) * ip};
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) {
+        return V{fma(-cp, phi.re, dp.re), fma(-cp, phi.im, dp.im)};
+    }
+    __device__ __forceinline__ static R abs2(V v) { return fma(v.re, v.re, v.im * v.im); }
+    __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
+        V q{p.re * s, p.im * s};
+        R f = g_exp(-dt * fma(g, abs2(q), vpot));
+        return V{q.re * f, q.im * f};
+    }
+};
+
+// Real time, complex field: c = i kappa, coefficients complex.
+template <typename R> struct FRealTime {
+    using V = cx<R>;
+    using C = cx<R>;
+    __device__ __forceinline__ static V zero() { return V{R(0), R(0)}; }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, R k) {
+        // r = p0 + i k (pm + p1 - 2 p0)
+        R dre = (pm.re + p1.re) - R(2) * p0.re;
+        R dim = (pm.im + p1.im) - R(2) * p0.im;
+        return V{fma(-k, dim, p0.re), fma(k, dre, p0.im)};
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ip) {
+        // (r + i k dprev) * ip
+        R ure = fma(-k, dprev.im, r.re);
+        R uim = fma(k, dprev.re, r.im);
+        return V{fma(ure, ip.re, -uim * ip.im), fma(ure, ip.im, uim * ip.re)};
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) {
+        // dp - cp * phi
+        R pre = fma(cp.re, phi.re, -cp.im * phi.im);
+        R pim = fma(cp.re, phi.im, cp.im * phi.re);
+        return V{dp.re - pre, dp.im - pim};
+    }
+    __device__ __forceinline__ static R abs2(V v) { return fma(v.re, v.re, v.im * v.im); }
+    __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
+        V q{p.re * s, p.im * s};
+        R sn, cs;
+        g_sincos(dt * fma(g, abs2(q), vpot), &sn, &cs);
+        // exp(-i theta) q
+        return V{fma(cs, q.re, sn * q.im), fma(cs, q.im, -sn * q.re)};
+    }
+};
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum `v` over the block in a fixed order; valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = (lane < (int)((blockDim.x + 31) >> 5)) ? red[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// Block partial of sum |phi|^2, then the last block to finish sums the
+// partials in block order and writes the norm (and the renormalisation
+// factor) -- deterministic whatever the block completion order.
+__device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a) {
+    __shared__ double red[32];
+    __shared__ int is_last;
+    double bsum = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        a.partials[blockIdx.x] = bsum;
+        __threadfence();
+        unsigned prev = atomicAdd(a.counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(a.partials + b);
+    double total = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        double nrm = a.dV * total;
+        *a.norm_out = nrm;
+        if (a.want_scale) *a.scale_out = 1.0 / sqrt(nrm);
+        *a.counter = 0u;
+    }
+}
+
+// ------------------------------------------------------------------ one line
+// Solves one line starting at `line` (element stride `st`).  Load / store
+// functors hide the kick (x sweep) and the norm accumulation (z sweep).
+template <class F, typename R, int B, int W, class LoadF, class PutF>
+__device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename F::C *__restrict__ cp,
+                                                    const typename F::C *__restrict__ ip,
+                                                    LoadF load, PutF put) {
+    using V = typename F::V;
+    V D[B + W];
+    V pm = F::zero();
+    V p0 = load(0);
+    V p1 = load(1);
+    V dprev = F::zero();
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        if (q < n) {
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + q));
+            D[q] = dprev;
+            pm = p0;
+            p0 = p1;
+            p1 = load(q + 2);
+        }
+    }
+    int t0 = 0;
+    for (; t0 + B + W <= n; t0 += B) {
+        V P[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) P[q] = load(t0 + W + q + 2);
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + t0 + W + q));
+            D[W + q] = dprev;
+            pm = p0;
+            p0 = p1;
+            p1 = P[q];
+        }
+        V phi = D[B + W - 1];
+#pragma unroll
+        for (int q = B + W - 2; q >= B; --q) phi = F::back(D[q], ldc(cp + t0 + q), phi);
+#pragma unroll
+        for (int q = B - 1; q >= 0; --q) {
+            phi = F::back(D[q], ldc(cp + t0 + q), phi);
+            put(t0 + q, phi);
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) D[q] = D[B + q];
+    }
+    const int rem = n - t0;  // 0 <= rem < B + W: finish exactly
+#pragma unroll
+    for (int q = W; q < B + W; ++q) {
+        if (q < rem) {
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + t0 + q));
+            D[q] = dprev;
+            pm = p0;
+            p0 = p1;
+            p1 = load(t0 + q + 2);
+        }
+    }
+    V phi = F::zero();
+#pragma unroll
+    for (int q = B + W - 1; q >= 0; --q) {
+        if (q < rem) {
+            phi = F::back(D[q], ldc(cp + t0 + q), (q == rem - 1) ? F::zero() : phi);
+            put(t0 + q, phi);
+        }
+    }
+}
+
+// Exact two-pass Thomas: dp is staged in psi (node t+1 <- dp[t] once psi[t]
+// has been consumed) and read back by the backward sweep.
+template <class F, typename R, class LoadF, class PutF>
+__device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F::C *__restrict__ cp,
+                                                 const typename F::C *__restrict__ ip,
+                                                 typename F::V *line, long long st, LoadF load,
+                                                 PutF put) {
+    using V = typename F::V;
+    V pm = F::zero();
+    V p0 = load(0);
+    V p1 = load(1);
+    V dprev = F::zero();
+    for (int t = 0; t < n; ++t) {
+        dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + t));
+        pm = p0;
+        p0 = p1;
+        p1 = load(t + 2);
+        if (t < n - 1) line[(long long)(t + 1) * st] = dprev;
+    }
+    V phi = dprev;
+    put(n - 1, phi);
+    for (int t = n - 2; t >= 0; --t) {
+        phi = F::back(line[(long long)(t + 1) * st], ldc(cp + t), phi);
+        put(t, phi);
+    }
+}
+
+// Outputs per chunk of the windowed solve: 16, or 8 for 16-byte elements
+// (complex FP64) to bound the register ring.
+template <typename V> __host__ __device__ constexpr int chunk_len() { return sizeof(V) >= 16 ? 8 : 16; }
+
+// ------------------------------------------------------------------ kernel
+// One thread per line; consecutive threads own lines that are adjacent in
+// memory (consecutive z for the x and y sweeps), so every row of a warp's
+// lines is one coalesced access.
+template <class F, typename R, int W, int KIND>
+__global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
+    using V = typename F::V;
+    using C = typename F::C;
+    const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    Acc<R> acc;
+    if (L < a.n_lines) {
+        V *line = static_cast<V *>(a.psi) + (L / a.inner) * a.outer_stride + (L % a.inner);
+        const long long st = a.stride;
+        const int n = a.N - 2;
+        const C *cp = static_cast<const C *>(a.cp);
+        const C *ip = static_cast<const C *>(a.ip);
+        const R kap = (R)a.kappa;
+        R s = R(1), dt = R(0), g = R(0), hx = R(0), x0 = R(0), dx = R(0), vyz = R(0);
+        if (KIND == K_X) {
+            s = (R)__ldg(a.scale);
+            dt = (R)a.dt;
+            g = (R)a.g;
+            const int j = (int)(L / a.nz), k = (int)(L % a.nz);
+            const double y = a.origin[1] + j * a.d[1];
+            const double z = a.origin[2] + k * a.d[2];
+            vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
+            hx = (R)a.half_w2[0];
+            x0 = (R)a.origin[0];
+            dx = (R)a.d[0];
+        }
+        auto load = [&](int t) -> V {
+            if (t >= n) return F::zero();
+            V v = line[(long long)(t + 1) * st];
+            if (KIND == K_X) {
+                const R x = fma((R)(t + 1), dx, x0);
+                v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
+            }
+            return v;
+        };
+        auto put = [&](int t, V v) {
+            line[(long long)(t + 1) * st] = v;
+            if (KIND == K_Z) acc.add(F::abs2(v));
+        };
+        line[0] = F::zero();
+        line[(long long)(a.N - 1) * st] = F::zero();
+        if constexpr (W > 0)
+            solve_line_windowed<F, R, chunk_len<V>(), W>(n, kap, cp, ip, load, put);
+        else
+            solve_line_exact<F, R>(n, kap, cp, ip, line, st, load, put);
+    }
+    if (KIND == K_Z) norm_finalize(acc.value(), a);
+}
+
+}  // namespace gpcn

@@ -1,0 +1,8 @@
+// Line-solve kernels: float, form FImagCplx.
+#include "k_sweep_inst.cuh"
+
+namespace gpcn {
+cudaError_t launch_sweep_f32_ic(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    return launch_form<FImagCplx<float>, float>(L, a, s);
+}
+}  // namespace gpcn

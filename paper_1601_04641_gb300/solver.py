@@ -1,0 +1,155 @@
+"""Python front end of libgpcn: one condensate on one GPU.
+
+PyTorch provides the device memory of psi and the CUDA stream; every step of
+the method runs in the library's CUDA kernels through the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+
+_TORCH_DTYPES = {("f64", "complex"): "complex128", ("f32", "complex"): "complex64",
+                 ("f64", "real"): "float64", ("f32", "real"): "float32"}
+_NP_DTYPES = {("f64", "complex"): np.complex128, ("f32", "complex"): np.complex64,
+              ("f64", "real"): np.float64, ("f32", "real"): np.float32}
+
+
+class GP:
+    """Split-step Crank-Nicolson solver of the 3D GP equation in a fully
+    anisotropic harmonic trap (imaginary or real time).
+
+    shape: (nx, ny, nz); d: (dx, dy, dz); omega: (gamma, nu, lambda).
+    precision: "f64" or "f32" (element precision of psi; reductions are FP64);
+    field: "complex" or "real" (real allows imaginary time only).
+    """
+
+    def __init__(self, shape, d, dt, omega, g, precision="f64", field="complex", device=None,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.lib = N.load()
+        self.shape = tuple(int(s) for s in shape)
+        self.d = tuple(float(x) for x in d)
+        self.precision, self.field = precision, field
+        key = (precision, field)
+        if key not in _TORCH_DTYPES:
+            raise ValueError("precision must be f64/f32 and field complex/real")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.np_dtype = _NP_DTYPES[key]
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.psi = torch.zeros(self.shape, dtype=getattr(torch, _TORCH_DTYPES[key]),
+                                   device=self.device)
+            grid = N.Grid(*self.shape, *self.d)
+            h = N.Handle()
+            st = self.lib.gp_create_ext(ctypes.byref(h), grid, float(dt), float(omega[0]),
+                                        float(omega[1]), float(omega[2]), float(g),
+                                        N.GP_F64 if precision == "f64" else N.GP_F32,
+                                        N.GP_COMPLEX if field == "complex" else N.GP_REAL,
+                                        ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.c_void_p(self.psi.data_ptr()),
+                                        self.psi.numel() * self.psi.element_size())
+            N.check(st, None)
+        self.h = h
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        N.check(st, self.h)
+
+    # ------------------------------------------------------------ state
+    def init_gaussian(self):
+        self._ck(self.lib.gp_init_gaussian(self.h))
+
+    def set_psi(self, arr):
+        """Copy psi in from a numpy array or a CUDA tensor of this shape."""
+        torch = self._torch
+        if isinstance(arr, torch.Tensor) and arr.is_cuda:
+            t = arr.to(dtype=self.psi.dtype).contiguous()
+            if tuple(t.shape) != self.shape:
+                raise ValueError("shape mismatch")
+            self._ck(self.lib.gp_set_psi(self.h, ctypes.c_void_p(t.data_ptr()), 1))
+            self._keep = t
+            return
+        a = np.ascontiguousarray(np.asarray(arr), dtype=self.np_dtype)
+        if a.shape != self.shape:
+            raise ValueError("shape mismatch")
+        self._ck(self.lib.gp_set_psi(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def get_psi(self, as_numpy=True):
+        """Current psi (pending renormalisation applied)."""
+        if as_numpy:
+            out = np.empty(self.shape, dtype=self.np_dtype)
+            self._ck(self.lib.gp_get_psi(self.h, out.ctypes.data_as(ctypes.c_void_p), 0))
+            return out
+        out = self._torch.empty_like(self.psi)
+        self._ck(self.lib.gp_get_psi(self.h, ctypes.c_void_p(out.data_ptr()), 1))
+        return out
+
+    def set_g(self, g):
+        self._ck(self.lib.gp_set_g(self.h, float(g)))
+
+    def set_dt(self, dt):
+        self._ck(self.lib.gp_set_dt(self.h, float(dt)))
+
+    # ------------------------------------------------------------ stepping
+    def step_imag(self, nsteps=1):
+        self._ck(self.lib.gp_step_imag(self.h, int(nsteps)))
+
+    def step_real(self, nsteps=1):
+        self._ck(self.lib.gp_step_real(self.h, int(nsteps)))
+
+    def stage(self, stage, realtime=False):
+        self._ck(self.lib.gp_step_stage(self.h, int(stage), int(bool(realtime))))
+
+    def run_imag_until(self, mu_tol, check_every=10, max_steps=100000):
+        taken = ctypes.c_int(0)
+        self._ck(self.lib.gp_run_imag_until(self.h, float(mu_tol), int(check_every),
+                                            int(max_steps), ctypes.byref(taken)))
+        return taken.value
+
+    def observables(self):
+        o = N.Obs()
+        self._ck(self.lib.gp_observables(self.h, ctypes.byref(o)))
+        return {"norm": o.norm, "mu": o.mu, "energy": o.energy, "rms_x": o.rms_x,
+                "rms_y": o.rms_y, "rms_z": o.rms_z, "step": o.step, "t": o.t}
+
+    def set_tracking(self, every, capacity=1024):
+        """Queue the observables every `every` steps on the device (no host sync)."""
+        self._ck(self.lib.gp_set_tracking(self.h, int(every), int(capacity)))
+
+    def tracking(self, max_records=1 << 16):
+        """Tracked records so far, oldest first."""
+        buf = (N.Obs * max_records)()
+        cnt = ctypes.c_int(0)
+        self._ck(self.lib.gp_get_tracking(self.h, buf, int(max_records), ctypes.byref(cnt)))
+        return [{"norm": o.norm, "mu": o.mu, "energy": o.energy, "rms_x": o.rms_x, "rms_y": o.rms_y,
+                 "rms_z": o.rms_z, "step": o.step, "t": o.t} for o in buf[:min(cnt.value, max_records)]]
+
+    def sync(self):
+        self._ck(self.lib.gp_sync(self.h))
+
+    # ------------------------------------------------------------ tuning
+    def window(self, mode=0):
+        w = (ctypes.c_int * 3)()
+        self._ck(self.lib.gp_get_window(self.h, int(mode), w))
+        return tuple(w)
+
+    def set_window(self, window):
+        self._ck(self.lib.gp_set_window(self.h, int(window)))
+
+    def set_threads(self, axis, threads):
+        self._ck(self.lib.gp_set_threads(self.h, int(axis), int(threads)))

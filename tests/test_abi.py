@@ -1,0 +1,96 @@
+"""C ABI checks that need no GPU: libgpcn.so builds for sm_103a, loads, exports
+every function include/gp.h declares, and rejects bad arguments on the host
+before touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1601_04641_gb300 import _native as N
+from paper_1601_04641_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(gp_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return N.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gp_create", "gp_step_imag", "gp_step_real", "gp_observables"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", N.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(gp_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for name in declared_functions():
+        getattr(lib, name)
+
+
+def test_binding_declares_exactly_the_header():
+    assert sorted(N.SIGNATURES) == declared_functions()
+
+
+def _create(lib, **kw):
+    args = dict(nx=8, ny=8, nz=8, dx=0.1, dy=0.1, dz=0.1, dt=1e-3, gamma=1.0, nu=1.0, lam=1.0,
+                g=1.0, prec=N.GP_F64, field=N.GP_COMPLEX)
+    args.update(kw)
+    h = N.Handle()
+    grid = N.Grid(args["nx"], args["ny"], args["nz"], args["dx"], args["dy"], args["dz"])
+    st = lib.gp_create(ctypes.byref(h), grid, args["dt"], args["gamma"], args["nu"], args["lam"],
+                       args["g"], args["prec"], args["field"], None)
+    return st, h
+
+
+@pytest.mark.parametrize("bad", [dict(nx=2), dict(nz=0), dict(dx=0.0), dict(dy=-1.0),
+                                 dict(dz=float("nan")), dict(dt=0.0), dict(dt=float("inf")),
+                                 dict(gamma=-1.0), dict(nu=float("nan")), dict(g=float("inf")),
+                                 dict(prec=7), dict(field=9)])
+def test_bad_arguments_are_rejected_on_the_host(lib, bad):
+    st, h = _create(lib, **bad)
+    assert st == N.GP_ERR_ARG
+    assert not h.value
+    assert lib.gp_last_error(None)
+
+
+def test_null_handle_and_out_pointers(lib):
+    assert lib.gp_step_imag(None, 1) == N.GP_ERR_ARG
+    assert lib.gp_observables(None, None) == N.GP_ERR_ARG
+    grid = N.Grid(8, 8, 8, 0.1, 0.1, 0.1)
+    assert lib.gp_create(None, grid, 1e-3, 1.0, 1.0, 1.0, 1.0, 0, 0, None) == N.GP_ERR_ARG
+    lib.gp_destroy(None)
+    assert b"sm_103a" in lib.gp_version()
+
+
+def test_valid_create_without_gpu_reports_cuda_error(lib):
+    """Valid arguments reach CUDA; with no device that is GP_ERR_CUDA, not a crash."""
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    st, h = _create(lib)
+    if has_gpu:
+        assert st == N.GP_OK
+        lib.gp_destroy(h)
+    else:
+        assert st in (N.GP_ERR_CUDA, N.GP_ERR_NOMEM)

@@ -1,0 +1,284 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, on the same seeded
+inputs (GPU only).
+
+Tolerances: the FP64 path within 1e-12 relative in psi and mu (1e-13 for a
+single stage); the FP32 forms |d mu|/mu <= 1e-5 and relative L2 of psi <= 1e-4.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_04641_gb300 import _native as N
+from paper_1601_04641_gb300 import build, inputs
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SHAPE = (37, 29, 41)          # every axis spans several chunks plus a ragged tail
+D = (0.31, 0.27, 0.22)
+OMEGA = (1.0, 1.4, 2.0)
+OBS = ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def make(shape, d, dt, omega, g, prec="f64", field="complex"):
+    from paper_1601_04641_gb300.solver import GP
+    return GP(shape, d, dt, omega, g, prec, field)
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def oracle_stage(psi, stage, d, dt, omega, g, realtime):
+    if stage == 0:
+        oracle.kick(psi, d, dt, omega, g, realtime)
+    oracle.sweep(psi, d, stage, dt, realtime)
+    if stage == 2 and not realtime:
+        oracle.renormalize(psi, d)
+    return psi
+
+
+# ---------------------------------------------------------------- single stages
+@pytest.mark.parametrize("realtime", [False, True])
+@pytest.mark.parametrize("stage", [0, 1, 2])
+def test_single_stage_fp64(stage, realtime):
+    dt, g = 0.013, 7.5
+    psi0 = inputs.random_field(SHAPE, seed=21 + stage)
+    gp = make(SHAPE, D, dt, OMEGA, g)
+    gp.set_psi(psi0)
+    gp.stage(stage, realtime)
+    got = gp.get_psi()
+    ref = oracle_stage(psi0.copy(), stage, D, dt, OMEGA, g, realtime)
+    assert rel_max(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("window", [0, 4, 8, 16])
+@pytest.mark.parametrize("realtime", [False, True])
+def test_every_window_matches_oracle_step(window, realtime):
+    """The windowed backward sweep (every admissible window) and the exact
+    two-pass form give the oracle's step."""
+    dt, g = 0.004, 12.0
+    psi0 = inputs.random_field(SHAPE, seed=5)
+    gp = make(SHAPE, D, dt, OMEGA, g)
+    mode = 1 if realtime else 0
+    try:
+        gp.set_window(window)
+    except N.GPError:
+        pytest.skip("window %d below the admissible minimum %s" % (window, gp.window(mode)))
+    assert gp.window(mode) == (window,) * 3
+    gp.set_psi(psi0)
+    for _ in range(3):
+        (gp.step_real if realtime else gp.step_imag)(1)
+    got = gp.get_psi()
+    ref = psi0.copy()
+    oracle.step(ref, D, dt, OMEGA, g, realtime, 3)
+    assert rel_max(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 3), (3, 4, 5), (5, 3, 4), (4, 5, 3), (6, 7, 8),
+                                   (19, 18, 17), (2 * 16 + 4 + 2, 3, 24 + 2)])
+@pytest.mark.parametrize("realtime", [False, True])
+def test_edge_sizes(shape, realtime):
+    """One interior node, interiors shorter than the window, exactly one chunk
+    plus window, and line counts far from a block multiple."""
+    d, dt, g = (0.4, 0.35, 0.3), 0.01, 3.0
+    psi0 = inputs.random_field(shape, seed=sum(shape))
+    if not np.any(psi0):
+        psi0[tuple(n // 2 for n in shape)] = 0.7 - 0.2j
+    for window in (-1, 0):
+        gp = make(shape, d, dt, OMEGA, g)
+        gp.set_window(window)
+        gp.set_psi(psi0)
+        (gp.step_real if realtime else gp.step_imag)(2)
+        got = gp.get_psi()
+        ref = psi0.copy()
+        oracle.step(ref, d, dt, OMEGA, g, realtime, 2)
+        assert rel_max(got, ref) <= 1e-12, (shape, window)
+
+
+@pytest.mark.parametrize("threads", [32, 64, 96, 256])
+def test_block_sizes(threads):
+    dt, g = 0.004, 12.0
+    psi0 = inputs.random_field(SHAPE, seed=8)
+    gp = make(SHAPE, D, dt, OMEGA, g)
+    for ax in range(3):
+        gp.set_threads(ax, threads)
+    gp.set_psi(psi0)
+    gp.step_real(2)
+    ref = psi0.copy()
+    oracle.step(ref, D, dt, OMEGA, g, True, 2)
+    assert rel_max(gp.get_psi(), ref) <= 1e-12
+
+
+# ---------------------------------------------------------------- observables
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_observables_of_a_random_field(prec, tol):
+    psi0 = inputs.random_field(SHAPE, seed=3)
+    gp = make(SHAPE, D, 0.01, OMEGA, 25.0, prec)
+    gp.set_psi(psi0.astype(np.complex64 if prec == "f32" else np.complex128))
+    got = gp.observables()
+    ref = oracle.observables(psi0 if prec == "f64" else psi0.astype(np.complex64).astype(np.complex128),
+                             D, OMEGA, 25.0)
+    for k in OBS:
+        assert abs(got[k] - ref[k]) <= tol * abs(ref[k]), (k, got[k], ref[k])
+
+
+def test_nonfinite_psi_is_reported():
+    psi0 = inputs.random_field((8, 9, 10), seed=1)
+    psi0[4, 4, 4] = np.nan
+    gp = make((8, 9, 10), (0.3, 0.3, 0.3), 0.01, OMEGA, 1.0)
+    gp.set_psi(psi0)
+    with pytest.raises(N.GPError) as e:
+        gp.observables()
+    assert e.value.status == N.GP_ERR_NONFINITE
+
+
+def test_real_time_on_real_field_is_refused():
+    gp = make((8, 8, 8), (0.3, 0.3, 0.3), 0.01, OMEGA, 1.0, "f64", "real")
+    with pytest.raises(N.GPError) as e:
+        gp.step_real(1)
+    assert e.value.status == N.GP_ERR_STATE
+
+
+# ---------------------------------------------------------------- whole runs, FP64
+@pytest.mark.parametrize("field", ["real", "complex"])
+def test_imag_small_fp64_matches_golden(field):
+    """64x48x40 imaginary time from the Gaussian, 300 steps: mu, E, rms, norm
+    and sampled psi match the oracle's stored values to 1e-12."""
+    gold = json.load(open(os.path.join(HERE, "golden", "imag_small_oracle.json")))
+    p = inputs.imag_small()
+    gp = make(p.shape, p.d, p.dt, p.omega, p.g, "f64", field)
+    gp.init_gaussian()
+    done = 0
+    for target in (0, 1, 10, 100, 300):
+        gp.step_imag(target - done)
+        done = target
+        got = gp.observables()
+        ref = gold["checkpoints"][str(target)]
+        for k in OBS:
+            assert abs(got[k] - ref[k]) <= 1e-12 * abs(ref[k]), (target, k, got[k], ref[k])
+    psi = gp.get_psi()
+    scale = max(abs(complex(s["re"], s["im"])) for s in gold["samples_after_300"])
+    for s in gold["samples_after_300"]:
+        v = psi[tuple(s["site"])]
+        assert abs(v - complex(s["re"], s["im"])) <= 1e-12 * scale
+
+
+def test_real_time_fp64_matches_oracle_and_conserves_norm():
+    shape, d, dt, g = (40, 34, 30), (0.3, 0.3, 0.3), 0.005, 40.0
+    omega = (0.5, 1.0, 1.5)
+    psi0 = inputs.random_field(shape, seed=12)
+    oracle.renormalize(psi0, d)
+    gp = make(shape, d, dt, omega, g)
+    gp.set_psi(psi0)
+    gp.step_real(200)
+    got = gp.get_psi()
+    ref = psi0.copy()
+    oracle.step(ref, d, dt, omega, g, True, 200)
+    assert rel_l2(got, ref) <= 1e-12
+    assert rel_max(got, ref) <= 1e-12
+    o = gp.observables()
+    r = oracle.observables(ref, d, omega, g)
+    for k in OBS:
+        assert abs(o[k] - r[k]) <= 1e-12 * abs(r[k])
+    assert abs(o["norm"] - 1.0) <= 1e-12
+
+
+def test_run_imag_until_matches_oracle():
+    p = inputs.sized_box((24, 22, 20), (1.0, 1.4, 2.0), 50.0, dt_factor=0.2)
+    ref = oracle.gaussian(p.shape, p.d, p.omega)
+    steps_ref, mu_ref = oracle.run_imag_until(ref, p.d, p.dt, p.omega, p.g, 1e-9, 10, 5000)
+    gp = make(p.shape, p.d, p.dt, p.omega, p.g, "f64", "real")
+    gp.init_gaussian()
+    steps = gp.run_imag_until(1e-9, 10, 5000)
+    assert steps == steps_ref
+    assert abs(gp.observables()["mu"] - mu_ref) <= 1e-12 * mu_ref
+
+
+def test_quench_sequence_fp64():
+    """Imaginary-time preparation at g, quench to 2g (set_g), real time."""
+    shape, d, omega = (30, 26, 22), (0.35, 0.35, 0.35), (0.5, 1.0, 1.5)
+    dt_i, dt_r = 0.1 * 0.35 ** 2, 0.02 * 0.35 ** 2
+    ref = oracle.gaussian(shape, d, omega)
+    oracle.step(ref, d, dt_i, omega, 20.0, False, 100)
+    gp = make(shape, d, dt_i, omega, 20.0)
+    gp.init_gaussian()
+    gp.step_imag(100)
+    assert rel_max(gp.get_psi(), ref) <= 1e-12
+    gp.set_g(40.0)
+    gp.set_dt(dt_r)
+    gp.step_real(100)
+    oracle.step(ref, d, dt_r, omega, 40.0, True, 100)
+    assert rel_max(gp.get_psi(), ref) <= 1e-12
+
+
+# ---------------------------------------------------------------- FP32 forms
+def test_imag_small_fp32_forms():
+    gold = json.load(open(os.path.join(HERE, "golden", "imag_small_oracle.json")))
+    p = inputs.imag_small()
+    ref_psi = oracle.gaussian(p.shape, p.d, p.omega)
+    oracle.step(ref_psi, p.d, p.dt, p.omega, p.g, False, 300)
+    for field in ("real", "complex"):
+        gp = make(p.shape, p.d, p.dt, p.omega, p.g, "f32", field)
+        gp.init_gaussian()
+        gp.step_imag(300)
+        o = gp.observables()
+        ref = gold["checkpoints"]["300"]
+        assert abs(o["mu"] - ref["mu"]) <= 1e-5 * ref["mu"]
+        for k in ("energy", "rms_x", "rms_y", "rms_z", "norm"):
+            assert abs(o[k] - ref[k]) <= 1e-5 * abs(ref[k]), (field, k)
+        assert rel_l2(gp.get_psi().astype(np.complex128), ref_psi) <= 1e-4
+
+
+def test_real_time_fp32_form():
+    shape, d, dt, g = (48, 40, 32), (0.25, 0.25, 0.25), 0.02 * 0.25 ** 2, 40.0
+    omega = (0.5, 1.0, 1.5)
+    psi0 = oracle.gaussian(shape, d, omega)
+    oracle.step(psi0, d, 0.1 * 0.25 ** 2, omega, 20.0, False, 100)
+    gp = make(shape, d, dt, omega, g, "f32", "complex")
+    gp.set_psi(psi0.astype(np.complex64))
+    gp.step_real(300)
+    ref = psi0.astype(np.complex64).astype(np.complex128)
+    oracle.step(ref, d, dt, omega, g, True, 300)
+    o = gp.observables()
+    r = oracle.observables(ref, d, omega, g)
+    assert abs(o["mu"] - r["mu"]) <= 1e-5 * r["mu"]
+    assert abs(o["energy"] - r["energy"]) <= 1e-5 * r["energy"]
+    assert rel_l2(gp.get_psi().astype(np.complex128), ref) <= 1e-4
+
+
+# ---------------------------------------------------------------- full-size, sampled
+@pytest.mark.parametrize("which", ["real_medium", "real_large"])
+def test_full_size_one_step_sampled(which):
+    """At the benchmark sizes (240x200x160 FP64, 480x400x320 complex64) one
+    real-time step from a seeded field matches the oracle's step at 4096
+    seeded sample sites."""
+    p = getattr(inputs, which)()
+    prec = "f64" if which == "real_medium" else "f32"
+    psi0 = inputs.random_field(p.shape, seed=99)
+    if prec == "f32":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    gp = make(p.shape, p.d, p.dt, p.omega, p.g, prec, "complex")
+    gp.set_psi(psi0.astype(np.complex64) if prec == "f32" else psi0)
+    gp.step_real(1)
+    got = gp.get_psi()
+    gp.close()
+    ref = psi0
+    oracle.step(ref, p.d, p.dt, p.omega, p.g, True, 1)
+    rng = np.random.default_rng(7)
+    idx = tuple(rng.integers(0, n, size=4096) for n in p.shape)
+    scale = np.max(np.abs(ref))
+    err = np.max(np.abs(got[idx] - ref[idx])) / scale
+    assert err <= (1e-12 if prec == "f64" else 1e-5), err
