@@ -81,6 +81,7 @@ struct gp_handle_s {
     long long step = 0;
     double t = 0;
     int threads[3] = {128, 128, 128};
+    bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     // observables history queued during stepping
     int track_every = 0, track_cap = 0, track_count = 0;
     double *d_track = nullptr;
@@ -133,15 +134,17 @@ int modes_of(gp_handle h) { return h->field == GP_COMPLEX ? 2 : 1; }
 
 // FP64 Thomas coefficients of the CN matrix (-c, 1+2c, -c) on n interior
 // nodes: den[0] = 1+2c, den[t] = 1+2c + c cp[t-1], ip = 1/den, cp = -c ip.
+// The inverse pivot is returned as its deviation from one,
+// ipm1 = ip - 1 = (1 - den) / den, which the kernels apply as u + u ipm1.
 void thomas_coefficients(std::complex<double> c, int n, std::vector<std::complex<double>> &cp,
-                         std::vector<std::complex<double>> &ip) {
+                         std::vector<std::complex<double>> &ipm1) {
     cp.assign(n, 0.0);
-    ip.assign(n, 0.0);
-    const std::complex<double> b = 1.0 + 2.0 * c;
+    ipm1.assign(n, 0.0);
     for (int t = 0; t < n; ++t) {
-        const std::complex<double> den = (t == 0) ? b : b + c * cp[t - 1];
-        ip[t] = 1.0 / den;
-        cp[t] = -c * ip[t];
+        const std::complex<double> excess = 2.0 * c + (t == 0 ? 0.0 : c * cp[t - 1]);  // den - 1
+        const std::complex<double> den = 1.0 + excess;
+        ipm1[t] = -excess / den;
+        cp[t] = -c / den;
     }
 }
 
@@ -385,7 +388,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     const CoefSet &cs = h->coef[mode][ax];
     L.window = cs.window;
     L.threads = h->threads[ax];
-    L.contiguous = 0;
+    L.contiguous = (ax == 2 && h->contiguous_z && cs.window > 0) ? 1 : 0;
 
     SweepArgs a;
     std::memset(&a, 0, sizeof(a));

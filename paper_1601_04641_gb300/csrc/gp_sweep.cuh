@@ -8,6 +8,11 @@
 // multipliers cp[t], built once per dt on the host in FP64):
 //     forward   dp[t] = (r[t] + c dp[t-1]) ip[t]
 //     backward  phi[t] = dp[t] - cp[t] phi[t+1],  phi[n-1] = dp[n-1].
+// The tables hold ip[t] - 1 (small, about -2c) rather than ip[t], and the
+// forward step forms u + u (ip - 1) with fused multiply-adds: |ip| is close
+// to one, so a rounded ip would act as a gain error on every dp, the same in
+// every step, and in real time that is a steady norm drift (about 3e-8 per
+// FP32 sweep); stored as a deviation its rounding error is ~|2c| smaller.
 //
 // One thread owns one line and streams it once from HBM: the forward sweep
 // is exact; the backward sweep is windowed.  dp values are kept in a
@@ -80,7 +85,10 @@ template <typename R> struct FImagReal {
     __device__ __forceinline__ static V rhs(V pm, V p0, V p1, R k) {
         return fma(k, (pm + p1) - R(2) * p0, p0);
     }
-    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ip) { return fma(k, dprev, r) * ip; }
+    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ipm1) {
+        const V u = fma(k, dprev, r);
+        return fma(u, ipm1, u);
+    }
     __device__ __forceinline__ static V back(V dp, C cp, V phi) { return fma(-cp, phi, dp); }
     __device__ __forceinline__ static R abs2(V v) { return v * v; }
     __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
@@ -98,8 +106,9 @@ template <typename R> struct FImagCplx {
         return V{fma(k, (pm.re + p1.re) - R(2) * p0.re, p0.re),
                  fma(k, (pm.im + p1.im) - R(2) * p0.im, p0.im)};
     }
-    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ip) {
-        return V{fma(k, dprev.re, r.re) * ip, fma(k, dprev.im, r.im) * ip};
+    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ipm1) {
+        const R ure = fma(k, dprev.re, r.re), uim = fma(k, dprev.im, r.im);
+        return V{fma(ure, ipm1, ure), fma(uim, ipm1, uim)};
     }
     __device__ __forceinline__ static V back(V dp, C cp, V phi) {
         return V{fma(-cp, phi.re, dp.re), fma(-cp, phi.im, dp.im)};
@@ -123,11 +132,11 @@ template <typename R> struct FRealTime {
         R dim = (pm.im + p1.im) - R(2) * p0.im;
         return V{fma(-k, dim, p0.re), fma(k, dre, p0.im)};
     }
-    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ip) {
-        // (r + i k dprev) * ip
-        R ure = fma(-k, dprev.im, r.re);
-        R uim = fma(k, dprev.re, r.im);
-        return V{fma(ure, ip.re, -uim * ip.im), fma(ure, ip.im, uim * ip.re)};
+    __device__ __forceinline__ static V fwd(V r, V dprev, R k, C ipm1) {
+        // u = r + i k dprev;  u ip = u + u (ip - 1)
+        const R ure = fma(-k, dprev.im, r.re);
+        const R uim = fma(k, dprev.re, r.im);
+        return V{fma(ure, ipm1.re, fma(-uim, ipm1.im, ure)), fma(ure, ipm1.im, fma(uim, ipm1.re, uim))};
     }
     __device__ __forceinline__ static V back(V dp, C cp, V phi) {
         // dp - cp * phi
@@ -195,40 +204,44 @@ __device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a) {
 }
 
 // ------------------------------------------------------------------ one line
-// Solves one line starting at `line` (element stride `st`).  Load / store
-// functors hide the kick (x sweep) and the norm accumulation (z sweep).
-template <class F, typename R, int B, int W, class LoadF, class PutF>
+// Outputs per chunk of the windowed solve: 16, or 8 for 16-byte elements
+// (complex FP64) to bound the register ring.
+template <typename V> __host__ __device__ constexpr int chunk_len() { return sizeof(V) >= 16 ? 8 : 16; }
+
+// Windowed Thomas solve of one line of n interior unknowns.  `io` supplies
+// single values (load1 / put1, interior index t -> node t+1) and chunks of
+// B consecutive values (chunk_load then chunk_val(q); chunk_put(q) then
+// chunk_store), so that the contiguous axis can stage chunks through shared
+// memory.
+template <class F, typename R, int B, int W, class IO>
 __device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename F::C *__restrict__ cp,
-                                                    const typename F::C *__restrict__ ip,
-                                                    LoadF load, PutF put) {
+                                                    const typename F::C *__restrict__ ipm1, IO &io) {
     using V = typename F::V;
     V D[B + W];
     V pm = F::zero();
-    V p0 = load(0);
-    V p1 = load(1);
+    V p0 = io.load1(0);
+    V p1 = io.load1(1);
     V dprev = F::zero();
 #pragma unroll
     for (int q = 0; q < W; ++q) {
         if (q < n) {
-            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + q));
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + q));
             D[q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = load(q + 2);
+            p1 = io.load1(q + 2);
         }
     }
     int t0 = 0;
     for (; t0 + B + W <= n; t0 += B) {
-        V P[B];
-#pragma unroll
-        for (int q = 0; q < B; ++q) P[q] = load(t0 + W + q + 2);
+        io.chunk_load(t0 + W + 2);
 #pragma unroll
         for (int q = 0; q < B; ++q) {
-            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + t0 + W + q));
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + W + q));
             D[W + q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = P[q];
+            p1 = io.chunk_val(q);
         }
         V phi = D[B + W - 1];
 #pragma unroll
@@ -236,8 +249,9 @@ __device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename
 #pragma unroll
         for (int q = B - 1; q >= 0; --q) {
             phi = F::back(D[q], ldc(cp + t0 + q), phi);
-            put(t0 + q, phi);
+            io.chunk_put(t0, q, phi);
         }
+        io.chunk_store(t0);
 #pragma unroll
         for (int q = 0; q < W; ++q) D[q] = D[B + q];
     }
@@ -245,11 +259,11 @@ __device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename
 #pragma unroll
     for (int q = W; q < B + W; ++q) {
         if (q < rem) {
-            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + t0 + q));
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + q));
             D[q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = load(t0 + q + 2);
+            p1 = io.load1(t0 + q + 2);
         }
     }
     V phi = F::zero();
@@ -257,46 +271,75 @@ __device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename
     for (int q = B + W - 1; q >= 0; --q) {
         if (q < rem) {
             phi = F::back(D[q], ldc(cp + t0 + q), (q == rem - 1) ? F::zero() : phi);
-            put(t0 + q, phi);
+            io.put1(t0 + q, phi);
         }
     }
 }
 
 // Exact two-pass Thomas: dp is staged in psi (node t+1 <- dp[t] once psi[t]
 // has been consumed) and read back by the backward sweep.
-template <class F, typename R, class LoadF, class PutF>
+template <class F, typename R, class IO>
 __device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F::C *__restrict__ cp,
-                                                 const typename F::C *__restrict__ ip,
-                                                 typename F::V *line, long long st, LoadF load,
-                                                 PutF put) {
+                                                 const typename F::C *__restrict__ ipm1, IO &io) {
     using V = typename F::V;
     V pm = F::zero();
-    V p0 = load(0);
-    V p1 = load(1);
+    V p0 = io.load1(0);
+    V p1 = io.load1(1);
     V dprev = F::zero();
     for (int t = 0; t < n; ++t) {
-        dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ip + t));
+        dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t));
         pm = p0;
         p0 = p1;
-        p1 = load(t + 2);
-        if (t < n - 1) line[(long long)(t + 1) * st] = dprev;
+        p1 = io.load1(t + 2);
+        if (t < n - 1) io.stage(t, dprev);
     }
     V phi = dprev;
-    put(n - 1, phi);
+    io.put1(n - 1, phi);
     for (int t = n - 2; t >= 0; --t) {
-        phi = F::back(line[(long long)(t + 1) * st], ldc(cp + t), phi);
-        put(t, phi);
+        phi = F::back(io.unstage(t), ldc(cp + t), phi);
+        io.put1(t, phi);
     }
 }
 
-// Outputs per chunk of the windowed solve: 16, or 8 for 16-byte elements
-// (complex FP64) to bound the register ring.
-template <typename V> __host__ __device__ constexpr int chunk_len() { return sizeof(V) >= 16 ? 8 : 16; }
+// ------------------------------------------------------------------ per-thread line access
+// One thread owns one line (element stride st).  The x sweep applies the
+// kick to every value it loads; the z sweep adds |phi|^2 of every value it
+// stores to the thread's norm sum.
+template <class F, typename R, int KIND> struct LineIO {
+    using V = typename F::V;
+    V *line;
+    long long st;
+    int n;
+    R s, dt, g, hx, x0, dx, vyz;
+    Acc<R> *acc;
+    __device__ __forceinline__ V load1(int t) const {
+        if (t >= n) return F::zero();
+        V v = line[(long long)(t + 1) * st];
+        if (KIND == K_X) {
+            const R x = fma((R)(t + 1), dx, x0);
+            v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
+        }
+        return v;
+    }
+    __device__ __forceinline__ void put1(int t, V v) const {
+        line[(long long)(t + 1) * st] = v;
+        if (KIND == K_Z) acc->add(F::abs2(v));
+    }
+    V P[chunk_len<V>()];  // prefetched chunk (all loads issued before use)
+    __device__ __forceinline__ void chunk_load(int tf) {
+#pragma unroll
+        for (int q = 0; q < chunk_len<V>(); ++q) P[q] = load1(tf + q);
+    }
+    __device__ __forceinline__ V chunk_val(int q) const { return P[q]; }
+    __device__ __forceinline__ void chunk_put(int tf, int q, V v) const { put1(tf + q, v); }
+    __device__ __forceinline__ void chunk_store(int) const {}
+    __device__ __forceinline__ void stage(int t, V v) const { line[(long long)(t + 1) * st] = v; }
+    __device__ __forceinline__ V unstage(int t) const { return line[(long long)(t + 1) * st]; }
+};
 
-// ------------------------------------------------------------------ kernel
 // One thread per line; consecutive threads own lines that are adjacent in
 // memory (consecutive z for the x and y sweeps), so every row of a warp's
-// lines is one coalesced access.
+// lines is one coalesced access.  Window 0 selects the exact two-pass form.
 template <class F, typename R, int W, int KIND>
 __global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
     using V = typename F::V;
@@ -304,46 +347,121 @@ __global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
     const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     Acc<R> acc;
     if (L < a.n_lines) {
-        V *line = static_cast<V *>(a.psi) + (L / a.inner) * a.outer_stride + (L % a.inner);
-        const long long st = a.stride;
-        const int n = a.N - 2;
-        const C *cp = static_cast<const C *>(a.cp);
-        const C *ip = static_cast<const C *>(a.ip);
-        const R kap = (R)a.kappa;
-        R s = R(1), dt = R(0), g = R(0), hx = R(0), x0 = R(0), dx = R(0), vyz = R(0);
+        LineIO<F, R, KIND> io;
+        io.line = static_cast<V *>(a.psi) + (L / a.inner) * a.outer_stride + (L % a.inner);
+        io.st = a.stride;
+        io.n = a.N - 2;
+        io.acc = &acc;
+        io.s = R(1);
+        io.dt = io.g = io.hx = io.x0 = io.dx = io.vyz = R(0);
         if (KIND == K_X) {
-            s = (R)__ldg(a.scale);
-            dt = (R)a.dt;
-            g = (R)a.g;
+            io.s = (R)__ldg(a.scale);
+            io.dt = (R)a.dt;
+            io.g = (R)a.g;
             const int j = (int)(L / a.nz), k = (int)(L % a.nz);
             const double y = a.origin[1] + j * a.d[1];
             const double z = a.origin[2] + k * a.d[2];
-            vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
-            hx = (R)a.half_w2[0];
-            x0 = (R)a.origin[0];
-            dx = (R)a.d[0];
+            io.vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
+            io.hx = (R)a.half_w2[0];
+            io.x0 = (R)a.origin[0];
+            io.dx = (R)a.d[0];
         }
-        auto load = [&](int t) -> V {
-            if (t >= n) return F::zero();
-            V v = line[(long long)(t + 1) * st];
-            if (KIND == K_X) {
-                const R x = fma((R)(t + 1), dx, x0);
-                v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
-            }
-            return v;
-        };
-        auto put = [&](int t, V v) {
-            line[(long long)(t + 1) * st] = v;
-            if (KIND == K_Z) acc.add(F::abs2(v));
-        };
-        line[0] = F::zero();
-        line[(long long)(a.N - 1) * st] = F::zero();
+        const C *cp = static_cast<const C *>(a.cp);
+        const C *ipm1 = static_cast<const C *>(a.ip);
+        io.line[0] = F::zero();
+        io.line[(long long)(a.N - 1) * io.st] = F::zero();
         if constexpr (W > 0)
-            solve_line_windowed<F, R, chunk_len<V>(), W>(n, kap, cp, ip, load, put);
+            solve_line_windowed<F, R, chunk_len<V>(), W>(io.n, (R)a.kappa, cp, ipm1, io);
         else
-            solve_line_exact<F, R>(n, kap, cp, ip, line, st, load, put);
+            solve_line_exact<F, R>(io.n, (R)a.kappa, cp, ipm1, io);
     }
     if (KIND == K_Z) norm_finalize(acc.value(), a);
+}
+
+// ------------------------------------------------------------------ contiguous axis
+// A warp owns 32 consecutive stride-1 lines (one contiguous block of
+// 32 * N elements).  Chunks of B values per line are moved between global
+// and shared memory cooperatively -- each instruction covers 32/B lines x B
+// consecutive elements -- and transposed through a padded tile so that lane
+// l then reads / writes row l with no bank conflicts.  Single values of the
+// first and last chunk use direct loads and stores.
+constexpr int kTileWarps = 4;
+
+template <class F, typename R, int B> struct TileIO {
+    using V = typename F::V;
+    static constexpr int LD = B + 1;   // padded row
+    static constexpr int LPI = 32 / B; // lines per cooperative instruction
+    V *base0;                          // node 0 of the warp's first line
+    V *tile;                           // 32 x LD values of this warp
+    int N, n, lane, nvalid;
+    Acc<R> *acc;
+    __device__ __forceinline__ V load1(int t) const {
+        if (t >= n || lane >= nvalid) return F::zero();
+        return base0[(long long)lane * N + t + 1];
+    }
+    __device__ __forceinline__ void put1(int t, V v) const {
+        if (lane < nvalid) {
+            base0[(long long)lane * N + t + 1] = v;
+            acc->add(F::abs2(v));
+        }
+    }
+    // Cooperative load of interior values tf..tf+B-1 of the warp's 32 lines
+    // (values past the last interior node read as 0); lane l then reads row l.
+    __device__ __forceinline__ void chunk_load(int tf) const {
+        __syncwarp();
+#pragma unroll 4
+        for (int it = 0; it < B; ++it) {
+            const int q = it * LPI + lane / B, e = lane % B;
+            const int node = tf + 1 + e;
+            V v = F::zero();
+            if (q < nvalid && node <= N - 2) v = base0[(long long)q * N + node];
+            tile[q * LD + e] = v;
+        }
+        __syncwarp();
+    }
+    __device__ __forceinline__ V chunk_val(int q) const { return tile[lane * LD + q]; }
+    // Lane l writes row l (its inputs there are consumed); chunk_store then
+    // writes the 32 x B outputs back cooperatively.
+    __device__ __forceinline__ void chunk_put(int, int q, V v) const {
+        tile[lane * LD + q] = v;
+        if (lane < nvalid) acc->add(F::abs2(v));
+    }
+    __device__ __forceinline__ void chunk_store(int tf) const {
+        __syncwarp();
+#pragma unroll 4
+        for (int it = 0; it < B; ++it) {
+            const int q = it * LPI + lane / B, e = lane % B;
+            if (q < nvalid) base0[(long long)q * N + tf + 1 + e] = tile[q * LD + e];
+        }
+    }
+};
+
+template <class F, typename R, int W>
+__global__ void __launch_bounds__(kTileWarps * 32) sweep_contig_kernel(SweepArgs a) {
+    using V = typename F::V;
+    using C = typename F::C;
+    constexpr int B = chunk_len<V>();
+    __shared__ V tiles[kTileWarps][32 * (B + 1)];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long L0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+    Acc<R> acc;
+    if (L0 < a.n_lines) {
+        TileIO<F, R, B> io;
+        io.base0 = static_cast<V *>(a.psi) + L0 * a.N;
+        io.tile = tiles[warp];
+        io.N = a.N;
+        io.n = a.N - 2;
+        io.lane = lane;
+        io.nvalid = (int)min(32LL, a.n_lines - L0);
+        io.acc = &acc;
+        if (lane < io.nvalid) {
+            io.base0[(long long)lane * a.N] = F::zero();
+            io.base0[(long long)lane * a.N + a.N - 1] = F::zero();
+        }
+        solve_line_windowed<F, R, B, W>(io.n, (R)a.kappa, static_cast<const C *>(a.cp),
+                                        static_cast<const C *>(a.ip), io);
+    }
+    norm_finalize(acc.value(), a);
 }
 
 }  // namespace gpcn

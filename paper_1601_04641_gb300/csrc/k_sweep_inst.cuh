@@ -6,8 +6,23 @@
 
 namespace gpcn {
 
+template <class F, typename R>
+static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    const unsigned threads = (unsigned)L.threads;
+    if (threads % 32 || threads > 32 * kTileWarps) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((a.n_lines + threads - 1) / threads);
+    switch (L.window) {
+    case 4: sweep_contig_kernel<F, R, 4><<<blocks, threads, 0, s>>>(a); break;
+    case 8: sweep_contig_kernel<F, R, 8><<<blocks, threads, 0, s>>>(a); break;
+    case 16: sweep_contig_kernel<F, R, 16><<<blocks, threads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <class F, typename R, int KIND>
 static cudaError_t launch_kind(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    if (KIND == K_Z && L.contiguous) return launch_contig<F, R>(L, a, s);
     const unsigned threads = (unsigned)L.threads;
     const unsigned blocks = (unsigned)((a.n_lines + threads - 1) / threads);
     switch (L.window) {
