@@ -40,10 +40,13 @@
  *  - Work is queued on the handle's CUDA stream.  Calls that return values
  *    to the host (gp_observables, gp_get_psi to host memory,
  *    gp_run_imag_until) synchronise that stream; the step calls do not.
- *  - The library owns psi unless it was created with gp_create_ext, in
- *    which case the caller owns the device buffer and must keep it alive
- *    until gp_destroy.  All other device buffers (CN coefficient tables,
- *    reduction partials, scalars) are owned by the handle.
+ *  - Line solves are out of place: the handle keeps psi in two device
+ *    buffers and each sweep reads one and writes the other.  The first
+ *    buffer is the caller's when the handle was made by gp_create_ext (the
+ *    caller keeps it alive until gp_destroy); the second, and every other
+ *    device buffer (CN coefficient tables, reduction partials, scalars),
+ *    is owned by the handle.  gp_get_psi / gp_psi_device_ptr give the
+ *    current psi whichever buffer holds it.
  *  - A handle is not thread-safe: calls on one handle must not overlap.
  */
 #ifndef GPCN_GP_H
@@ -186,6 +189,21 @@ gp_status gp_set_window(gp_handle h, int window);
 /* Threads per block of the line-solve kernel of one axis (multiple of 32,
  * 32..256). */
 gp_status gp_set_threads(gp_handle h, int axis, int threads);
+
+/* Interior nodes per segment of the line solves of one axis (0 = the
+ * automatic choice).  Lines are cut into segments, one thread each, that
+ * warm their forward sweep up over the W+1 nodes before the segment. */
+gp_status gp_set_segments(gp_handle h, int axis, int seg_len);
+
+/* Segment length and count per axis that the next imaginary- (mode 0) or
+ * real-time (mode 1) step will use. */
+gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]);
+
+/* Device pointer of the buffer that holds the current psi, and whether a
+ * renormalisation factor is still pending on it (the value is then psi
+ * times that factor; gp_get_psi applies it).  Valid until the next call
+ * that queues work on the handle. */
+gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale);
 
 /* Last error message for this handle (or for the calling thread's last
  * failed create when h is NULL).  Never NULL. */

@@ -58,6 +58,9 @@ SIGNATURES = {
     "gp_get_window": (_i, [Handle, _i, ctypes.POINTER(_i)]),
     "gp_set_window": (_i, [Handle, _i]),
     "gp_set_threads": (_i, [Handle, _i, _i]),
+    "gp_set_segments": (_i, [Handle, _i, _i]),
+    "gp_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "gp_psi_device_ptr": (_i, [Handle, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
     "gp_last_error": (ctypes.c_char_p, [Handle]),
     "gp_version": (ctypes.c_char_p, []),
 }

@@ -65,8 +65,9 @@ struct gp_handle_s {
     gp_precision prec = GP_F64;
     gp_field field = GP_COMPLEX;
     size_t elem = 0, sites = 0, bytes = 0;
-    void *psi = nullptr;
-    bool own_psi = false;
+    void *buf[2] = {nullptr, nullptr};  // ping-pong psi buffers (sweeps are out of place)
+    int cur = 0;                        // buf[cur] holds the current psi
+    bool own_buf0 = false;
     cudaStream_t stream = nullptr;
     char *d_coef = nullptr;
     size_t coef_bytes = 0;
@@ -82,6 +83,7 @@ struct gp_handle_s {
     double t = 0;
     int threads[3] = {128, 128, 128};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
+    int seg_override[3] = {0, 0, 0};  // interior nodes per segment, 0 = automatic
     // observables history queued during stepping
     int track_every = 0, track_cap = 0, track_count = 0;
     double *d_track = nullptr;
@@ -247,7 +249,7 @@ size_t blocks_for(long long items, int threads) { return (size_t)((items + threa
 FieldArgs field_args(gp_handle h) {
     FieldArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.psi = h->psi;
+    a.psi = h->buf[h->cur];
     for (int ax = 0; ax < 3; ++ax) {
         a.n[ax] = h->n[ax];
         a.d[ax] = h->d[ax];
@@ -270,8 +272,9 @@ FieldArgs field_args(gp_handle h) {
 constexpr int kNormBlocks = 152 * 4;
 
 gp_status alloc_scratch(gp_handle h) {
+    // z sweep: at most one block per 32 (line, segment) threads, segments of >= 1 node
     size_t cap = kNormBlocks;
-    cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32));  // z sweep at >= 32 threads/block
+    cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32) * (size_t)(h->n[2] - 2));
     FieldArgs fa = field_args(h);
     cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
     if (cudaMalloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
@@ -293,7 +296,8 @@ void release(gp_handle h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->own_psi && h->psi) cudaFree(h->psi);
+    if (h->own_buf0 && h->buf[0]) cudaFree(h->buf[0]);
+    if (h->buf[1]) cudaFree(h->buf[1]);
     cudaFree(h->d_coef);
     cudaFree(h->d_scal);
     cudaFree(h->d_obs);
@@ -340,20 +344,25 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
             delete h;
             return fail(nullptr, GP_ERR_ARG, "dev_psi too small or not 16-byte aligned");
         }
-        h->psi = dev_psi;
-        h->own_psi = false;
+        h->buf[0] = dev_psi;
+        h->own_buf0 = false;
     } else {
-        if (cudaMalloc(&h->psi, h->bytes) != cudaSuccess) {
+        if (cudaMalloc(&h->buf[0], h->bytes) != cudaSuccess) {
             cudaGetLastError();
             delete h;
             return fail(nullptr, GP_ERR_NOMEM, "cudaMalloc of psi failed");
         }
-        h->own_psi = true;
-        if (cudaMemsetAsync(h->psi, 0, h->bytes, h->stream) != cudaSuccess) {
+        h->own_buf0 = true;
+        if (cudaMemsetAsync(h->buf[0], 0, h->bytes, h->stream) != cudaSuccess) {
             cudaGetLastError();
             release(h);
             return fail(nullptr, GP_ERR_CUDA, "cudaMemsetAsync of psi failed");
         }
+    }
+    if (cudaMalloc(&h->buf[1], h->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        release(h);
+        return fail(nullptr, GP_ERR_NOMEM, "cudaMalloc of the second psi buffer failed");
     }
     st = alloc_scratch(h);
     if (st == GP_OK) st = build_coefficients(h);
@@ -377,6 +386,30 @@ gp_status enter(gp_handle h) {
 
 gp_status queue_observables(gp_handle h, double *dst);
 
+// Segments of one axis: enough (line, segment) threads to fill the GPU a
+// few times over, each segment a whole number of chunks.  The exact form
+// (window 0) solves whole lines.
+void segments(gp_handle h, int ax, int window, long long lines, int *seg_len, int *n_seg) {
+    const int n = h->n[ax] - 2;
+    const int chunk = (h->prec == GP_F64 && h->field == GP_COMPLEX) ? 8 : 16;
+    int len = n;
+    if (window > 0) {
+        if (h->seg_override[ax] > 0) {
+            len = std::min(n, h->seg_override[ax]);
+        } else {
+            const long long target = 152LL * 768 * 4;  // ~4 waves of resident threads
+            long long want = (target + lines - 1) / lines;
+            const long long most = std::max(1, n / (4 * chunk));
+            want = std::max(1LL, std::min(want, most));
+            len = (int)((n + want - 1) / want);
+            len = (len + chunk - 1) / chunk * chunk;
+            len = std::min(len, n);
+        }
+    }
+    *seg_len = std::max(1, len);
+    *n_seg = (n + *seg_len - 1) / *seg_len;
+}
+
 // One stage of a step: 0 = kick + x sweep, 1 = y sweep, 2 = z sweep + norm.
 gp_status run_stage(gp_handle h, int stage, bool realtime) {
     SweepLaunch L;
@@ -393,7 +426,8 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     SweepArgs a;
     std::memset(&a, 0, sizeof(a));
     const long long nx = h->n[0], ny = h->n[1], nz = h->n[2];
-    a.psi = h->psi;
+    a.psi = h->buf[h->cur];
+    a.psi_out = h->buf[h->cur ^ 1];
     a.cp = h->d_coef + cs.off_cp;
     a.ip = h->d_coef + cs.off_ip;
     a.n_lines = sweep_lines(h, ax);
@@ -411,6 +445,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
         a.stride = 1;
     }
     a.N = h->n[ax];
+    segments(h, ax, L.window, a.n_lines, &a.seg_len, &a.n_seg);
     a.kappa = h->dt / (4.0 * h->d[ax] * h->d[ax]);
     a.scale = h->d_scal + (h->scale_pending ? S_SCALE : S_ONE);
     a.dt = h->dt;
@@ -428,9 +463,11 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     a.scale_out = h->d_scal + S_SCALE;
     a.dV = h->d[0] * h->d[1] * h->d[2];
     a.want_scale = realtime ? 0 : 1;
-    if (stage == 2 && blocks_for(a.n_lines, L.threads) > h->partial_cap)
+    const int zthreads = L.contiguous ? 32 * 4 : L.threads;
+    if (stage == 2 && blocks_for(a.n_lines, zthreads) * (size_t)a.n_seg > h->partial_cap)
         return fail(h, GP_ERR_STATE, "z sweep grid exceeds the partials buffer");
     GP_CK(h, launch_sweep(L, a, h->stream));
+    h->cur ^= 1;
     if (stage == 0) h->scale_pending = false;
     if (stage == 2 && !realtime) h->scale_pending = true;
     return GP_OK;
@@ -528,7 +565,7 @@ gp_status gp_set_psi(gp_handle h, const void *psi, int on_device) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
-    GP_CK(h, cudaMemcpyAsync(h->psi, psi, h->bytes,
+    GP_CK(h, cudaMemcpyAsync(h->buf[h->cur], psi, h->bytes,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              h->stream));
     if (!on_device) GP_CK(h, cudaStreamSynchronize(h->stream));
@@ -550,10 +587,10 @@ gp_status gp_get_psi(gp_handle h, void *psi, int on_device) {
         return GP_OK;
     }
     if (h->scale_pending) {  // fold the pending factor into psi (same rounding as the next kick)
-        GP_CK(h, launch_apply_scale(p, cplx, a, h->psi, h->stream));
+        GP_CK(h, launch_apply_scale(p, cplx, a, h->buf[h->cur], h->stream));
         h->scale_pending = false;
     }
-    GP_CK(h, cudaMemcpyAsync(psi, h->psi, h->bytes, cudaMemcpyDeviceToHost, h->stream));
+    GP_CK(h, cudaMemcpyAsync(psi, h->buf[h->cur], h->bytes, cudaMemcpyDeviceToHost, h->stream));
     GP_CK(h, cudaStreamSynchronize(h->stream));
     return GP_OK;
 }
@@ -721,6 +758,28 @@ gp_status gp_set_threads(gp_handle h, int axis, int threads) {
     if (threads < 32 || threads > 256 || threads % 32)
         return fail(h, GP_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
     h->threads[axis] = threads;
+    return GP_OK;
+}
+
+gp_status gp_set_segments(gp_handle h, int axis, int seg_len) {
+    if (!h || axis < 0 || axis > 2) return fail(h, GP_ERR_ARG, "bad axis");
+    if (seg_len < 0) return fail(h, GP_ERR_ARG, "seg_len must be >= 0");
+    h->seg_override[axis] = seg_len;
+    return GP_OK;
+}
+
+gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]) {
+    if (!h || !seg_len || !n_seg || mode < 0 || mode > 1) return fail(h, GP_ERR_ARG, "bad arguments");
+    if (mode >= modes_of(h)) return fail(h, GP_ERR_STATE, "no real-time tables on a GP_REAL field");
+    for (int ax = 0; ax < 3; ++ax)
+        segments(h, ax, h->coef[mode][ax].window, sweep_lines(h, ax), &seg_len[ax], &n_seg[ax]);
+    return GP_OK;
+}
+
+gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
+    if (!h || !ptr) return fail(h, GP_ERR_ARG, "bad arguments");
+    *ptr = h->buf[h->cur];
+    if (pending_scale) *pending_scale = h->scale_pending ? 1 : 0;
     return GP_OK;
 }
 

@@ -21,7 +21,8 @@ enum Kind { K_X = 0, K_Y = 1, K_Z = 2 };
 
 // Arguments of one line-solve launch (all lines of one axis).
 struct SweepArgs {
-    void *psi;             // element array, layout z-fastest
+    const void *psi;       // input element array, layout z-fastest
+    void *psi_out;         // output array (a different buffer: sweeps are out of place)
     const void *cp;        // Thomas multipliers cp[t], t = 0..N-3 (real or complex)
     const void *ip;        // inverse pivots ip[t]
     long long n_lines;     // lines of this axis
@@ -29,6 +30,8 @@ struct SweepArgs {
     long long outer_stride;
     long long stride;      // element stride along the line
     int N;                 // nodes along the line (interior N - 2)
+    int seg_len;           // interior nodes per segment (a multiple of the chunk length)
+    int n_seg;             // segments per line (grid.y); one thread per (line, segment)
     double kappa;          // |c| = dt / (4 d^2)
     // kick (K_X): site (i, j, k) with i along the line, (j, k) = (L / nz, L % nz)
     const double *scale;   // pending renormalisation factor applied on load
@@ -44,7 +47,6 @@ struct SweepArgs {
     double *scale_out;     // 1 / sqrt(norm) when want_scale
     double dV;
     int want_scale;
-    // exact two-pass solve scratch flag (window 0): dp is staged in psi itself
 };
 
 struct SweepLaunch {

@@ -14,16 +14,25 @@
 // every step, and in real time that is a steady norm drift (about 3e-8 per
 // FP32 sweep); stored as a deviation its rounding error is ~|2c| smaller.
 //
-// One thread owns one line and streams it once from HBM: the forward sweep
-// is exact; the backward sweep is windowed.  dp values are kept in a
-// register ring of B + W entries.  After dp[t0 .. t0+B+W-1] are known, the
-// chunk phi[t0 .. t0+B-1] is recovered by starting the backward recurrence
-// at t0+B+W-1 with phi ~ dp (dropping cp * phi[t0+B+W]) and running it down
-// to t0.  The dropped term reaches phi[t0+B-1] multiplied by W+1 factors
-// |cp| < 1, so the chunk is exact to |cp|_max^(W+1) * max|phi|; the host
-// picks W so that this is below an eighth of the unit roundoff (or uses the
-// exact two-pass form, window 0, which stages dp in psi and reads it back).
-// The last chunk of a line is solved exactly from phi[n-1] = dp[n-1].
+// Every value is read once from one buffer and written once to the other
+// (sweeps are out of place, ping-ponging between two arrays).  A line is cut
+// into segments of seg_len interior nodes, one thread per (line, segment),
+// which gives the GPU enough independent sequential recurrences to cover
+// memory latency.  Both recurrences contract: an error in dp[t-1] reaches
+// dp[t] multiplied by c ip[t] = -cp[t], and an error in phi[t+1] reaches
+// phi[t] multiplied by -cp[t], with |cp| < 1.  So
+//  - a segment starting at t_b runs the forward sweep from t_b - (W+1) with
+//    dp = 0 there (the line start needs no warm-up): the error at t_b is at
+//    most |cp|_max^(W+2) * max|dp|;
+//  - the backward sweep is windowed: dp values sit in a register ring of
+//    B + W entries, and once dp[t0 .. t0+B+W-1] are known the chunk
+//    phi[t0 .. t0+B-1] is recovered by starting the backward recurrence at
+//    t0+B+W-1 with phi ~ dp (dropping cp * phi[t0+B+W]); the dropped term
+//    reaches phi[t0+B-1] through W+1 factors, i.e. |cp|_max^(W+1) max|phi|.
+// The host picks W so that |cp|_max^(W+1) is below an eighth of the unit
+// roundoff, or uses the exact two-pass form (window 0, one segment), which
+// stages dp in the output and reads it back.  The last chunk of a line is
+// solved exactly from phi[n-1] = dp[n-1].
 //
 // The x sweep carries the fused potential-plus-nonlinear kick (calcnu),
 // applied to each value as it is loaded, together with the pending
@@ -183,17 +192,18 @@ __device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a) {
     __shared__ double red[32];
     __shared__ int is_last;
     double bsum = block_sum(v, red);
+    const unsigned nblocks = gridDim.x * gridDim.y;
     if (threadIdx.x == 0) {
-        a.partials[blockIdx.x] = bsum;
+        a.partials[blockIdx.y * gridDim.x + blockIdx.x] = bsum;
         __threadfence();
         unsigned prev = atomicAdd(a.counter, 1u);
-        is_last = (prev == gridDim.x - 1);
+        is_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(a.partials + b);
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) s += __ldcg(a.partials + b);
     double total = block_sum(s, red);
     if (threadIdx.x == 0) {
         double nrm = a.dV * total;
@@ -203,37 +213,51 @@ __device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a) {
     }
 }
 
-// ------------------------------------------------------------------ one line
+// ------------------------------------------------------------------ one segment
 // Outputs per chunk of the windowed solve: 16, or 8 for 16-byte elements
 // (complex FP64) to bound the register ring.
 template <typename V> __host__ __device__ constexpr int chunk_len() { return sizeof(V) >= 16 ? 8 : 16; }
 
-// Windowed Thomas solve of one line of n interior unknowns.  `io` supplies
-// single values (load1 / put1, interior index t -> node t+1) and chunks of
-// B consecutive values (chunk_load then chunk_val(q); chunk_put(q) then
-// chunk_store), so that the contiguous axis can stage chunks through shared
-// memory.
+// Windowed Thomas solve of the interior nodes [tb, te) of a line of n
+// interior unknowns.  `io` supplies single values (load1 / put1, interior
+// index t -> node t+1, loads past the line end read 0) and chunks of B
+// consecutive values (chunk_load then chunk_val(q); chunk_put(q) then
+// chunk_store), so that the contiguous axis can stage chunks through
+// shared memory.  te - tb is a multiple of B unless te == n.
 template <class F, typename R, int B, int W, class IO>
-__device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename F::C *__restrict__ cp,
-                                                    const typename F::C *__restrict__ ipm1, IO &io) {
+__device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
+                                              const typename F::C *__restrict__ cp,
+                                              const typename F::C *__restrict__ ipm1, IO &io) {
     using V = typename F::V;
-    V D[B + W];
-    V pm = F::zero();
-    V p0 = io.load1(0);
-    V p1 = io.load1(1);
+    // forward warm-up from dp = 0 at tw (exact when tw == 0)
+    const int tw = tb > W + 1 ? tb - (W + 1) : 0;
+    V pm = tw > 0 ? io.load1(tw - 1) : F::zero();
+    V p0 = io.load1(tw);
+    V p1 = io.load1(tw + 1);
     V dprev = F::zero();
+    for (int t = tw; t < tb; ++t) {
+        dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t));
+        pm = p0;
+        p0 = p1;
+        p1 = io.load1(t + 2);
+    }
+    // the segment behaves as a line ending at e: W look-ahead values beyond
+    // te start the windowed backward sweep of its last chunk
+    const int e = min(te + W, n);
+    const int m = e - tb;
+    V D[B + W];
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-        if (q < n) {
-            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + q));
+        if (q < m) {
+            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + tb + q));
             D[q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = io.load1(q + 2);
+            p1 = io.load1(tb + q + 2);
         }
     }
-    int t0 = 0;
-    for (; t0 + B + W <= n; t0 += B) {
+    int t0 = tb;
+    for (; t0 + B + W <= e; t0 += B) {
         io.chunk_load(t0 + W + 2);
 #pragma unroll
         for (int q = 0; q < B; ++q) {
@@ -255,7 +279,7 @@ __device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename
 #pragma unroll
         for (int q = 0; q < W; ++q) D[q] = D[B + q];
     }
-    const int rem = n - t0;  // 0 <= rem < B + W: finish exactly
+    const int rem = e - t0;  // 0 <= rem < B + W: finish from dp[e-1]
 #pragma unroll
     for (int q = W; q < B + W; ++q) {
         if (q < rem) {
@@ -271,13 +295,13 @@ __device__ __forceinline__ void solve_line_windowed(int n, R kap, const typename
     for (int q = B + W - 1; q >= 0; --q) {
         if (q < rem) {
             phi = F::back(D[q], ldc(cp + t0 + q), (q == rem - 1) ? F::zero() : phi);
-            io.put1(t0 + q, phi);
+            if (t0 + q < te) io.put1(t0 + q, phi);
         }
     }
 }
 
-// Exact two-pass Thomas: dp is staged in psi (node t+1 <- dp[t] once psi[t]
-// has been consumed) and read back by the backward sweep.
+// Exact two-pass Thomas over a whole line: dp is staged in the output and
+// read back by the backward sweep.
 template <class F, typename R, class IO>
 __device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F::C *__restrict__ cp,
                                                  const typename F::C *__restrict__ ipm1, IO &io) {
@@ -302,19 +326,20 @@ __device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F:
 }
 
 // ------------------------------------------------------------------ per-thread line access
-// One thread owns one line (element stride st).  The x sweep applies the
-// kick to every value it loads; the z sweep adds |phi|^2 of every value it
-// stores to the thread's norm sum.
+// One thread owns one segment of one line (element stride st).  The x sweep
+// applies the kick to every value it loads; the z sweep adds |phi|^2 of
+// every value it stores to the thread's norm sum.
 template <class F, typename R, int KIND> struct LineIO {
     using V = typename F::V;
-    V *line;
+    const V *in;
+    V *out;
     long long st;
     int n;
     R s, dt, g, hx, x0, dx, vyz;
     Acc<R> *acc;
     __device__ __forceinline__ V load1(int t) const {
         if (t >= n) return F::zero();
-        V v = line[(long long)(t + 1) * st];
+        V v = in[(long long)(t + 1) * st];
         if (KIND == K_X) {
             const R x = fma((R)(t + 1), dx, x0);
             v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
@@ -322,7 +347,7 @@ template <class F, typename R, int KIND> struct LineIO {
         return v;
     }
     __device__ __forceinline__ void put1(int t, V v) const {
-        line[(long long)(t + 1) * st] = v;
+        out[(long long)(t + 1) * st] = v;
         if (KIND == K_Z) acc->add(F::abs2(v));
     }
     V P[chunk_len<V>()];  // prefetched chunk (all loads issued before use)
@@ -333,13 +358,14 @@ template <class F, typename R, int KIND> struct LineIO {
     __device__ __forceinline__ V chunk_val(int q) const { return P[q]; }
     __device__ __forceinline__ void chunk_put(int tf, int q, V v) const { put1(tf + q, v); }
     __device__ __forceinline__ void chunk_store(int) const {}
-    __device__ __forceinline__ void stage(int t, V v) const { line[(long long)(t + 1) * st] = v; }
-    __device__ __forceinline__ V unstage(int t) const { return line[(long long)(t + 1) * st]; }
+    __device__ __forceinline__ void stage(int t, V v) const { out[(long long)(t + 1) * st] = v; }
+    __device__ __forceinline__ V unstage(int t) const { return out[(long long)(t + 1) * st]; }
 };
 
-// One thread per line; consecutive threads own lines that are adjacent in
-// memory (consecutive z for the x and y sweeps), so every row of a warp's
-// lines is one coalesced access.  Window 0 selects the exact two-pass form.
+// One thread per (line, segment): blockIdx.y is the segment; consecutive
+// threads own lines that are adjacent in memory (consecutive z for the x
+// and y sweeps), so every row of a warp's lines is one coalesced access.
+// Window 0 selects the exact two-pass form (one segment).
 template <class F, typename R, int W, int KIND>
 __global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
     using V = typename F::V;
@@ -348,7 +374,9 @@ __global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
     Acc<R> acc;
     if (L < a.n_lines) {
         LineIO<F, R, KIND> io;
-        io.line = static_cast<V *>(a.psi) + (L / a.inner) * a.outer_stride + (L % a.inner);
+        const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
+        io.in = static_cast<const V *>(a.psi) + off;
+        io.out = static_cast<V *>(a.psi_out) + off;
         io.st = a.stride;
         io.n = a.N - 2;
         io.acc = &acc;
@@ -368,40 +396,45 @@ __global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
         }
         const C *cp = static_cast<const C *>(a.cp);
         const C *ipm1 = static_cast<const C *>(a.ip);
-        io.line[0] = F::zero();
-        io.line[(long long)(a.N - 1) * io.st] = F::zero();
-        if constexpr (W > 0)
-            solve_line_windowed<F, R, chunk_len<V>(), W>(io.n, (R)a.kappa, cp, ipm1, io);
-        else
+        const int seg = blockIdx.y;
+        if (seg == 0) io.out[0] = F::zero();
+        if (seg == a.n_seg - 1) io.out[(long long)(a.N - 1) * io.st] = F::zero();
+        if constexpr (W > 0) {
+            const int tb = seg * a.seg_len;
+            const int te = seg == a.n_seg - 1 ? io.n : tb + a.seg_len;
+            solve_segment<F, R, chunk_len<V>(), W>(io.n, tb, te, (R)a.kappa, cp, ipm1, io);
+        } else {
             solve_line_exact<F, R>(io.n, (R)a.kappa, cp, ipm1, io);
+        }
     }
     if (KIND == K_Z) norm_finalize(acc.value(), a);
 }
 
 // ------------------------------------------------------------------ contiguous axis
-// A warp owns 32 consecutive stride-1 lines (one contiguous block of
-// 32 * N elements).  Chunks of B values per line are moved between global
-// and shared memory cooperatively -- each instruction covers 32/B lines x B
-// consecutive elements -- and transposed through a padded tile so that lane
-// l then reads / writes row l with no bank conflicts.  Single values of the
-// first and last chunk use direct loads and stores.
+// A warp owns one segment of 32 consecutive stride-1 lines (one contiguous
+// block of 32 * N elements).  Chunks of B values per line are moved between
+// global and shared memory cooperatively -- each instruction covers 32/B
+// lines x B consecutive elements -- and transposed through a padded tile so
+// that lane l then reads / writes row l with no bank conflicts.  Single
+// values of the warm-up, first and last chunk use direct loads and stores.
 constexpr int kTileWarps = 4;
 
 template <class F, typename R, int B> struct TileIO {
     using V = typename F::V;
     static constexpr int LD = B + 1;   // padded row
     static constexpr int LPI = 32 / B; // lines per cooperative instruction
-    V *base0;                          // node 0 of the warp's first line
+    const V *in0;                      // node 0 of the warp's first line (input)
+    V *out0;                           // same node in the output buffer
     V *tile;                           // 32 x LD values of this warp
     int N, n, lane, nvalid;
     Acc<R> *acc;
     __device__ __forceinline__ V load1(int t) const {
         if (t >= n || lane >= nvalid) return F::zero();
-        return base0[(long long)lane * N + t + 1];
+        return in0[(long long)lane * N + t + 1];
     }
     __device__ __forceinline__ void put1(int t, V v) const {
         if (lane < nvalid) {
-            base0[(long long)lane * N + t + 1] = v;
+            out0[(long long)lane * N + t + 1] = v;
             acc->add(F::abs2(v));
         }
     }
@@ -414,7 +447,7 @@ template <class F, typename R, int B> struct TileIO {
             const int q = it * LPI + lane / B, e = lane % B;
             const int node = tf + 1 + e;
             V v = F::zero();
-            if (q < nvalid && node <= N - 2) v = base0[(long long)q * N + node];
+            if (q < nvalid && node <= N - 2) v = in0[(long long)q * N + node];
             tile[q * LD + e] = v;
         }
         __syncwarp();
@@ -431,7 +464,7 @@ template <class F, typename R, int B> struct TileIO {
 #pragma unroll 4
         for (int it = 0; it < B; ++it) {
             const int q = it * LPI + lane / B, e = lane % B;
-            if (q < nvalid) base0[(long long)q * N + tf + 1 + e] = tile[q * LD + e];
+            if (q < nvalid) out0[(long long)q * N + tf + 1 + e] = tile[q * LD + e];
         }
     }
 };
@@ -447,19 +480,23 @@ __global__ void __launch_bounds__(kTileWarps * 32) sweep_contig_kernel(SweepArgs
     Acc<R> acc;
     if (L0 < a.n_lines) {
         TileIO<F, R, B> io;
-        io.base0 = static_cast<V *>(a.psi) + L0 * a.N;
+        io.in0 = static_cast<const V *>(a.psi) + L0 * a.N;
+        io.out0 = static_cast<V *>(a.psi_out) + L0 * a.N;
         io.tile = tiles[warp];
         io.N = a.N;
         io.n = a.N - 2;
         io.lane = lane;
         io.nvalid = (int)min(32LL, a.n_lines - L0);
         io.acc = &acc;
+        const int seg = blockIdx.y;
         if (lane < io.nvalid) {
-            io.base0[(long long)lane * a.N] = F::zero();
-            io.base0[(long long)lane * a.N + a.N - 1] = F::zero();
+            if (seg == 0) io.out0[(long long)lane * a.N] = F::zero();
+            if (seg == a.n_seg - 1) io.out0[(long long)lane * a.N + a.N - 1] = F::zero();
         }
-        solve_line_windowed<F, R, B, W>(io.n, (R)a.kappa, static_cast<const C *>(a.cp),
-                                        static_cast<const C *>(a.ip), io);
+        const int tb = seg * a.seg_len;
+        const int te = seg == a.n_seg - 1 ? io.n : tb + a.seg_len;
+        solve_segment<F, R, B, W>(io.n, tb, te, (R)a.kappa, static_cast<const C *>(a.cp),
+                                  static_cast<const C *>(a.ip), io);
     }
     norm_finalize(acc.value(), a);
 }

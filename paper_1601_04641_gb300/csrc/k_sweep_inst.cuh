@@ -8,13 +8,12 @@ namespace gpcn {
 
 template <class F, typename R>
 static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
-    const unsigned threads = (unsigned)L.threads;
-    if (threads % 32 || threads > 32 * kTileWarps) return cudaErrorInvalidValue;
-    const unsigned blocks = (unsigned)((a.n_lines + threads - 1) / threads);
+    const unsigned threads = 32 * kTileWarps;
+    const dim3 grid((unsigned)((a.n_lines + threads - 1) / threads), (unsigned)a.n_seg);
     switch (L.window) {
-    case 4: sweep_contig_kernel<F, R, 4><<<blocks, threads, 0, s>>>(a); break;
-    case 8: sweep_contig_kernel<F, R, 8><<<blocks, threads, 0, s>>>(a); break;
-    case 16: sweep_contig_kernel<F, R, 16><<<blocks, threads, 0, s>>>(a); break;
+    case 4: sweep_contig_kernel<F, R, 4><<<grid, threads, 0, s>>>(a); break;
+    case 8: sweep_contig_kernel<F, R, 8><<<grid, threads, 0, s>>>(a); break;
+    case 16: sweep_contig_kernel<F, R, 16><<<grid, threads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -24,12 +23,12 @@ template <class F, typename R, int KIND>
 static cudaError_t launch_kind(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     if (KIND == K_Z && L.contiguous) return launch_contig<F, R>(L, a, s);
     const unsigned threads = (unsigned)L.threads;
-    const unsigned blocks = (unsigned)((a.n_lines + threads - 1) / threads);
+    const dim3 grid((unsigned)((a.n_lines + threads - 1) / threads), (unsigned)a.n_seg);
     switch (L.window) {
-    case 0: sweep_lines_kernel<F, R, 0, KIND><<<blocks, threads, 0, s>>>(a); break;
-    case 4: sweep_lines_kernel<F, R, 4, KIND><<<blocks, threads, 0, s>>>(a); break;
-    case 8: sweep_lines_kernel<F, R, 8, KIND><<<blocks, threads, 0, s>>>(a); break;
-    case 16: sweep_lines_kernel<F, R, 16, KIND><<<blocks, threads, 0, s>>>(a); break;
+    case 0: sweep_lines_kernel<F, R, 0, KIND><<<grid, threads, 0, s>>>(a); break;
+    case 4: sweep_lines_kernel<F, R, 4, KIND><<<grid, threads, 0, s>>>(a); break;
+    case 8: sweep_lines_kernel<F, R, 8, KIND><<<grid, threads, 0, s>>>(a); break;
+    case 16: sweep_lines_kernel<F, R, 16, KIND><<<grid, threads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

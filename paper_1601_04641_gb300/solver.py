@@ -151,5 +151,14 @@ class GP:
     def set_window(self, window):
         self._ck(self.lib.gp_set_window(self.h, int(window)))
 
+    def set_segments(self, axis, seg_len):
+        self._ck(self.lib.gp_set_segments(self.h, int(axis), int(seg_len)))
+
+    def segments(self, mode=0):
+        a = (ctypes.c_int * 3)()
+        b = (ctypes.c_int * 3)()
+        self._ck(self.lib.gp_get_segments(self.h, int(mode), a, b))
+        return tuple(a), tuple(b)
+
     def set_threads(self, axis, threads):
         self._ck(self.lib.gp_set_threads(self.h, int(axis), int(threads)))

@@ -4,6 +4,7 @@ inputs (GPU only).
 Tolerances: the FP64 path within 1e-12 relative in psi and mu (1e-13 for a
 single stage); the FP32 forms |d mu|/mu <= 1e-5 and relative L2 of psi <= 1e-4.
 """
+import ctypes
 import json
 import os
 
@@ -106,6 +107,46 @@ def test_edge_sizes(shape, realtime):
         ref = psi0.copy()
         oracle.step(ref, d, dt, OMEGA, g, realtime, 2)
         assert rel_max(got, ref) <= 1e-12, (shape, window)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("seg", [1, 7, 16, 17, 33, 100])
+def test_segment_lengths(seg, prec):
+    """Lines cut into segments of any length (one thread each, forward sweep
+    warmed up over W+1 nodes) give the oracle's step."""
+    dt, g = 0.004, 12.0
+    psi0 = inputs.random_field(SHAPE, seed=31)
+    if prec == "f32":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    gp = make(SHAPE, D, dt, OMEGA, g, prec)
+    for ax in range(3):
+        gp.set_segments(ax, seg)
+    gp.set_psi(psi0.astype(np.complex64) if prec == "f32" else psi0)
+    gp.step_real(2)
+    gp.step_imag(2)
+    ref = psi0.copy()
+    oracle.step(ref, D, dt, OMEGA, g, True, 2)
+    oracle.step(ref, D, dt, OMEGA, g, False, 2)
+    assert rel_max(gp.get_psi().astype(np.complex128), ref) <= (1e-12 if prec == "f64" else 2e-6)
+
+
+def test_device_pointer_follows_the_current_buffer():
+    """Three out-of-place sweeps per step: psi alternates between the caller's
+    buffer and the library's second one, and the pointer call says which."""
+    gp = make((10, 9, 8), (0.3, 0.3, 0.3), 0.01, OMEGA, 1.0)
+    gp.init_gaussian()
+
+    def current():
+        ptr, pending = ctypes.c_void_p(), ctypes.c_int(0)
+        assert gp.lib.gp_psi_device_ptr(gp.h, ctypes.byref(ptr), ctypes.byref(pending)) == 0
+        return ptr.value, pending.value
+
+    assert current() == (gp.psi.data_ptr(), 1)
+    gp.step_real(1)
+    ptr, pending = current()
+    assert ptr != gp.psi.data_ptr() and pending == 0
+    gp.step_imag(1)
+    assert current() == (gp.psi.data_ptr(), 1)
 
 
 @pytest.mark.parametrize("threads", [32, 64, 96, 256])
