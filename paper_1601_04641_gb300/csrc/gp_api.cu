@@ -81,7 +81,7 @@ struct gp_handle_s {
     bool scale_pending = false;
     long long step = 0;
     double t = 0;
-    int threads[3] = {128, 128, 128};
+    int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     int seg_override[3] = {0, 0, 0};  // interior nodes per segment, 0 = automatic
     // observables history queued during stepping
@@ -397,7 +397,7 @@ void segments(gp_handle h, int ax, int window, long long lines, int *seg_len, in
         if (h->seg_override[ax] > 0) {
             len = std::min(n, h->seg_override[ax]);
         } else {
-            const long long target = 152LL * 768 * 4;  // ~4 waves of resident threads
+            const long long target = 152LL * 448 * 2;  // ~2 waves of resident threads
             long long want = (target + lines - 1) / lines;
             const long long most = std::max(1, n / (4 * chunk));
             want = std::max(1LL, std::min(want, most));
@@ -463,7 +463,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     a.scale_out = h->d_scal + S_SCALE;
     a.dV = h->d[0] * h->d[1] * h->d[2];
     a.want_scale = realtime ? 0 : 1;
-    const int zthreads = L.contiguous ? 32 * 4 : L.threads;
+    const int zthreads = L.contiguous ? 32 : L.threads;
     if (stage == 2 && blocks_for(a.n_lines, zthreads) * (size_t)a.n_seg > h->partial_cap)
         return fail(h, GP_ERR_STATE, "z sweep grid exceeds the partials buffer");
     GP_CK(h, launch_sweep(L, a, h->stream));

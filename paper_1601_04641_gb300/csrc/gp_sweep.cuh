@@ -213,37 +213,67 @@ __device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a) {
     }
 }
 
+// ------------------------------------------------------------------ async copies
+// Global -> shared copies that bypass registers (cp.async); a copy whose
+// source is out of range writes zeros (source size 0).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int src = valid ? BYTES : 0;
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES),
+                     "r"(src)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most `pending` of this thread's newest copy groups are in flight.
+__device__ __forceinline__ void cp_async_wait(int pending) {
+    switch (pending) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    }
+}
+
 // ------------------------------------------------------------------ one segment
 // Outputs per chunk of the windowed solve: 16, or 8 for 16-byte elements
 // (complex FP64) to bound the register ring.
 template <typename V> __host__ __device__ constexpr int chunk_len() { return sizeof(V) >= 16 ? 8 : 16; }
+// Chunks in a line's input ring: two readable, two in flight.
+constexpr int kRingChunks = 4;
 
 // Windowed Thomas solve of the interior nodes [tb, te) of a line of n
-// interior unknowns.  `io` supplies single values (load1 / put1, interior
-// index t -> node t+1, loads past the line end read 0) and chunks of B
-// consecutive values (chunk_load then chunk_val(q); chunk_put(q) then
-// chunk_store), so that the contiguous axis can stage chunks through
-// shared memory.  te - tb is a multiple of B unless te == n.
+// interior unknowns.  Inputs are read by interior position p (node p+1;
+// positions outside [0, n) read 0) after io.need(p_end) has made the
+// positions [p_end - B, p_end) readable; outputs go through io.put(t0, q, v)
+// (position t0 + q) and io.flush(t0, count).
 template <class F, typename R, int B, int W, class IO>
 __device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
                                               const typename F::C *__restrict__ cp,
                                               const typename F::C *__restrict__ ipm1, IO &io) {
     using V = typename F::V;
-    // forward warm-up from dp = 0 at tw (exact when tw == 0)
+    // forward warm-up from dp = 0 at tw (exact when tw == 0: node 0 is 0)
     const int tw = tb > W + 1 ? tb - (W + 1) : 0;
-    V pm = tw > 0 ? io.load1(tw - 1) : F::zero();
-    V p0 = io.load1(tw);
-    V p1 = io.load1(tw + 1);
+    // the segment behaves as a line ending at e: W look-ahead values beyond
+    // te start the windowed backward sweep of its last chunk
+    const int e = min(te + W, n);
+    io.start(tw - 1, e + 2);
+    io.need(tw + 2);
+    V pm = io.val(tw - 1);
+    V p0 = io.val(tw);
+    V p1 = io.val(tw + 1);
     V dprev = F::zero();
     for (int t = tw; t < tb; ++t) {
         dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t));
         pm = p0;
         p0 = p1;
-        p1 = io.load1(t + 2);
+        io.need(t + 3);
+        p1 = io.val(t + 2);
     }
-    // the segment behaves as a line ending at e: W look-ahead values beyond
-    // te start the windowed backward sweep of its last chunk
-    const int e = min(te + W, n);
     const int m = e - tb;
     V D[B + W];
 #pragma unroll
@@ -253,19 +283,20 @@ __device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
             D[q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = io.load1(tb + q + 2);
+            io.need(tb + q + 3);
+            p1 = io.val(tb + q + 2);
         }
     }
     int t0 = tb;
     for (; t0 + B + W <= e; t0 += B) {
-        io.chunk_load(t0 + W + 2);
+        io.need(t0 + W + 2 + B);
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + W + q));
             D[W + q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = io.chunk_val(q);
+            p1 = io.val(t0 + W + 2 + q);
         }
         V phi = D[B + W - 1];
 #pragma unroll
@@ -273,13 +304,14 @@ __device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
 #pragma unroll
         for (int q = B - 1; q >= 0; --q) {
             phi = F::back(D[q], ldc(cp + t0 + q), phi);
-            io.chunk_put(t0, q, phi);
+            io.put(t0, q, phi);
         }
-        io.chunk_store(t0);
+        io.flush(t0, B);
 #pragma unroll
         for (int q = 0; q < W; ++q) D[q] = D[B + q];
     }
     const int rem = e - t0;  // 0 <= rem < B + W: finish from dp[e-1]
+    io.need(e + 2);
 #pragma unroll
     for (int q = W; q < B + W; ++q) {
         if (q < rem) {
@@ -287,7 +319,7 @@ __device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
             D[q] = dprev;
             pm = p0;
             p0 = p1;
-            p1 = io.load1(t0 + q + 2);
+            p1 = io.val(t0 + q + 2);
         }
     }
     V phi = F::zero();
@@ -295,13 +327,14 @@ __device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
     for (int q = B + W - 1; q >= 0; --q) {
         if (q < rem) {
             phi = F::back(D[q], ldc(cp + t0 + q), (q == rem - 1) ? F::zero() : phi);
-            if (t0 + q < te) io.put1(t0 + q, phi);
+            if (t0 + q < te) io.put(t0, q, phi);
         }
     }
+    io.flush(t0, min(rem, te - t0));
 }
 
-// Exact two-pass Thomas over a whole line: dp is staged in the output and
-// read back by the backward sweep.
+// Exact two-pass Thomas over a whole line (window 0): dp is staged in the
+// output and read back by the backward sweep.  Direct loads and stores.
 template <class F, typename R, class IO>
 __device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F::C *__restrict__ cp,
                                                  const typename F::C *__restrict__ ipm1, IO &io) {
@@ -325,164 +358,250 @@ __device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F:
     }
 }
 
-// ------------------------------------------------------------------ per-thread line access
-// One thread owns one segment of one line (element stride st).  The x sweep
-// applies the kick to every value it loads; the z sweep adds |phi|^2 of
-// every value it stores to the thread's norm sum.
-template <class F, typename R, int KIND> struct LineIO {
+// ------------------------------------------------------------------ kick / norm hooks
+// The x sweep applies the kick to every value it reads; the z sweep adds
+// |phi|^2 of every value it writes to the thread's norm sum.
+template <class F, typename R, int KIND> struct Hooks {
+    using V = typename F::V;
+    R s, dt, g, hx, x0, dx, vyz;
+    Acc<R> *acc;
+    __device__ __forceinline__ void init(const SweepArgs &a, long long L) {
+        s = R(1);
+        dt = g = hx = x0 = dx = vyz = R(0);
+        if (KIND == K_X) {
+            s = (R)__ldg(a.scale);
+            dt = (R)a.dt;
+            g = (R)a.g;
+            const int j = (int)(L / a.nz), k = (int)(L % a.nz);
+            const double y = a.origin[1] + j * a.d[1];
+            const double z = a.origin[2] + k * a.d[2];
+            vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
+            hx = (R)a.half_w2[0];
+            x0 = (R)a.origin[0];
+            dx = (R)a.d[0];
+        }
+    }
+    __device__ __forceinline__ V on_load(int p, V v) const {
+        if (KIND == K_X) {
+            const R x = fma((R)(p + 1), dx, x0);
+            v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
+        }
+        return v;
+    }
+    __device__ __forceinline__ void on_store(V v) const {
+        if (KIND == K_Z) acc->add(F::abs2(v));
+    }
+};
+
+// Direct per-thread access, for the exact two-pass form.
+template <class F, typename R, int KIND> struct DirectIO {
     using V = typename F::V;
     const V *in;
     V *out;
     long long st;
     int n;
-    R s, dt, g, hx, x0, dx, vyz;
-    Acc<R> *acc;
+    Hooks<F, R, KIND> hk;
     __device__ __forceinline__ V load1(int t) const {
-        if (t >= n) return F::zero();
-        V v = in[(long long)(t + 1) * st];
-        if (KIND == K_X) {
-            const R x = fma((R)(t + 1), dx, x0);
-            v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
-        }
-        return v;
+        if (t < 0 || t >= n) return F::zero();
+        return hk.on_load(t, in[(long long)(t + 1) * st]);
     }
     __device__ __forceinline__ void put1(int t, V v) const {
         out[(long long)(t + 1) * st] = v;
-        if (KIND == K_Z) acc->add(F::abs2(v));
+        hk.on_store(v);
     }
-    V P[chunk_len<V>()];  // prefetched chunk (all loads issued before use)
-    __device__ __forceinline__ void chunk_load(int tf) {
-#pragma unroll
-        for (int q = 0; q < chunk_len<V>(); ++q) P[q] = load1(tf + q);
-    }
-    __device__ __forceinline__ V chunk_val(int q) const { return P[q]; }
-    __device__ __forceinline__ void chunk_put(int tf, int q, V v) const { put1(tf + q, v); }
-    __device__ __forceinline__ void chunk_store(int) const {}
     __device__ __forceinline__ void stage(int t, V v) const { out[(long long)(t + 1) * st] = v; }
     __device__ __forceinline__ V unstage(int t) const { return out[(long long)(t + 1) * st]; }
 };
 
-// One thread per (line, segment): blockIdx.y is the segment; consecutive
-// threads own lines that are adjacent in memory (consecutive z for the x
-// and y sweeps), so every row of a warp's lines is one coalesced access.
-// Window 0 selects the exact two-pass form (one segment).
+// ------------------------------------------------------------------ strided axes
+// One thread owns one segment of one line (element stride st); consecutive
+// threads own lines adjacent in memory, so each cp.async instruction of a
+// warp reads one contiguous row.  Each thread streams its line through a
+// private column of a shared ring, ring[position % R][thread], R = 4 chunks:
+// while one chunk is consumed the next two are in flight.
+template <class F, typename R, int B, int KIND> struct ColumnIO {
+    using V = typename F::V;
+    static constexpr int RL = kRingChunks * B;  // ring length (power of two)
+    const V *in;
+    V *out;
+    V *ring;      // this thread's column: element p at ring[(p - s0) % RL * T]
+    long long st;
+    int n, T, s0, limit, issued, ready;
+    Hooks<F, R, KIND> hk;
+    __device__ __forceinline__ void issue() {
+        const int pb = s0 + issued * B;
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const int p = pb + e;
+            const bool ok = p >= 0 && p < n;
+            cp_async<sizeof(V)>(ring + ((p - s0) & (RL - 1)) * T, ok ? in + (long long)(p + 1) * st : in, ok);
+        }
+        cp_async_commit();
+        ++issued;
+    }
+    __device__ __forceinline__ void start(int first, int lim) {
+        s0 = first;
+        limit = lim;
+        issued = ready = 0;
+        while (issued < kRingChunks - 1 && s0 + issued * B < limit) issue();
+    }
+    __device__ __forceinline__ void need(int p_end) {
+        const int c = (p_end - 1 - s0) / B;
+        if (c < ready) return;
+        cp_async_wait(issued - 1 - c);
+        ready = c + 1;
+        while (issued <= c + kRingChunks - 2 && s0 + issued * B < limit) issue();
+    }
+    __device__ __forceinline__ V val(int p) const { return hk.on_load(p, ring[((p - s0) & (RL - 1)) * T]); }
+    __device__ __forceinline__ void put(int t0, int q, V v) const {
+        out[(long long)(t0 + q + 1) * st] = v;
+        hk.on_store(v);
+    }
+    __device__ __forceinline__ void flush(int, int) const {}
+};
+
+// One thread per (line, segment); blockIdx.y is the segment.  Window 0
+// selects the exact two-pass form over whole lines with direct access.
 template <class F, typename R, int W, int KIND>
-__global__ void __launch_bounds__(256) sweep_lines_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
     using V = typename F::V;
     using C = typename F::C;
+    constexpr int B = chunk_len<V>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     Acc<R> acc;
     if (L < a.n_lines) {
-        LineIO<F, R, KIND> io;
         const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
-        io.in = static_cast<const V *>(a.psi) + off;
-        io.out = static_cast<V *>(a.psi_out) + off;
-        io.st = a.stride;
-        io.n = a.N - 2;
-        io.acc = &acc;
-        io.s = R(1);
-        io.dt = io.g = io.hx = io.x0 = io.dx = io.vyz = R(0);
-        if (KIND == K_X) {
-            io.s = (R)__ldg(a.scale);
-            io.dt = (R)a.dt;
-            io.g = (R)a.g;
-            const int j = (int)(L / a.nz), k = (int)(L % a.nz);
-            const double y = a.origin[1] + j * a.d[1];
-            const double z = a.origin[2] + k * a.d[2];
-            io.vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
-            io.hx = (R)a.half_w2[0];
-            io.x0 = (R)a.origin[0];
-            io.dx = (R)a.d[0];
-        }
+        const V *in = static_cast<const V *>(a.psi) + off;
+        V *out = static_cast<V *>(a.psi_out) + off;
+        const int n = a.N - 2;
+        const int seg = blockIdx.y;
         const C *cp = static_cast<const C *>(a.cp);
         const C *ipm1 = static_cast<const C *>(a.ip);
-        const int seg = blockIdx.y;
-        if (seg == 0) io.out[0] = F::zero();
-        if (seg == a.n_seg - 1) io.out[(long long)(a.N - 1) * io.st] = F::zero();
+        if (seg == 0) out[0] = F::zero();
+        if (seg == a.n_seg - 1) out[(long long)(a.N - 1) * a.stride] = F::zero();
         if constexpr (W > 0) {
+            ColumnIO<F, R, B, KIND> io;
+            io.in = in;
+            io.out = out;
+            io.st = a.stride;
+            io.n = n;
+            io.T = blockDim.x;
+            io.ring = reinterpret_cast<V *>(smem_raw) + threadIdx.x;
+            io.hk.acc = &acc;
+            io.hk.init(a, L);
             const int tb = seg * a.seg_len;
-            const int te = seg == a.n_seg - 1 ? io.n : tb + a.seg_len;
-            solve_segment<F, R, chunk_len<V>(), W>(io.n, tb, te, (R)a.kappa, cp, ipm1, io);
+            const int te = seg == a.n_seg - 1 ? n : tb + a.seg_len;
+            solve_segment<F, R, B, W>(n, tb, te, (R)a.kappa, cp, ipm1, io);
         } else {
-            solve_line_exact<F, R>(io.n, (R)a.kappa, cp, ipm1, io);
+            DirectIO<F, R, KIND> io;
+            io.in = in;
+            io.out = out;
+            io.st = a.stride;
+            io.n = n;
+            io.hk.acc = &acc;
+            io.hk.init(a, L);
+            solve_line_exact<F, R>(n, (R)a.kappa, cp, ipm1, io);
         }
     }
     if (KIND == K_Z) norm_finalize(acc.value(), a);
 }
 
+template <typename V> __host__ __device__ constexpr size_t column_ring_bytes(int threads) {
+    return (size_t)kRingChunks * chunk_len<V>() * threads * sizeof(V);
+}
+
 // ------------------------------------------------------------------ contiguous axis
 // A warp owns one segment of 32 consecutive stride-1 lines (one contiguous
-// block of 32 * N elements).  Chunks of B values per line are moved between
-// global and shared memory cooperatively -- each instruction covers 32/B
-// lines x B consecutive elements -- and transposed through a padded tile so
-// that lane l then reads / writes row l with no bank conflicts.  Single
-// values of the warm-up, first and last chunk use direct loads and stores.
-constexpr int kTileWarps = 4;
-
-template <class F, typename R, int B> struct TileIO {
+// block of 32 * N elements).  Input chunks of B values per line are copied
+// cooperatively (each cp.async instruction covers 32/B lines x B consecutive
+// elements) into a per-warp ring, ring[line][position % R] (rows padded by
+// one element against bank conflicts), two chunks ahead of the consumer;
+// lane l reads row l.  Outputs are collected in a padded tile, row l per
+// lane, and written back cooperatively.
+template <class F, typename R, int B, int W> struct TileIO {
     using V = typename F::V;
-    static constexpr int LD = B + 1;   // padded row
-    static constexpr int LPI = 32 / B; // lines per cooperative instruction
-    const V *in0;                      // node 0 of the warp's first line (input)
-    V *out0;                           // same node in the output buffer
-    V *tile;                           // 32 x LD values of this warp
-    int N, n, lane, nvalid;
+    static constexpr int RL = kRingChunks * B;   // ring length per line (power of two)
+    static constexpr int RS = RL + 1;            // padded ring row
+    static constexpr int OS = B + W + 1;         // padded output row
+    static constexpr int LPI = 32 / B;           // lines per cooperative instruction
+    const V *in0;                                // node 0 of the warp's first line
+    V *out0;
+    V *ring, *otile;
+    int N, n, lane, nvalid, s0, limit, issued, ready;
     Acc<R> *acc;
-    __device__ __forceinline__ V load1(int t) const {
-        if (t >= n || lane >= nvalid) return F::zero();
-        return in0[(long long)lane * N + t + 1];
-    }
-    __device__ __forceinline__ void put1(int t, V v) const {
-        if (lane < nvalid) {
-            out0[(long long)lane * N + t + 1] = v;
-            acc->add(F::abs2(v));
-        }
-    }
-    // Cooperative load of interior values tf..tf+B-1 of the warp's 32 lines
-    // (values past the last interior node read as 0); lane l then reads row l.
-    __device__ __forceinline__ void chunk_load(int tf) const {
-        __syncwarp();
+    __device__ __forceinline__ void issue() {
+        const int pb = s0 + issued * B;
 #pragma unroll 4
         for (int it = 0; it < B; ++it) {
             const int q = it * LPI + lane / B, e = lane % B;
-            const int node = tf + 1 + e;
-            V v = F::zero();
-            if (q < nvalid && node <= N - 2) v = in0[(long long)q * N + node];
-            tile[q * LD + e] = v;
+            const int p = pb + e;
+            const bool ok = q < nvalid && p >= 0 && p < n;
+            cp_async<sizeof(V)>(ring + q * RS + ((p - s0) & (RL - 1)),
+                                ok ? in0 + (long long)q * N + p + 1 : in0, ok);
         }
-        __syncwarp();
+        cp_async_commit();
+        ++issued;
     }
-    __device__ __forceinline__ V chunk_val(int q) const { return tile[lane * LD + q]; }
-    // Lane l writes row l (its inputs there are consumed); chunk_store then
-    // writes the 32 x B outputs back cooperatively.
-    __device__ __forceinline__ void chunk_put(int, int q, V v) const {
-        tile[lane * LD + q] = v;
+    __device__ __forceinline__ void start(int first, int lim) {
+        s0 = first;
+        limit = lim;
+        issued = ready = 0;
+        while (issued < kRingChunks - 1 && s0 + issued * B < limit) issue();
+    }
+    __device__ __forceinline__ void need(int p_end) {
+        const int c = (p_end - 1 - s0) / B;
+        if (c < ready) return;
+        __syncwarp();  // every lane is done with the chunk slot about to be refilled
+        cp_async_wait(issued - 1 - c);
+        __syncwarp();  // the chunk written by all lanes' copies is visible to all lanes
+        ready = c + 1;
+        while (issued <= c + kRingChunks - 2 && s0 + issued * B < limit) issue();
+    }
+    __device__ __forceinline__ V val(int p) const { return ring[lane * RS + ((p - s0) & (RL - 1))]; }
+    __device__ __forceinline__ void put(int, int q, V v) const {
+        otile[lane * OS + q] = v;
         if (lane < nvalid) acc->add(F::abs2(v));
     }
-    __device__ __forceinline__ void chunk_store(int tf) const {
+    // Write positions t0 .. t0+count-1 of the 32 lines back to global memory.
+    __device__ __forceinline__ void flush(int t0, int count) const {
         __syncwarp();
+        if (count == B) {
 #pragma unroll 4
-        for (int it = 0; it < B; ++it) {
-            const int q = it * LPI + lane / B, e = lane % B;
-            if (q < nvalid) out0[(long long)q * N + tf + 1 + e] = tile[q * LD + e];
+            for (int it = 0; it < B; ++it) {
+                const int q = it * LPI + lane / B, e = lane % B;
+                if (q < nvalid) out0[(long long)q * N + t0 + 1 + e] = otile[q * OS + e];
+            }
+        } else {
+            for (int q = 0; q < nvalid; ++q)
+                for (int e = lane; e < count; e += 32) out0[(long long)q * N + t0 + 1 + e] = otile[q * OS + e];
         }
+        __syncwarp();
     }
 };
 
+template <typename V, int W> __host__ __device__ constexpr size_t tile_warp_bytes() {
+    return (size_t)32 * ((kRingChunks * chunk_len<V>() + 1) + (chunk_len<V>() + W + 1)) * sizeof(V);
+}
+constexpr int kTileWarps = 2;
+
 template <class F, typename R, int W>
-__global__ void __launch_bounds__(kTileWarps * 32) sweep_contig_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_contig_kernel(SweepArgs a) {
     using V = typename F::V;
     using C = typename F::C;
     constexpr int B = chunk_len<V>();
-    __shared__ V tiles[kTileWarps][32 * (B + 1)];
+    using IO = TileIO<F, R, B, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long L0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
     Acc<R> acc;
     if (L0 < a.n_lines) {
-        TileIO<F, R, B> io;
+        IO io;
+        V *wbase = reinterpret_cast<V *>(smem_raw + warp * tile_warp_bytes<V, W>());
+        io.ring = wbase;
+        io.otile = wbase + 32 * IO::RS;
         io.in0 = static_cast<const V *>(a.psi) + L0 * a.N;
         io.out0 = static_cast<V *>(a.psi_out) + L0 * a.N;
-        io.tile = tiles[warp];
         io.N = a.N;
         io.n = a.N - 2;
         io.lane = lane;

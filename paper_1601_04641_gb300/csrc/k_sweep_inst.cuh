@@ -6,32 +6,60 @@
 
 namespace gpcn {
 
-template <class F, typename R>
-static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+template <class F, typename R, int W>
+static cudaError_t launch_contig_w(const SweepArgs &a, cudaStream_t s) {
+    using V = typename F::V;
     const unsigned threads = 32 * kTileWarps;
     const dim3 grid((unsigned)((a.n_lines + threads - 1) / threads), (unsigned)a.n_seg);
+    const size_t smem = kTileWarps * tile_warp_bytes<V, W>();
+    static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_contig_kernel<F, R, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    sweep_contig_kernel<F, R, W><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class F, typename R>
+static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     switch (L.window) {
-    case 4: sweep_contig_kernel<F, R, 4><<<grid, threads, 0, s>>>(a); break;
-    case 8: sweep_contig_kernel<F, R, 8><<<grid, threads, 0, s>>>(a); break;
-    case 16: sweep_contig_kernel<F, R, 16><<<grid, threads, 0, s>>>(a); break;
+    case 4: return launch_contig_w<F, R, 4>(a, s);
+    case 8: return launch_contig_w<F, R, 8>(a, s);
+    case 16: return launch_contig_w<F, R, 16>(a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+template <class F, typename R, int W, int KIND>
+static cudaError_t launch_lines_w(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    using V = typename F::V;
+    const unsigned threads = (unsigned)L.threads;
+    const dim3 grid((unsigned)((a.n_lines + threads - 1) / threads), (unsigned)a.n_seg);
+    const size_t smem = W > 0 ? column_ring_bytes<V>(threads) : 0;
+    static int attr = 0;  // largest dynamic shared memory opted in so far
+    if ((int)smem > attr && smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_lines_kernel<F, R, W, KIND>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = (int)smem;
+    }
+    sweep_lines_kernel<F, R, W, KIND><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <class F, typename R, int KIND>
 static cudaError_t launch_kind(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     if (KIND == K_Z && L.contiguous) return launch_contig<F, R>(L, a, s);
-    const unsigned threads = (unsigned)L.threads;
-    const dim3 grid((unsigned)((a.n_lines + threads - 1) / threads), (unsigned)a.n_seg);
     switch (L.window) {
-    case 0: sweep_lines_kernel<F, R, 0, KIND><<<grid, threads, 0, s>>>(a); break;
-    case 4: sweep_lines_kernel<F, R, 4, KIND><<<grid, threads, 0, s>>>(a); break;
-    case 8: sweep_lines_kernel<F, R, 8, KIND><<<grid, threads, 0, s>>>(a); break;
-    case 16: sweep_lines_kernel<F, R, 16, KIND><<<grid, threads, 0, s>>>(a); break;
+    case 0: return launch_lines_w<F, R, 0, KIND>(L, a, s);
+    case 4: return launch_lines_w<F, R, 4, KIND>(L, a, s);
+    case 8: return launch_lines_w<F, R, 8, KIND>(L, a, s);
+    case 16: return launch_lines_w<F, R, 16, KIND>(L, a, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <class F, typename R>
