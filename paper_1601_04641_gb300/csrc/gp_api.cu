@@ -48,6 +48,10 @@ thread_local std::string g_create_error;
 // Device scalars of a handle.
 enum Scalar { S_SCALE = 0, S_ONE = 1, S_NORM_SWEEP = 2, S_NORM_INIT = 3, S_COUNT = 8 };
 
+struct KickTables {
+    size_t off[3] = {0, 0, 0};  // byte offsets of exp(-dt V_a) per axis (imaginary time)
+};
+
 struct CoefSet {
     size_t off_cp = 0, off_ip = 0;  // byte offsets into the coefficient buffer
     int window = 0;                  // chosen window (0: exact two-pass)
@@ -72,6 +76,7 @@ struct gp_handle_s {
     char *d_coef = nullptr;
     size_t coef_bytes = 0;
     CoefSet coef[2][3];
+    KickTables kick;
     int forced_window = -1;
     double *d_scal = nullptr;
     double *d_obs = nullptr;
@@ -83,6 +88,7 @@ struct gp_handle_s {
     double t = 0;
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
+    bool pair_lines = true;    // two lines per thread on the strided axes when possible
     int seg_override[3] = {0, 0, 0};  // interior nodes per segment, 0 = automatic
     // observables history queued during stepping
     int track_every = 0, track_cap = 0, track_count = 0;
@@ -169,7 +175,26 @@ gp_status build_coefficients(gp_handle h) {
             off = align_up(off + esz * n, 256);
         }
     }
+    for (int ax = 0; ax < 3; ++ax) {
+        h->kick.off[ax] = off;
+        off = align_up(off + rsz * h->n[ax], 256);
+    }
     host.assign(off, 0);
+    // exp(-dt w^2 a^2 / 2) per node of each axis: the trap part of the
+    // imaginary-time kick factorises over the axes.
+    for (int ax = 0; ax < 3; ++ax) {
+        for (int i = 0; i < h->n[ax]; ++i) {
+            const double a = (i - 0.5 * (h->n[ax] - 1)) * h->d[ax];
+            const double v = std::exp(-h->dt * 0.5 * h->w[ax] * h->w[ax] * a * a);
+            char *dst = host.data() + h->kick.off[ax] + i * rsz;
+            if (f32) {
+                const float fv = (float)v;
+                std::memcpy(dst, &fv, sizeof(fv));
+            } else {
+                std::memcpy(dst, &v, sizeof(v));
+            }
+        }
+    }
     for (int mode = 0; mode < modes_of(h); ++mode) {
         for (int ax = 0; ax < 3; ++ax) {
             const int n = h->n[ax] - 2;
@@ -386,12 +411,24 @@ gp_status enter(gp_handle h) {
 
 gp_status queue_observables(gp_handle h, double *dst);
 
+// Two adjacent lines per thread on the strided axes when every pair is
+// adjacent in memory and 2-element aligned: an even number of lines and,
+// for y lines (i, k), an even nz.  Elements of 8 bytes or less only.
+int lines_per_thread(gp_handle h, int ax) {
+    if (!h->pair_lines || ax == 2 || h->elem > 8) return 1;
+    if (sweep_lines(h, ax) % 2) return 1;
+    if (ax == 1 && h->n[2] % 2) return 1;
+    return 2;
+}
+
 // Segments of one axis: enough (line, segment) threads to fill the GPU a
 // few times over, each segment a whole number of chunks.  The exact form
 // (window 0) solves whole lines.
 void segments(gp_handle h, int ax, int window, long long lines, int *seg_len, int *n_seg) {
     const int n = h->n[ax] - 2;
-    const int chunk = (h->prec == GP_F64 && h->field == GP_COMPLEX) ? 8 : 16;
+    const int lpt = lines_per_thread(h, ax);
+    lines /= lpt;
+    const int chunk = (h->elem * lpt >= 16) ? 8 : 16;
     int len = n;
     if (window > 0) {
         if (h->seg_override[ax] > 0) {
@@ -421,6 +458,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     const CoefSet &cs = h->coef[mode][ax];
     L.window = cs.window;
     L.threads = h->threads[ax];
+    L.lpt = lines_per_thread(h, ax);
     L.contiguous = (ax == 2 && h->contiguous_z && cs.window > 0) ? 1 : 0;
 
     SweepArgs a;
@@ -448,6 +486,11 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     segments(h, ax, L.window, a.n_lines, &a.seg_len, &a.n_seg);
     a.kappa = h->dt / (4.0 * h->d[ax] * h->d[ax]);
     a.scale = h->d_scal + (h->scale_pending ? S_SCALE : S_ONE);
+    if (!realtime) {
+        a.kick_ex = h->d_coef + h->kick.off[0];
+        a.kick_ey = h->d_coef + h->kick.off[1];
+        a.kick_ez = h->d_coef + h->kick.off[2];
+    }
     a.dt = h->dt;
     a.g = h->g;
     for (int q = 0; q < 3; ++q) {

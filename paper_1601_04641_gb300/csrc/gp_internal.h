@@ -35,6 +35,9 @@ struct SweepArgs {
     double kappa;          // |c| = dt / (4 d^2)
     // kick (K_X): site (i, j, k) with i along the line, (j, k) = (L / nz, L % nz)
     const double *scale;   // pending renormalisation factor applied on load
+    const void *kick_ex;   // imaginary time: exp(-dt V_x(i)) per x node (else null)
+    const void *kick_ey;   //                 exp(-dt V_y(j)) per y node
+    const void *kick_ez;   //                 exp(-dt V_z(k)) per z node
     double dt, g;
     double half_w2[3];     // (gamma^2, nu^2, lambda^2) / 2
     double origin[3];      // coordinate of node 0 per axis
@@ -55,6 +58,7 @@ struct SweepLaunch {
     Kind kind;
     int window;            // 4, 8, 16, or 0 for the exact two-pass solve
     int threads;           // threads per block
+    int lpt;               // lines per thread of the strided kernel (1, or 2 adjacent lines)
     int contiguous;        // 1: warp-tiled kernel for the stride-1 axis
 };
 

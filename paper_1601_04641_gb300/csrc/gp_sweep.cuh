@@ -66,6 +66,62 @@ __device__ __forceinline__ double g_exp(double x) { return exp(x); }
 __device__ __forceinline__ void g_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void g_sincos(double x, double *s, double *c) { sincos(x, s, c); }
 
+// Short Taylor polynomials for the kick's small arguments (textbook series,
+// Horner form).  Each is used only where its truncation error is below a
+// quarter of the unit roundoff; larger arguments fall back to exp / sincos.
+//   FP32: sin through x^5, cos through x^6 for |x| <= 0.2 (next terms
+//         x^7/7!, x^8/8! below 2^-26 relative); exp(-y) through y^4 for
+//         |y| <= 0.05 (next term below 2^-27).
+//   FP64: sin through x^9, cos through x^10 for |x| <= 0.1 (next terms below
+//         2^-58 relative); exp(-y) through y^7 for |y| <= 0.02 (next term
+//         below 2^-60).
+template <typename R> struct Series;
+template <> struct Series<float> {
+    static constexpr float kTrig = 0.2f, kExp = 0.05f;
+    __device__ __forceinline__ static void sincos(float x, float *sn, float *cs) {
+        const float x2 = x * x;
+        *sn = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
+        *cs = fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f), 1.f);
+    }
+    __device__ __forceinline__ static float expm(float y) {  // exp(-y)
+        return fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.f / 24.f, -1.f / 6.f), 0.5f), -1.f), 1.f);
+    }
+};
+template <> struct Series<double> {
+    static constexpr double kTrig = 0.1, kExp = 0.02;
+    __device__ __forceinline__ static void sincos(double x, double *sn, double *cs) {
+        const double x2 = x * x;
+        *sn = x * fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0),
+                              -1.0 / 6.0), 1.0);
+        *cs = fma(x2, fma(x2, fma(x2, fma(x2, fma(x2, -1.0 / 3628800.0, 1.0 / 40320.0), -1.0 / 720.0),
+                                  1.0 / 24.0), -0.5), 1.0);
+    }
+    __device__ __forceinline__ static double expm(double y) {  // exp(-y)
+        return fma(y, fma(y, fma(y, fma(y, fma(y, fma(y, fma(y, -1.0 / 5040.0, 1.0 / 720.0),
+                                                         -1.0 / 120.0), 1.0 / 24.0), -1.0 / 6.0),
+                                  0.5), -1.0), 1.0);
+    }
+};
+template <typename R> __device__ __forceinline__ void kick_sincos(R x, R *sn, R *cs) {
+    if (fabs(x) <= Series<R>::kTrig) Series<R>::sincos(x, sn, cs);
+    else g_sincos(x, sn, cs);
+}
+template <typename R> __device__ __forceinline__ R kick_expm(R y) {
+    return fabs(y) <= Series<R>::kExp ? Series<R>::expm(y) : g_exp(-y);
+}
+
+// Per-site kick state of one x line.  Imaginary time: exp(-dt V) is the
+// product of per-axis factors exp(-dt V_x(i)) (a table) and
+// exp(-dt (V_y(j) + V_z(k))) (fixed along the line), times exp(-dt g |psi|^2).
+// Real time: theta = dt (V + g |psi|^2) and exp(-i theta).
+template <typename R> struct KickState {
+    R s;              // pending renormalisation factor
+    R dtg;            // dt * g
+    R eyz;            // exp(-dt (V_y + V_z)) of the line (imaginary time)
+    const R *ex;      // exp(-dt V_x(i)) per node (imaginary time)
+    R dt, hx, x0, dx, vyz;  // real time: V = hx x^2 + vyz, x = x0 + i dx
+};
+
 // Per-thread sum: plain FP64, or FP32 with an error-free two-sum
 // compensation term (Knuth) so that long FP32 sums keep FP64-like accuracy.
 template <typename R> struct Acc;
@@ -88,6 +144,7 @@ template <> struct Acc<float> {
 // ------------------------------------------------------------------ forms
 // Imaginary time, real field: c = kappa, coefficients real.
 template <typename R> struct FImagReal {
+    using Real = R;
     using V = R;
     using C = R;
     __device__ __forceinline__ static V zero() { return R(0); }
@@ -100,14 +157,15 @@ template <typename R> struct FImagReal {
     }
     __device__ __forceinline__ static V back(V dp, C cp, V phi) { return fma(-cp, phi, dp); }
     __device__ __forceinline__ static R abs2(V v) { return v * v; }
-    __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
-        V q = p * s;
-        return q * g_exp(-dt * fma(g, q * q, vpot));
+    __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
+        const V q = p * k.s;
+        return q * (__ldg(k.ex + node) * k.eyz * kick_expm(k.dtg * (q * q)));
     }
 };
 
 // Imaginary time, complex field: c = kappa real, applied to both parts.
 template <typename R> struct FImagCplx {
+    using Real = R;
     using V = cx<R>;
     using C = R;
     __device__ __forceinline__ static V zero() { return V{R(0), R(0)}; }
@@ -123,15 +181,16 @@ template <typename R> struct FImagCplx {
         return V{fma(-cp, phi.re, dp.re), fma(-cp, phi.im, dp.im)};
     }
     __device__ __forceinline__ static R abs2(V v) { return fma(v.re, v.re, v.im * v.im); }
-    __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
-        V q{p.re * s, p.im * s};
-        R f = g_exp(-dt * fma(g, abs2(q), vpot));
+    __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
+        const V q{p.re * k.s, p.im * k.s};
+        const R f = __ldg(k.ex + node) * k.eyz * kick_expm(k.dtg * abs2(q));
         return V{q.re * f, q.im * f};
     }
 };
 
 // Real time, complex field: c = i kappa, coefficients complex.
 template <typename R> struct FRealTime {
+    using Real = R;
     using V = cx<R>;
     using C = cx<R>;
     __device__ __forceinline__ static V zero() { return V{R(0), R(0)}; }
@@ -154,13 +213,36 @@ template <typename R> struct FRealTime {
         return V{dp.re - pre, dp.im - pim};
     }
     __device__ __forceinline__ static R abs2(V v) { return fma(v.re, v.re, v.im * v.im); }
-    __device__ __forceinline__ static V kick(V p, R s, R dt, R vpot, R g) {
-        V q{p.re * s, p.im * s};
+    __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
+        const V q{p.re * k.s, p.im * k.s};
+        const R x = fma((R)node, k.dx, k.x0);
+        const R theta = fma(k.dtg, abs2(q), k.dt * fma(k.hx * x, x, k.vyz));
         R sn, cs;
-        g_sincos(dt * fma(g, abs2(q), vpot), &sn, &cs);
+        kick_sincos(theta, &sn, &cs);
         // exp(-i theta) q
         return V{fma(cs, q.re, sn * q.im), fma(cs, q.im, -sn * q.re)};
     }
+};
+
+// Two adjacent lines advanced together by one thread: every operation is
+// applied to both, the recursion coefficients are shared, and a pair of
+// elements moves as one 8- or 16-byte access.
+template <class F> struct FPair {
+    using Real = typename F::Real;
+    using E = typename F::V;
+    struct __align__(2 * sizeof(E)) V { E a, b; };
+    using C = typename F::C;
+    __device__ __forceinline__ static V zero() { return V{F::zero(), F::zero()}; }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, Real k) {
+        return V{F::rhs(pm.a, p0.a, p1.a, k), F::rhs(pm.b, p0.b, p1.b, k)};
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, Real k, C ipm1) {
+        return V{F::fwd(r.a, dprev.a, k, ipm1), F::fwd(r.b, dprev.b, k, ipm1)};
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) {
+        return V{F::back(dp.a, cp, phi.a), F::back(dp.b, cp, phi.b)};
+    }
+    __device__ __forceinline__ static Real abs2(V v) { return F::abs2(v.a) + F::abs2(v.b); }
 };
 
 // ------------------------------------------------------------------ reductions
@@ -361,48 +443,69 @@ __device__ __forceinline__ void solve_line_exact(int n, R kap, const typename F:
 // ------------------------------------------------------------------ kick / norm hooks
 // The x sweep applies the kick to every value it reads; the z sweep adds
 // |phi|^2 of every value it writes to the thread's norm sum.
-template <class F, typename R, int KIND> struct Hooks {
+template <typename R, int KIND> __device__ __forceinline__ void kick_init(KickState<R> &k, const SweepArgs &a,
+                                                                          long long L) {
+    const int j = (int)(L / a.nz), kk = (int)(L % a.nz);
+    k.s = (R)__ldg(a.scale);
+    k.dtg = (R)(a.dt * a.g);
+    k.ex = static_cast<const R *>(a.kick_ex);
+    k.eyz = a.kick_ex ? __ldg(static_cast<const R *>(a.kick_ey) + j) * __ldg(static_cast<const R *>(a.kick_ez) + kk)
+                      : R(1);
+    const double y = a.origin[1] + j * a.d[1];
+    const double z = a.origin[2] + kk * a.d[2];
+    k.dt = (R)a.dt;
+    k.vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
+    k.hx = (R)a.half_w2[0];
+    k.x0 = (R)a.origin[0];
+    k.dx = (R)a.d[0];
+}
+
+// F is the single-line form; M is F (one line per thread) or FPair<F>.
+template <class F, class M, typename R, int KIND> struct Hooks;
+template <class F, typename R, int KIND> struct Hooks<F, F, R, KIND> {
     using V = typename F::V;
-    R s, dt, g, hx, x0, dx, vyz;
+    KickState<R> k;
     Acc<R> *acc;
     __device__ __forceinline__ void init(const SweepArgs &a, long long L) {
-        s = R(1);
-        dt = g = hx = x0 = dx = vyz = R(0);
-        if (KIND == K_X) {
-            s = (R)__ldg(a.scale);
-            dt = (R)a.dt;
-            g = (R)a.g;
-            const int j = (int)(L / a.nz), k = (int)(L % a.nz);
-            const double y = a.origin[1] + j * a.d[1];
-            const double z = a.origin[2] + k * a.d[2];
-            vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
-            hx = (R)a.half_w2[0];
-            x0 = (R)a.origin[0];
-            dx = (R)a.d[0];
-        }
+        if (KIND == K_X) kick_init<R, KIND>(k, a, L);
     }
     __device__ __forceinline__ V on_load(int p, V v) const {
-        if (KIND == K_X) {
-            const R x = fma((R)(p + 1), dx, x0);
-            v = F::kick(v, s, dt, fma(hx * x, x, vyz), g);
-        }
+        if (KIND == K_X) v = F::kick(v, k, p + 1);
         return v;
     }
     __device__ __forceinline__ void on_store(V v) const {
         if (KIND == K_Z) acc->add(F::abs2(v));
     }
 };
+template <class F, typename R, int KIND> struct Hooks<F, FPair<F>, R, KIND> {
+    using V = typename FPair<F>::V;
+    KickState<R> ka, kb;
+    Acc<R> *acc;
+    __device__ __forceinline__ void init(const SweepArgs &a, long long L) {
+        if (KIND == K_X) {
+            kick_init<R, KIND>(ka, a, L);
+            kick_init<R, KIND>(kb, a, L + 1);
+        }
+    }
+    __device__ __forceinline__ V on_load(int p, V v) const {
+        if (KIND == K_X) v = V{F::kick(v.a, ka, p + 1), F::kick(v.b, kb, p + 1)};
+        return v;
+    }
+    __device__ __forceinline__ void on_store(V v) const {
+        if (KIND == K_Z) acc->add(FPair<F>::abs2(v));
+    }
+};
 
 // Direct per-thread access, for the exact two-pass form.
-template <class F, typename R, int KIND> struct DirectIO {
-    using V = typename F::V;
+template <class F, class M, typename R, int KIND> struct DirectIO {
+    using V = typename M::V;
     const V *in;
     V *out;
     long long st;
     int n;
-    Hooks<F, R, KIND> hk;
+    Hooks<F, M, R, KIND> hk;
     __device__ __forceinline__ V load1(int t) const {
-        if (t < 0 || t >= n) return F::zero();
+        if (t < 0 || t >= n) return M::zero();
         return hk.on_load(t, in[(long long)(t + 1) * st]);
     }
     __device__ __forceinline__ void put1(int t, V v) const {
@@ -419,15 +522,15 @@ template <class F, typename R, int KIND> struct DirectIO {
 // warp reads one contiguous row.  Each thread streams its line through a
 // private column of a shared ring, ring[position % R][thread], R = 4 chunks:
 // while one chunk is consumed the next two are in flight.
-template <class F, typename R, int B, int KIND> struct ColumnIO {
-    using V = typename F::V;
+template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
+    using V = typename M::V;
     static constexpr int RL = kRingChunks * B;  // ring length (power of two)
     const V *in;
     V *out;
     V *ring;      // this thread's column: element p at ring[(p - s0) % RL * T]
     long long st;
     int n, T, s0, limit, issued, ready;
-    Hooks<F, R, KIND> hk;
+    Hooks<F, M, R, KIND> hk;
     __device__ __forceinline__ void issue() {
         const int pb = s0 + issued * B;
 #pragma unroll
@@ -460,31 +563,37 @@ template <class F, typename R, int B, int KIND> struct ColumnIO {
     __device__ __forceinline__ void flush(int, int) const {}
 };
 
-// One thread per (line, segment); blockIdx.y is the segment.  Window 0
-// selects the exact two-pass form over whole lines with direct access.
-template <class F, typename R, int W, int KIND>
+template <class F, int LPT> struct LinesPerThread { using M = F; };
+template <class F> struct LinesPerThread<F, 2> { using M = FPair<F>; };
+
+// One thread per (line, segment), or per (pair of adjacent lines, segment)
+// when LPT = 2; blockIdx.y is the segment.  Window 0 selects the exact
+// two-pass form over whole lines with direct access.
+template <class F, typename R, int W, int KIND, int LPT>
 __global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
-    using V = typename F::V;
+    using M = typename LinesPerThread<F, LPT>::M;
+    using V = typename M::V;
     using C = typename F::C;
     constexpr int B = chunk_len<V>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long L = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * LPT;
     Acc<R> acc;
     if (L < a.n_lines) {
         const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
-        const V *in = static_cast<const V *>(a.psi) + off;
-        V *out = static_cast<V *>(a.psi_out) + off;
+        const V *in = reinterpret_cast<const V *>(static_cast<const typename F::V *>(a.psi) + off);
+        V *out = reinterpret_cast<V *>(static_cast<typename F::V *>(a.psi_out) + off);
+        const long long st = a.stride / LPT;  // stride in units of V
         const int n = a.N - 2;
         const int seg = blockIdx.y;
         const C *cp = static_cast<const C *>(a.cp);
         const C *ipm1 = static_cast<const C *>(a.ip);
-        if (seg == 0) out[0] = F::zero();
-        if (seg == a.n_seg - 1) out[(long long)(a.N - 1) * a.stride] = F::zero();
+        if (seg == 0) out[0] = M::zero();
+        if (seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::zero();
         if constexpr (W > 0) {
-            ColumnIO<F, R, B, KIND> io;
+            ColumnIO<F, M, R, B, KIND> io;
             io.in = in;
             io.out = out;
-            io.st = a.stride;
+            io.st = st;
             io.n = n;
             io.T = blockDim.x;
             io.ring = reinterpret_cast<V *>(smem_raw) + threadIdx.x;
@@ -492,16 +601,16 @@ __global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
             io.hk.init(a, L);
             const int tb = seg * a.seg_len;
             const int te = seg == a.n_seg - 1 ? n : tb + a.seg_len;
-            solve_segment<F, R, B, W>(n, tb, te, (R)a.kappa, cp, ipm1, io);
+            solve_segment<M, R, B, W>(n, tb, te, (R)a.kappa, cp, ipm1, io);
         } else {
-            DirectIO<F, R, KIND> io;
+            DirectIO<F, M, R, KIND> io;
             io.in = in;
             io.out = out;
-            io.st = a.stride;
+            io.st = st;
             io.n = n;
             io.hk.acc = &acc;
             io.hk.init(a, L);
-            solve_line_exact<F, R>(n, (R)a.kappa, cp, ipm1, io);
+            solve_line_exact<M, R>(n, (R)a.kappa, cp, ipm1, io);
         }
     }
     if (KIND == K_Z) norm_finalize(acc.value(), a);
@@ -530,6 +639,7 @@ template <class F, typename R, int B, int W> struct TileIO {
     V *ring, *otile;
     int N, n, lane, nvalid, s0, limit, issued, ready;
     Acc<R> *acc;
+    R csum;  // |phi|^2 of the chunk being written (added to acc per chunk)
     __device__ __forceinline__ void issue() {
         const int pb = s0 + issued * B;
 #pragma unroll 4
@@ -559,12 +669,14 @@ template <class F, typename R, int B, int W> struct TileIO {
         while (issued <= c + kRingChunks - 2 && s0 + issued * B < limit) issue();
     }
     __device__ __forceinline__ V val(int p) const { return ring[lane * RS + ((p - s0) & (RL - 1))]; }
-    __device__ __forceinline__ void put(int, int q, V v) const {
+    __device__ __forceinline__ void put(int, int q, V v) {
         otile[lane * OS + q] = v;
-        if (lane < nvalid) acc->add(F::abs2(v));
+        csum += F::abs2(v);
     }
     // Write positions t0 .. t0+count-1 of the 32 lines back to global memory.
-    __device__ __forceinline__ void flush(int t0, int count) const {
+    __device__ __forceinline__ void flush(int t0, int count) {
+        if (lane < nvalid) acc->add(csum);
+        csum = R(0);
         __syncwarp();
         if (count == B) {
 #pragma unroll 4
@@ -607,6 +719,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_contig_kernel(SweepA
         io.lane = lane;
         io.nvalid = (int)min(32LL, a.n_lines - L0);
         io.acc = &acc;
+        io.csum = R(0);
         const int seg = blockIdx.y;
         if (lane < io.nvalid) {
             if (seg == 0) io.out0[(long long)lane * a.N] = F::zero();

@@ -33,21 +33,30 @@ static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaS
     }
 }
 
-template <class F, typename R, int W, int KIND>
-static cudaError_t launch_lines_w(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
-    using V = typename F::V;
+template <class F, typename R, int W, int KIND, int LPT>
+static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    using V = typename LinesPerThread<F, LPT>::M::V;
     const unsigned threads = (unsigned)L.threads;
-    const dim3 grid((unsigned)((a.n_lines + threads - 1) / threads), (unsigned)a.n_seg);
+    const long long units = (a.n_lines + LPT - 1) / LPT;
+    const dim3 grid((unsigned)((units + threads - 1) / threads), (unsigned)a.n_seg);
     const size_t smem = W > 0 ? column_ring_bytes<V>(threads) : 0;
     static int attr = 0;  // largest dynamic shared memory opted in so far
     if ((int)smem > attr && smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_lines_kernel<F, R, W, KIND>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_lines_kernel<F, R, W, KIND, LPT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = (int)smem;
     }
-    sweep_lines_kernel<F, R, W, KIND><<<grid, threads, smem, s>>>(a);
+    sweep_lines_kernel<F, R, W, KIND, LPT><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <class F, typename R, int W, int KIND>
+static cudaError_t launch_lines_w(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    if constexpr (sizeof(typename F::V) <= 8) {
+        if (L.lpt == 2) return launch_lines_wl<F, R, W, KIND, 2>(L, a, s);
+    }
+    return launch_lines_wl<F, R, W, KIND, 1>(L, a, s);
 }
 
 template <class F, typename R, int KIND>

@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SHAPE = (37, 29, 41)          # every axis spans several chunks plus a ragged tail
+EVEN = (36, 30, 42)           # even sizes: the strided sweeps pair adjacent lines per thread
 D = (0.31, 0.27, 0.22)
 OMEGA = (1.0, 1.4, 2.0)
 OBS = ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z")
@@ -65,14 +66,15 @@ def test_single_stage_fp64(stage, realtime):
     assert rel_max(got, ref) <= 1e-13
 
 
+@pytest.mark.parametrize("shape", [SHAPE, EVEN])
 @pytest.mark.parametrize("window", [0, 4, 8, 16])
 @pytest.mark.parametrize("realtime", [False, True])
-def test_every_window_matches_oracle_step(window, realtime):
+def test_every_window_matches_oracle_step(window, realtime, shape):
     """The windowed backward sweep (every admissible window) and the exact
     two-pass form give the oracle's step."""
     dt, g = 0.004, 12.0
-    psi0 = inputs.random_field(SHAPE, seed=5)
-    gp = make(SHAPE, D, dt, OMEGA, g)
+    psi0 = inputs.random_field(shape, seed=5)
+    gp = make(shape, D, dt, OMEGA, g)
     mode = 1 if realtime else 0
     try:
         gp.set_window(window)
@@ -86,6 +88,38 @@ def test_every_window_matches_oracle_step(window, realtime):
     ref = psi0.copy()
     oracle.step(ref, D, dt, OMEGA, g, realtime, 3)
     assert rel_max(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [SHAPE, EVEN])
+@pytest.mark.parametrize("window", [4, 8, 16])
+@pytest.mark.parametrize("realtime", [False, True])
+def test_every_window_fp32(window, realtime, shape):
+    dt, g = 0.004, 12.0
+    psi0 = inputs.random_field(shape, seed=6).astype(np.complex64)
+    gp = make(shape, D, dt, OMEGA, g, "f32")
+    gp.set_window(window)
+    gp.set_psi(psi0)
+    (gp.step_real if realtime else gp.step_imag)(3)
+    ref = psi0.astype(np.complex128)
+    oracle.step(ref, D, dt, OMEGA, g, realtime, 3)
+    assert rel_max(gp.get_psi().astype(np.complex128), ref) <= 2e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+@pytest.mark.parametrize("realtime", [False, True])
+def test_kick_large_arguments(prec, tol, realtime):
+    """A stiff trap and a large g push the kick arguments dt V and dt g |psi|^2
+    past the range of the short series, onto the exp / sincos fallback."""
+    shape, d, dt, omega, g = (30, 28, 26), (0.3, 0.3, 0.3), 0.002, (6.0, 5.0, 4.0), 3000.0
+    psi0 = inputs.random_field(shape, seed=17) * 2.0
+    if prec == "f32":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    gp = make(shape, d, dt, omega, g, prec)
+    gp.set_psi(psi0.astype(np.complex64) if prec == "f32" else psi0)
+    (gp.step_real if realtime else gp.step_imag)(3)
+    ref = psi0.copy()
+    oracle.step(ref, d, dt, omega, g, realtime, 3)
+    assert rel_max(gp.get_psi().astype(np.complex128), ref) <= tol
 
 
 @pytest.mark.parametrize("shape", [(3, 3, 3), (3, 4, 5), (5, 3, 4), (4, 5, 3), (6, 7, 8),
@@ -109,16 +143,17 @@ def test_edge_sizes(shape, realtime):
         assert rel_max(got, ref) <= 1e-12, (shape, window)
 
 
+@pytest.mark.parametrize("shape", [SHAPE, EVEN])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("seg", [1, 7, 16, 17, 33, 100])
-def test_segment_lengths(seg, prec):
+def test_segment_lengths(seg, prec, shape):
     """Lines cut into segments of any length (one thread each, forward sweep
     warmed up over W+1 nodes) give the oracle's step."""
     dt, g = 0.004, 12.0
-    psi0 = inputs.random_field(SHAPE, seed=31)
+    psi0 = inputs.random_field(shape, seed=31)
     if prec == "f32":
         psi0 = psi0.astype(np.complex64).astype(np.complex128)
-    gp = make(SHAPE, D, dt, OMEGA, g, prec)
+    gp = make(shape, D, dt, OMEGA, g, prec)
     for ax in range(3):
         gp.set_segments(ax, seg)
     gp.set_psi(psi0.astype(np.complex64) if prec == "f32" else psi0)
