@@ -640,15 +640,31 @@ template <class F, typename R, int B, int W> struct TileIO {
     int N, n, lane, nvalid, s0, limit, issued, ready;
     Acc<R> *acc;
     R csum;  // |phi|^2 of the chunk being written (added to acc per chunk)
+    // Per-lane constants of the cooperative copies: lane copies element e of
+    // lines qb, qb + LPI, qb + 2 LPI, ... (its first `nit` of them are valid).
+    int e, qb, nit;
+    const V *src_lane;  // in0 + qb * N + 1 + e
+    V *dst_lane;        // ring + qb * RS
+    __device__ __forceinline__ void setup() {
+        e = lane % B;
+        qb = lane / B;
+        nit = qb < nvalid ? (nvalid - qb + LPI - 1) / LPI : 0;
+        src_lane = in0 + (long long)qb * N + 1 + e;
+        dst_lane = ring + qb * RS;
+    }
     __device__ __forceinline__ void issue() {
         const int pb = s0 + issued * B;
+        const int p = pb + e;
+        const bool pos_ok = p >= 0 && p < n;
+        const int ro = (issued * B + e) & (RL - 1);
+        const V *src = src_lane + pb;
+        V *dst = dst_lane + ro;
 #pragma unroll 4
         for (int it = 0; it < B; ++it) {
-            const int q = it * LPI + lane / B, e = lane % B;
-            const int p = pb + e;
-            const bool ok = q < nvalid && p >= 0 && p < n;
-            cp_async<sizeof(V)>(ring + q * RS + ((p - s0) & (RL - 1)),
-                                ok ? in0 + (long long)q * N + p + 1 : in0, ok);
+            const bool ok = pos_ok && it < nit;
+            cp_async<sizeof(V)>(dst, ok ? src : in0, ok);
+            src += (long long)LPI * N;
+            dst += LPI * RS;
         }
         cp_async_commit();
         ++issued;
@@ -679,14 +695,17 @@ template <class F, typename R, int B, int W> struct TileIO {
         csum = R(0);
         __syncwarp();
         if (count == B) {
+            V *dst = out0 + (long long)qb * N + t0 + 1 + e;
+            const V *src = otile + qb * OS + e;
 #pragma unroll 4
             for (int it = 0; it < B; ++it) {
-                const int q = it * LPI + lane / B, e = lane % B;
-                if (q < nvalid) out0[(long long)q * N + t0 + 1 + e] = otile[q * OS + e];
+                if (it < nit) *dst = *src;
+                dst += (long long)LPI * N;
+                src += LPI * OS;
             }
         } else {
             for (int q = 0; q < nvalid; ++q)
-                for (int e = lane; e < count; e += 32) out0[(long long)q * N + t0 + 1 + e] = otile[q * OS + e];
+                for (int ee = lane; ee < count; ee += 32) out0[(long long)q * N + t0 + 1 + ee] = otile[q * OS + ee];
         }
         __syncwarp();
     }
@@ -720,6 +739,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_contig_kernel(SweepA
         io.nvalid = (int)min(32LL, a.n_lines - L0);
         io.acc = &acc;
         io.csum = R(0);
+        io.setup();
         const int seg = blockIdx.y;
         if (lane < io.nvalid) {
             if (seg == 0) io.out0[(long long)lane * a.N] = F::zero();
