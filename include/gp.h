@@ -177,7 +177,9 @@ gp_status gp_set_stream(gp_handle h, void *cuda_stream);
 gp_status gp_sync(gp_handle h);
 
 /* Window of the windowed back substitution per axis for imaginary (mode 0)
- * or real (mode 1) time; 0 means the exact two-pass solve is used. */
+ * or real (mode 1) time; 0 means the exact two-pass solve is used.  By
+ * default FP32 fields use the smallest admissible window and FP64 fields the
+ * exact solve (FP64 arithmetic, not memory, bounds the FP64 forms). */
 gp_status gp_get_window(gp_handle h, int mode, int window[3]);
 
 /* Override the window of every axis and mode: -1 restores the automatic

@@ -213,7 +213,11 @@ gp_status build_coefficients(gp_handle h) {
                     break;
                 }
             }
-            cs.window = cs.min_window;
+            // FP64 on this part runs at a small fraction of its FP32 rate, so
+            // the FP64 forms are ALU-bound: the exact two-pass solve (fewer
+            // flops, twice the bytes) is faster there.  FP32 is bandwidth-bound
+            // and takes the windowed single-pass solve.
+            cs.window = f32 ? cs.min_window : 0;
             for (int t = 0; t < n; ++t) {
                 for (int which = 0; which < 2; ++which) {
                     const std::complex<double> v = which == 0 ? cp[t] : ip[t];
@@ -261,6 +265,12 @@ gp_status build_coefficients(gp_handle h) {
                 cs.window = ok ? h->forced_window : cs.window;
             }
     }
+    // a window the new dt no longer admits falls back to the exact solve
+    for (int mode = 0; mode < modes_of(h); ++mode)
+        for (int ax = 0; ax < 3; ++ax) {
+            CoefSet &cs = h->coef[mode][ax];
+            if (cs.window > 0 && (cs.min_window == 0 || cs.window < cs.min_window)) cs.window = 0;
+        }
     return GP_OK;
 }
 
@@ -433,12 +443,13 @@ void segments(gp_handle h, int ax, int window, long long lines, int *seg_len, in
     if (window > 0) {
         if (h->seg_override[ax] > 0) {
             len = std::min(n, h->seg_override[ax]);
+        } else if (ax == 2 && h->contiguous_z) {
+            len = n;  // warp-tiled stride-1 axis: whole lines (measured best)
         } else {
-            const long long target = 152LL * 448 * 2;  // ~2 waves of resident threads
-            long long want = (target + lines - 1) / lines;
-            const long long most = std::max(1, n / (4 * chunk));
-            want = std::max(1LL, std::min(want, most));
-            len = (int)((n + want - 1) / want);
+            // about 128 nodes per segment (measured best on the strided axes),
+            // rounded to whole chunks
+            const int want = std::max(1, (n + 127) / 128);
+            len = (n + want - 1) / want;
             len = (len + chunk - 1) / chunk * chunk;
             len = std::min(len, n);
         }
@@ -790,7 +801,7 @@ gp_status gp_set_window(gp_handle h, int window) {
     for (int mode = 0; mode < modes_of(h); ++mode)
         for (int ax = 0; ax < 3; ++ax) {
             CoefSet &cs = h->coef[mode][ax];
-            cs.window = window < 0 ? cs.min_window : window;
+            cs.window = window >= 0 ? window : (h->prec == GP_F32 ? cs.min_window : 0);
         }
     h->forced_window = window;
     return GP_OK;
