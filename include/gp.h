@@ -207,8 +207,37 @@ gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]);
  * that queues work on the handle. */
 gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale);
 
+/* Observables of a caller-owned device psi, computed without allocating any
+ * device memory.  No counterpart in the paper: it serves callers that cannot
+ * call cudaMalloc -- a host framework that owns all device memory through its
+ * own pool, or a latency-critical loop that must not pay cudaMalloc's
+ * implicit device synchronisation.  (A handle cannot serve them: gp_create
+ * allocates.)
+ *   dev_psi  device array of nx*ny*nz elements in the layout above, of the
+ *            type given by prec / field; read only; values are multiplied by
+ *            `scale` as they are read.
+ *   dev_out  device array of 16 doubles written by the kernel: [0..8] the raw
+ *            sums (|psi|^2, V|psi|^2, |psi|^4, x^2|psi|^2, y^2|psi|^2,
+ *            z^2|psi|^2, and the squared differences along x, y, z), [9..14]
+ *            norm, mu, energy, rms_x, rms_y, rms_z as in gp_obs, [15] 1.0 if
+ *            all of them are finite, else 0.0.
+ *   cuda_stream  stream to queue on (NULL: legacy default stream); the call
+ *            returns without synchronising.
+ * The reduction's block partials and completion counter live in one
+ * fixed-size static device array (about 576 KB, held by every GPU that loads
+ * the library until the process exits), so ny*nz may be at most 2,097,152;
+ * larger planes return GP_ERR_ARG with a message in gp_last_error(NULL).  The
+ * first call on each device looks the array's device address up (make it
+ * before any stream capture on that device).  All calls share the array:
+ * calls whose work overlaps on the GPU race and give undefined results.
+ * Other arguments are checked like gp_create's. */
+gp_status gp_observables_noalloc(const void *dev_psi, gp_grid grid, gp_precision prec,
+                                 gp_field field, double gamma, double nu, double lambda, double g,
+                                 double scale, double *dev_out, void *cuda_stream);
+
 /* Last error message for this handle (or for the calling thread's last
- * failed create when h is NULL).  Never NULL. */
+ * failed create, or failed gp_observables_noalloc, when h is NULL).  Never
+ * NULL. */
 const char *gp_last_error(gp_handle h);
 
 /* Library version string. */

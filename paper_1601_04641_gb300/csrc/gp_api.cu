@@ -45,6 +45,13 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+// Error message of a failed call that has no handle (read by gp_last_error(NULL)).
+void gpcn::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
+namespace {
+
 // Device scalars of a handle.
 enum Scalar { S_SCALE = 0, S_ONE = 1, S_NORM_SWEEP = 2, S_NORM_INIT = 3, S_COUNT = 8 };
 

@@ -98,6 +98,7 @@ enum ObsSlot {
 };
 
 int observables_blocks(const FieldArgs &a);
+void set_thread_error(const char *msg);
 constexpr int kReduceThreads = 256;
 
 }  // namespace gpcn
