@@ -201,6 +201,12 @@ gp_status gp_set_segments(gp_handle h, int axis, int seg_len);
  * real-time (mode 1) step will use. */
 gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]);
 
+/* Steps per CUDA graph: gp_step_imag / gp_step_real capture blocks of this
+ * many steps into a graph once and replay it (default 16; 0 or 1 launches
+ * kernel by kernel).  With tracking on, blocks are track_every steps long.
+ * Changing g, dt, the window, threads or segments re-captures. */
+gp_status gp_set_graph_block(gp_handle h, int steps);
+
 /* Device pointer of the buffer that holds the current psi, and whether a
  * renormalisation factor is still pending on it (the value is then psi
  * times that factor; gp_get_psi applies it).  Valid until the next call

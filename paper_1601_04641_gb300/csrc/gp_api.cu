@@ -9,6 +9,7 @@
 #include <complex>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -102,6 +103,11 @@ struct gp_handle_s {
     double *d_track = nullptr;
     std::vector<long long> track_step;
     std::vector<double> track_t;
+    // CUDA graphs of blocks of steps, replayed on the handle's stream
+    int graph_block = 16;              // steps per graph (0: launch kernel by kernel)
+    cudaStream_t cap_stream = nullptr; // private stream used only for capture
+    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+    double *d_obs_graph = nullptr;     // tracking record written inside a graph
     std::string err;
 };
 
@@ -346,6 +352,9 @@ void release(gp_handle h) {
     cudaFree(h->d_partials);
     cudaFree(h->d_counter);
     cudaFree(h->d_track);
+    cudaFree(h->d_obs_graph);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaGetLastError();
     delete h;
 }
@@ -534,10 +543,65 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     return GP_OK;
 }
 
-gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
-    if (nsteps < 0) return fail(h, GP_ERR_ARG, "nsteps < 0");
-    if (realtime && h->field != GP_COMPLEX)
-        return fail(h, GP_ERR_STATE, "real-time steps need a GP_COMPLEX field");
+void drop_graphs(gp_handle h) {
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+// One block of `g` steps as a CUDA graph (captured on first use, keyed by the
+// state the captured launches depend on: step kind, block length, which
+// buffer holds psi, whether a renormalisation factor is pending, and whether
+// the block ends with a tracking record), then launched on the handle's
+// stream.  Returns GP_STATE if capture is not possible, so the caller can
+// launch the block kernel by kernel instead.
+gp_status run_graph_block(gp_handle h, int g, bool realtime, bool with_obs) {
+    const auto key = std::make_tuple(realtime ? 1 : 0, g, h->cur, h->scale_pending ? 1 : 0, with_obs ? 1 : 0);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        if (with_obs && !h->d_obs_graph && cudaMalloc(&h->d_obs_graph, O_COUNT * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        const int cur0 = h->cur;
+        const bool pend0 = h->scale_pending;
+        cudaStream_t user = h->stream;
+        if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        h->stream = h->cap_stream;
+        gp_status st = GP_OK;
+        for (int s = 0; s < g && st == GP_OK; ++s)
+            for (int stage = 0; stage < 3 && st == GP_OK; ++stage) st = run_stage(h, stage, realtime);
+        if (st == GP_OK && with_obs) st = queue_observables(h, h->d_obs_graph);
+        h->stream = user;
+        h->cur = cur0;
+        h->scale_pending = pend0;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        const bool ok = st == GP_OK && ec == cudaSuccess && graph &&
+                        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        it = h->graphs.emplace(key, exec).first;
+    }
+    GP_CK(h, cudaGraphLaunch(it->second, h->stream));
+    // the state the g steps leave behind
+    if ((3 * g) % 2) h->cur ^= 1;
+    h->scale_pending = !realtime;
+    return GP_OK;
+}
+
+// Steps launched kernel by kernel (with tracking records queued in between).
+gp_status run_eager(gp_handle h, int nsteps, bool realtime) {
     for (int s = 0; s < nsteps; ++s) {
         for (int stage = 0; stage < 3; ++stage) {
             gp_status st = run_stage(h, stage, realtime);
@@ -554,6 +618,45 @@ gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
         }
     }
     return GP_OK;
+}
+
+gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
+    if (nsteps < 0) return fail(h, GP_ERR_ARG, "nsteps < 0");
+    if (realtime && h->field != GP_COMPLEX)
+        return fail(h, GP_ERR_STATE, "real-time steps need a GP_COMPLEX field");
+    // Whole blocks as graphs.  With tracking on, a block is track_every steps
+    // ending on a tracking step (its record is copied out of the graph's
+    // slot); steps up to the next tracking step go kernel by kernel.
+    while (nsteps > 1 && h->graph_block > 1) {
+        const bool tracking = h->track_every > 0 && h->track_count < h->track_cap;
+        int g = std::min(nsteps, h->graph_block);
+        if (tracking) {
+            const int lead = (int)((h->track_every - h->step % h->track_every) % h->track_every);
+            if (lead > 0) {
+                const int n = std::min(lead, nsteps);
+                gp_status st = run_eager(h, n, realtime);
+                if (st != GP_OK) return st;
+                nsteps -= n;
+                continue;
+            }
+            if (h->track_every < 2 || h->track_every > h->graph_block || nsteps < h->track_every) break;
+            g = h->track_every;
+        }
+        const gp_status st = run_graph_block(h, g, realtime, tracking);
+        if (st == GP_ERR_STATE) break;  // not capturable here: launch kernel by kernel
+        if (st != GP_OK) return st;
+        h->step += g;
+        h->t += g * h->dt;
+        nsteps -= g;
+        if (tracking) {
+            GP_CK(h, cudaMemcpyAsync(h->d_track + (size_t)h->track_count * O_COUNT, h->d_obs_graph,
+                                     O_COUNT * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            h->track_step.push_back(h->step);
+            h->track_t.push_back(h->t);
+            h->track_count += 1;
+        }
+    }
+    return run_eager(h, nsteps, realtime);
 }
 
 gp_status queue_observables(gp_handle h, double *dst) {
@@ -660,6 +763,7 @@ gp_status gp_set_g(gp_handle h, double g) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!std::isfinite(g)) return fail(h, GP_ERR_ARG, "g must be finite");
+    if (g != h->g) drop_graphs(h);
     h->g = g;
     return GP_OK;
 }
@@ -668,6 +772,7 @@ gp_status gp_set_dt(gp_handle h, double dt) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!finite_pos(dt)) return fail(h, GP_ERR_ARG, "dt must be finite and > 0");
+    drop_graphs(h);
     h->dt = dt;
     return build_coefficients(h);
 }
@@ -811,6 +916,7 @@ gp_status gp_set_window(gp_handle h, int window) {
             cs.window = window >= 0 ? window : (h->prec == GP_F32 ? cs.min_window : 0);
         }
     h->forced_window = window;
+    drop_graphs(h);
     return GP_OK;
 }
 
@@ -819,6 +925,7 @@ gp_status gp_set_threads(gp_handle h, int axis, int threads) {
     if (threads < 32 || threads > 256 || threads % 32)
         return fail(h, GP_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
     h->threads[axis] = threads;
+    drop_graphs(h);
     return GP_OK;
 }
 
@@ -826,6 +933,7 @@ gp_status gp_set_segments(gp_handle h, int axis, int seg_len) {
     if (!h || axis < 0 || axis > 2) return fail(h, GP_ERR_ARG, "bad axis");
     if (seg_len < 0) return fail(h, GP_ERR_ARG, "seg_len must be >= 0");
     h->seg_override[axis] = seg_len;
+    drop_graphs(h);
     return GP_OK;
 }
 
@@ -841,6 +949,13 @@ gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
     if (!h || !ptr) return fail(h, GP_ERR_ARG, "bad arguments");
     *ptr = h->buf[h->cur];
     if (pending_scale) *pending_scale = h->scale_pending ? 1 : 0;
+    return GP_OK;
+}
+
+gp_status gp_set_graph_block(gp_handle h, int steps) {
+    if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    if (steps < 0 || steps > 1024) return fail(h, GP_ERR_ARG, "steps must be in [0, 1024]");
+    h->graph_block = steps;
     return GP_OK;
 }
 

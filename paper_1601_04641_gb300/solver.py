@@ -160,5 +160,8 @@ class GP:
         self._ck(self.lib.gp_get_segments(self.h, int(mode), a, b))
         return tuple(a), tuple(b)
 
+    def set_graph_block(self, steps):
+        self._ck(self.lib.gp_set_graph_block(self.h, int(steps)))
+
     def set_threads(self, axis, threads):
         self._ck(self.lib.gp_set_threads(self.h, int(axis), int(threads)))
