@@ -255,9 +255,11 @@ def timed_region(torch, res, steps, dist):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     step(steps)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     e1.synchronize()
     torch.cuda.synchronize()
     if dist:

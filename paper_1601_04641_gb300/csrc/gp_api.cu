@@ -646,7 +646,7 @@ gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
         if (st == GP_ERR_STATE) break;  // not capturable here: launch kernel by kernel
         if (st != GP_OK) return st;
         h->step += g;
-        h->t += g * h->dt;
+        for (int k = 0; k < g; ++k) h->t += h->dt;  // same rounding as step by step
         nsteps -= g;
         if (tracking) {
             GP_CK(h, cudaMemcpyAsync(h->d_track + (size_t)h->track_count * O_COUNT, h->d_obs_graph,
