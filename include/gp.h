@@ -188,6 +188,14 @@ gp_status gp_get_window(gp_handle h, int mode, int window[3]);
  * under an eighth of the unit roundoff for this dt). */
 gp_status gp_set_window(gp_handle h, int window);
 
+/* Window of one axis in both modes (-1 automatic, 0 exact, 4 / 8 / 16 if
+ * admissible for that axis). */
+gp_status gp_set_axis_window(gp_handle h, int axis, int window);
+
+/* Two adjacent lines per thread on the strided axes (1, the default, where
+ * the layout allows it) or one (0).  The arithmetic per line is the same. */
+gp_status gp_set_pair_lines(gp_handle h, int on);
+
 /* Threads per block of the line-solve kernel of one axis (multiple of 32,
  * 32..256). */
 gp_status gp_set_threads(gp_handle h, int axis, int threads);
@@ -240,6 +248,44 @@ gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale);
 gp_status gp_observables_noalloc(const void *dev_psi, gp_grid grid, gp_precision prec,
                                  gp_field field, double gamma, double nu, double lambda, double g,
                                  double scale, double *dev_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------ batch
+ * Many independent condensates -- each with its own grid, spacings, dt,
+ * trap and g (SURVEY's batched form; the paper runs one condensate per
+ * program) -- advanced in imaginary time together: each step is three
+ * launches that cover all active instances (per-instance arguments, norm
+ * partials and counters), blocks of steps are replayed from CUDA graphs, and
+ * gp_batch_run_imag_until drops converged instances from the launches.  All
+ * instances share one precision and field; each axis uses one window for the
+ * whole batch (the largest of the instances' smallest admissible windows;
+ * the exact solve in FP64).  psi of instance i has the layout above. */
+typedef struct gp_batch_s *gp_batch;
+
+gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const double *dt,
+                          const double *gamma, const double *nu, const double *lambda,
+                          const double *g, gp_precision prec, gp_field field, void *cuda_stream);
+void gp_batch_destroy(gp_batch b);
+/* Every instance <- its normalised Gaussian (as gp_init_gaussian). */
+gp_status gp_batch_init_gaussian(gp_batch b);
+gp_status gp_batch_set_psi(gp_batch b, int i, const void *psi, int on_device);
+gp_status gp_batch_get_psi(gp_batch b, int i, void *psi, int on_device);
+/* nsteps imaginary-time steps of every instance. */
+gp_status gp_batch_step_imag(gp_batch b, int nsteps);
+/* Observables of every instance into out[0..n-1] (synchronises). */
+gp_status gp_batch_observables(gp_batch b, gp_obs *out);
+/* Imaginary time until |mu(n) - mu(n - check_every)| < mu_tol per instance
+ * (checked every check_every steps; converged instances stop stepping), or
+ * max_steps.  steps_taken[i] (may be NULL) receives each instance's steps. */
+gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, int max_steps,
+                                  int *steps_taken);
+/* The window per axis used for the whole batch. */
+gp_status gp_batch_get_window(gp_batch b, int window[3]);
+/* Segment length and count per axis of instance i. */
+gp_status gp_batch_get_segments(gp_batch b, int i, int seg_len[3], int n_seg[3]);
+/* Steps per CUDA graph (default 16; 0 or 1: launch by launch). */
+gp_status gp_batch_set_graph_block(gp_batch b, int steps);
+/* Last error of the batch (NULL: as gp_last_error(NULL)). */
+const char *gp_batch_last_error(gp_batch b);
 
 /* Last error message for this handle (or for the calling thread's last
  * failed create, or failed gp_observables_noalloc, when h is NULL).  Never

@@ -57,12 +57,28 @@ SIGNATURES = {
     "gp_sync": (_i, [Handle]),
     "gp_get_window": (_i, [Handle, _i, ctypes.POINTER(_i)]),
     "gp_set_window": (_i, [Handle, _i]),
+    "gp_set_axis_window": (_i, [Handle, _i, _i]),
+    "gp_set_pair_lines": (_i, [Handle, _i]),
     "gp_set_threads": (_i, [Handle, _i, _i]),
     "gp_set_segments": (_i, [Handle, _i, _i]),
     "gp_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_set_graph_block": (_i, [Handle, _i]),
     "gp_psi_device_ptr": (_i, [Handle, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
     "gp_observables_noalloc": (_i, [_vp, Grid, _i, _i, _d, _d, _d, _d, _d, _vp, _vp]),
+    "gp_batch_create": (_i, [ctypes.POINTER(Handle), _i, ctypes.POINTER(Grid), ctypes.POINTER(_d),
+                             ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
+                             _i, _i, _vp]),
+    "gp_batch_destroy": (None, [Handle]),
+    "gp_batch_init_gaussian": (_i, [Handle]),
+    "gp_batch_set_psi": (_i, [Handle, _i, _vp, _i]),
+    "gp_batch_get_psi": (_i, [Handle, _i, _vp, _i]),
+    "gp_batch_step_imag": (_i, [Handle, _i]),
+    "gp_batch_observables": (_i, [Handle, ctypes.POINTER(Obs)]),
+    "gp_batch_run_imag_until": (_i, [Handle, _d, _i, _i, ctypes.POINTER(_i)]),
+    "gp_batch_get_window": (_i, [Handle, ctypes.POINTER(_i)]),
+    "gp_batch_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "gp_batch_set_graph_block": (_i, [Handle, _i]),
+    "gp_batch_last_error": (ctypes.c_char_p, [Handle]),
     "gp_last_error": (ctypes.c_char_p, [Handle]),
     "gp_version": (ctypes.c_char_p, []),
 }
@@ -94,7 +110,8 @@ def load():
     return _lib
 
 
-def check(status, handle=None):
+def check(status, handle=None, batch=False):
     if status != GP_OK:
-        msg = load().gp_last_error(handle)
+        lib = load()
+        msg = lib.gp_batch_last_error(handle) if batch else lib.gp_last_error(handle)
         raise GPError(status, msg.decode() if msg else "")

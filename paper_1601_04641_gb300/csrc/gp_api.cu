@@ -2,6 +2,7 @@
 // argument checks, the FP64 precomputation of the CN recursion coefficients,
 // and the per-step launch sequence (kick + x sweep, y sweep, z sweep + norm).
 #include "gp.h"
+#include "gp_host.h"
 #include "gp_internal.h"
 
 #include <algorithm>
@@ -21,6 +22,30 @@ cudaError_t launch_sweep_f32_rt(const SweepLaunch &, const SweepArgs &, cudaStre
 cudaError_t launch_sweep_f64_ir(const SweepLaunch &, const SweepArgs &, cudaStream_t);
 cudaError_t launch_sweep_f64_ic(const SweepLaunch &, const SweepArgs &, cudaStream_t);
 cudaError_t launch_sweep_f64_rt(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+
+cudaError_t launch_sweep_f32_ir_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
+cudaError_t launch_sweep_f32_ic_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
+cudaError_t launch_sweep_f32_rt_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
+cudaError_t launch_sweep_f64_ir_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
+cudaError_t launch_sweep_f64_ic_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
+cudaError_t launch_sweep_f64_rt_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
+
+cudaError_t launch_sweep_batch(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    if (L.prec == P_F32) {
+        switch (L.form) {
+        case F_IMAG_REAL: return launch_sweep_f32_ir_batch(L, b, s);
+        case F_IMAG_CPLX: return launch_sweep_f32_ic_batch(L, b, s);
+        case F_REALTIME: return launch_sweep_f32_rt_batch(L, b, s);
+        }
+    } else {
+        switch (L.form) {
+        case F_IMAG_REAL: return launch_sweep_f64_ir_batch(L, b, s);
+        case F_IMAG_CPLX: return launch_sweep_f64_ic_batch(L, b, s);
+        case F_REALTIME: return launch_sweep_f64_rt_batch(L, b, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_sweep(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     if (L.prec == P_F32) {
@@ -56,17 +81,6 @@ namespace {
 // Device scalars of a handle.
 enum Scalar { S_SCALE = 0, S_ONE = 1, S_NORM_SWEEP = 2, S_NORM_INIT = 3, S_COUNT = 8 };
 
-struct KickTables {
-    size_t off[3] = {0, 0, 0};  // byte offsets of exp(-dt V_a) per axis (imaginary time)
-};
-
-struct CoefSet {
-    size_t off_cp = 0, off_ip = 0;  // byte offsets into the coefficient buffer
-    int window = 0;                  // chosen window (0: exact two-pass)
-    int min_window = 0;              // smallest admissible window (0: none)
-    double cp_max = 0.0;
-};
-
 }  // namespace
 
 struct gp_handle_s {
@@ -83,8 +97,8 @@ struct gp_handle_s {
     cudaStream_t stream = nullptr;
     char *d_coef = nullptr;
     size_t coef_bytes = 0;
-    CoefSet coef[2][3];
-    KickTables kick;
+    Tables tab;                         // offsets of the coefficient tables in d_coef
+    int window[2][3] = {{0, 0, 0}, {0, 0, 0}};  // window in use per mode and axis
     int forced_window = -1;
     double *d_scal = nullptr;
     double *d_obs = nullptr;
@@ -149,113 +163,36 @@ gp_status check_args(gp_grid grid, double dt, double gamma, double nu, double la
     return GP_OK;
 }
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
 int modes_of(gp_handle h) { return h->field == GP_COMPLEX ? 2 : 1; }
 
-// FP64 Thomas coefficients of the CN matrix (-c, 1+2c, -c) on n interior
-// nodes: den[0] = 1+2c, den[t] = 1+2c + c cp[t-1], ip = 1/den, cp = -c ip.
-// The inverse pivot is returned as its deviation from one,
-// ipm1 = ip - 1 = (1 - den) / den, which the kernels apply as u + u ipm1.
-void thomas_coefficients(std::complex<double> c, int n, std::vector<std::complex<double>> &cp,
-                         std::vector<std::complex<double>> &ipm1) {
-    cp.assign(n, 0.0);
-    ipm1.assign(n, 0.0);
-    for (int t = 0; t < n; ++t) {
-        const std::complex<double> excess = 2.0 * c + (t == 0 ? 0.0 : c * cp[t - 1]);  // den - 1
-        const std::complex<double> den = 1.0 + excess;
-        ipm1[t] = -excess / den;
-        cp[t] = -c / den;
+Geometry geom(gp_handle h) {
+    Geometry G;
+    for (int q = 0; q < 3; ++q) {
+        G.n[q] = h->n[q];
+        G.d[q] = h->d[q];
+        G.w[q] = h->w[q];
     }
+    G.dt = h->dt;
+    G.g = h->g;
+    return G;
 }
 
 // Build and upload the coefficient tables of both modes and all axes, and
 // pick the window of the windowed backward sweep for each.
 gp_status build_coefficients(gp_handle h) {
     const bool f32 = h->prec == GP_F32;
-    const size_t rsz = f32 ? sizeof(float) : sizeof(double);
-    const double eps = f32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
     std::vector<char> host;
-    size_t off = 0;
-    for (int mode = 0; mode < modes_of(h); ++mode) {
+    append_tables(geom(h), f32, modes_of(h), host, h->tab);
+    const size_t off = host.size();
+    for (int mode = 0; mode < modes_of(h); ++mode)
         for (int ax = 0; ax < 3; ++ax) {
-            const int n = h->n[ax] - 2;
-            const size_t esz = (mode == 1 ? 2 : 1) * rsz;
-            CoefSet &cs = h->coef[mode][ax];
-            cs.off_cp = off;
-            off = align_up(off + esz * n, 256);
-            cs.off_ip = off;
-            off = align_up(off + esz * n, 256);
+            const AxisTables &at = h->tab.ax[mode][ax];
+            int w = default_window(at, f32);
+            if (h->forced_window == 0 ||
+                (h->forced_window > 0 && at.min_window > 0 && h->forced_window >= at.min_window))
+                w = h->forced_window;
+            h->window[mode][ax] = w;
         }
-    }
-    for (int ax = 0; ax < 3; ++ax) {
-        h->kick.off[ax] = off;
-        off = align_up(off + rsz * h->n[ax], 256);
-    }
-    host.assign(off, 0);
-    // exp(-dt w^2 a^2 / 2) per node of each axis: the trap part of the
-    // imaginary-time kick factorises over the axes.
-    for (int ax = 0; ax < 3; ++ax) {
-        for (int i = 0; i < h->n[ax]; ++i) {
-            const double a = (i - 0.5 * (h->n[ax] - 1)) * h->d[ax];
-            const double v = std::exp(-h->dt * 0.5 * h->w[ax] * h->w[ax] * a * a);
-            char *dst = host.data() + h->kick.off[ax] + i * rsz;
-            if (f32) {
-                const float fv = (float)v;
-                std::memcpy(dst, &fv, sizeof(fv));
-            } else {
-                std::memcpy(dst, &v, sizeof(v));
-            }
-        }
-    }
-    for (int mode = 0; mode < modes_of(h); ++mode) {
-        for (int ax = 0; ax < 3; ++ax) {
-            const int n = h->n[ax] - 2;
-            const double kap = h->dt / (4.0 * h->d[ax] * h->d[ax]);
-            const std::complex<double> c = mode == 1 ? std::complex<double>(0.0, kap)
-                                                     : std::complex<double>(kap, 0.0);
-            std::vector<std::complex<double>> cp, ip;
-            thomas_coefficients(c, n, cp, ip);
-            CoefSet &cs = h->coef[mode][ax];
-            cs.cp_max = 0.0;
-            for (int t = 0; t < n - 1; ++t) cs.cp_max = std::max(cs.cp_max, std::abs(cp[t]));
-            cs.min_window = 0;
-            for (int w : {4, 8, 16}) {
-                if (std::pow(cs.cp_max, w + 1) <= eps / 8.0) {
-                    cs.min_window = w;
-                    break;
-                }
-            }
-            // FP64 on this part runs at a small fraction of its FP32 rate, so
-            // the FP64 forms are ALU-bound: the exact two-pass solve (fewer
-            // flops, twice the bytes) is faster there.  FP32 is bandwidth-bound
-            // and takes the windowed single-pass solve.
-            cs.window = f32 ? cs.min_window : 0;
-            for (int t = 0; t < n; ++t) {
-                for (int which = 0; which < 2; ++which) {
-                    const std::complex<double> v = which == 0 ? cp[t] : ip[t];
-                    char *dst = host.data() + (which == 0 ? cs.off_cp : cs.off_ip);
-                    if (mode == 1) {
-                        if (f32) {
-                            float pr[2] = {(float)v.real(), (float)v.imag()};
-                            std::memcpy(dst + t * 2 * rsz, pr, sizeof(pr));
-                        } else {
-                            double pr[2] = {v.real(), v.imag()};
-                            std::memcpy(dst + t * 2 * rsz, pr, sizeof(pr));
-                        }
-                    } else {
-                        if (f32) {
-                            float r = (float)v.real();
-                            std::memcpy(dst + t * rsz, &r, sizeof(r));
-                        } else {
-                            double r = v.real();
-                            std::memcpy(dst + t * rsz, &r, sizeof(r));
-                        }
-                    }
-                }
-            }
-        }
-    }
     if (h->d_coef && h->coef_bytes < off) {
         cudaFree(h->d_coef);
         h->d_coef = nullptr;
@@ -269,52 +206,16 @@ gp_status build_coefficients(gp_handle h) {
     }
     GP_CK(h, cudaMemcpyAsync(h->d_coef, host.data(), off, cudaMemcpyHostToDevice, h->stream));
     GP_CK(h, cudaStreamSynchronize(h->stream));
-    if (h->forced_window >= 0) {
-        for (int mode = 0; mode < modes_of(h); ++mode)
-            for (int ax = 0; ax < 3; ++ax) {
-                CoefSet &cs = h->coef[mode][ax];
-                const bool ok = h->forced_window == 0 ||
-                                (cs.min_window > 0 && h->forced_window >= cs.min_window);
-                cs.window = ok ? h->forced_window : cs.window;
-            }
-    }
-    // a window the new dt no longer admits falls back to the exact solve
-    for (int mode = 0; mode < modes_of(h); ++mode)
-        for (int ax = 0; ax < 3; ++ax) {
-            CoefSet &cs = h->coef[mode][ax];
-            if (cs.window > 0 && (cs.min_window == 0 || cs.window < cs.min_window)) cs.window = 0;
-        }
     return GP_OK;
 }
 
-long long sweep_lines(gp_handle h, int ax) {
-    const long long nx = h->n[0], ny = h->n[1], nz = h->n[2];
-    return ax == 0 ? ny * nz : ax == 1 ? nx * nz : nx * ny;
-}
+long long sweep_lines(gp_handle h, int ax) { return axis_lines(geom(h), ax); }
 
 size_t blocks_for(long long items, int threads) { return (size_t)((items + threads - 1) / threads); }
 
-FieldArgs field_args(gp_handle h) {
-    FieldArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.psi = h->buf[h->cur];
-    for (int ax = 0; ax < 3; ++ax) {
-        a.n[ax] = h->n[ax];
-        a.d[ax] = h->d[ax];
-        a.origin[ax] = -0.5 * (h->n[ax] - 1) * h->d[ax];
-        a.w[ax] = h->w[ax];
-        a.half_w2[ax] = 0.5 * h->w[ax] * h->w[ax];
-    }
-    a.g = h->g;
-    a.scale = h->d_scal + (h->scale_pending ? S_SCALE : S_ONE);
-    a.dV = h->d[0] * h->d[1] * h->d[2];
-    a.partials = h->d_partials;
-    a.counter = h->d_counter;
-    a.out = h->d_obs;
-    a.scale_out = h->d_scal + S_SCALE;
-    a.norm_out = h->d_scal + S_NORM_INIT;
-    a.sites = (long long)h->sites;
-    return a;
+FieldArgs handle_field_args(gp_handle h) {
+    return field_args(geom(h), h->buf[h->cur], h->d_scal + (h->scale_pending ? S_SCALE : S_ONE),
+                      h->d_partials, h->d_counter, h->d_obs, h->d_scal + S_SCALE, h->d_scal + S_NORM_INIT);
 }
 
 constexpr int kNormBlocks = 152 * 4;
@@ -323,7 +224,7 @@ gp_status alloc_scratch(gp_handle h) {
     // z sweep: at most one block per 32 (line, segment) threads, segments of >= 1 node
     size_t cap = kNormBlocks;
     cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32) * (size_t)(h->n[2] - 2));
-    FieldArgs fa = field_args(h);
+    FieldArgs fa = handle_field_args(h);
     cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
     if (cudaMalloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_scal, S_COUNT * sizeof(double)) != cudaSuccess ||
@@ -447,31 +348,10 @@ int lines_per_thread(gp_handle h, int ax) {
     return 2;
 }
 
-// Segments of one axis: enough (line, segment) threads to fill the GPU a
-// few times over, each segment a whole number of chunks.  The exact form
-// (window 0) solves whole lines.
-void segments(gp_handle h, int ax, int window, long long lines, int *seg_len, int *n_seg) {
-    const int n = h->n[ax] - 2;
-    const int lpt = lines_per_thread(h, ax);
-    lines /= lpt;
-    const int chunk = (h->elem * lpt >= 16) ? 8 : 16;
-    int len = n;
-    if (window > 0) {
-        if (h->seg_override[ax] > 0) {
-            len = std::min(n, h->seg_override[ax]);
-        } else if (ax == 2 && h->contiguous_z) {
-            len = n;  // warp-tiled stride-1 axis: whole lines (measured best)
-        } else {
-            // about 128 nodes per segment (measured best on the strided axes),
-            // rounded to whole chunks
-            const int want = std::max(1, (n + 127) / 128);
-            len = (n + want - 1) / want;
-            len = (len + chunk - 1) / chunk * chunk;
-            len = std::min(len, n);
-        }
-    }
-    *seg_len = std::max(1, len);
-    *n_seg = (n + *seg_len - 1) / *seg_len;
+// Segments of one axis (see choose_segments).
+void segments(gp_handle h, int ax, int window, int *seg_len, int *n_seg) {
+    choose_segments(geom(h), ax, window, lines_per_thread(h, ax), (int)h->elem, h->contiguous_z,
+                    h->seg_override[ax], seg_len, n_seg);
 }
 
 // One stage of a step: 0 = kick + x sweep, 1 = y sweep, 2 = z sweep + norm.
@@ -482,57 +362,16 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     L.kind = static_cast<Kind>(stage);
     const int mode = realtime ? 1 : 0;
     const int ax = stage;
-    const CoefSet &cs = h->coef[mode][ax];
-    L.window = cs.window;
+    L.window = h->window[mode][ax];
     L.threads = h->threads[ax];
     L.lpt = lines_per_thread(h, ax);
-    L.contiguous = (ax == 2 && h->contiguous_z && cs.window > 0) ? 1 : 0;
-
-    SweepArgs a;
-    std::memset(&a, 0, sizeof(a));
-    const long long nx = h->n[0], ny = h->n[1], nz = h->n[2];
-    a.psi = h->buf[h->cur];
-    a.psi_out = h->buf[h->cur ^ 1];
-    a.cp = h->d_coef + cs.off_cp;
-    a.ip = h->d_coef + cs.off_ip;
-    a.n_lines = sweep_lines(h, ax);
-    if (ax == 0) {
-        a.inner = ny * nz;
-        a.outer_stride = 0;
-        a.stride = ny * nz;
-    } else if (ax == 1) {
-        a.inner = nz;
-        a.outer_stride = ny * nz;
-        a.stride = nz;
-    } else {
-        a.inner = 1;
-        a.outer_stride = nz;
-        a.stride = 1;
-    }
-    a.N = h->n[ax];
-    segments(h, ax, L.window, a.n_lines, &a.seg_len, &a.n_seg);
-    a.kappa = h->dt / (4.0 * h->d[ax] * h->d[ax]);
-    a.scale = h->d_scal + (h->scale_pending ? S_SCALE : S_ONE);
-    if (!realtime) {
-        a.kick_ex = h->d_coef + h->kick.off[0];
-        a.kick_ey = h->d_coef + h->kick.off[1];
-        a.kick_ez = h->d_coef + h->kick.off[2];
-    }
-    a.dt = h->dt;
-    a.g = h->g;
-    for (int q = 0; q < 3; ++q) {
-        a.half_w2[q] = 0.5 * h->w[q] * h->w[q];
-        a.origin[q] = -0.5 * (h->n[q] - 1) * h->d[q];
-        a.d[q] = h->d[q];
-    }
-    a.nz = (int)nz;
-    a.ny = (int)ny;
-    a.partials = h->d_partials;
-    a.counter = h->d_counter;
-    a.norm_out = h->d_scal + S_NORM_SWEEP;
-    a.scale_out = h->d_scal + S_SCALE;
-    a.dV = h->d[0] * h->d[1] * h->d[2];
-    a.want_scale = realtime ? 0 : 1;
+    L.contiguous = (ax == 2 && h->contiguous_z && L.window > 0) ? 1 : 0;
+    int seg_len = 0, n_seg = 0;
+    segments(h, ax, L.window, &seg_len, &n_seg);
+    const SweepArgs a = sweep_args(geom(h), ax, realtime, h->buf[h->cur], h->buf[h->cur ^ 1], h->d_coef,
+                                   h->tab, seg_len, n_seg,
+                                   h->d_scal + (h->scale_pending ? S_SCALE : S_ONE), h->d_partials,
+                                   h->d_counter, h->d_scal + S_NORM_SWEEP, h->d_scal + S_SCALE);
     const int zthreads = L.contiguous ? 32 : L.threads;
     if (stage == 2 && blocks_for(a.n_lines, zthreads) * (size_t)a.n_seg > h->partial_cap)
         return fail(h, GP_ERR_STATE, "z sweep grid exceeds the partials buffer");
@@ -660,7 +499,7 @@ gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
 }
 
 gp_status queue_observables(gp_handle h, double *dst) {
-    FieldArgs a = field_args(h);
+    FieldArgs a = handle_field_args(h);
     a.out = dst;
     if ((size_t)observables_blocks(a) * 9 > h->partial_cap)
         return fail(h, GP_ERR_STATE, "observables grid exceeds the partials buffer");
@@ -714,7 +553,7 @@ void gp_destroy(gp_handle h) { release(h); }
 gp_status gp_init_gaussian(gp_handle h) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
-    FieldArgs a = field_args(h);
+    FieldArgs a = handle_field_args(h);
     const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
     const bool cplx = h->field == GP_COMPLEX;
     GP_CK(h, launch_gaussian(p, cplx, a, h->stream));
@@ -743,7 +582,7 @@ gp_status gp_get_psi(gp_handle h, void *psi, int on_device) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
-    FieldArgs a = field_args(h);
+    FieldArgs a = handle_field_args(h);
     const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
     const bool cplx = h->field == GP_COMPLEX;
     if (on_device) {
@@ -893,7 +732,7 @@ gp_status gp_sync(gp_handle h) {
 gp_status gp_get_window(gp_handle h, int mode, int window[3]) {
     if (!h || !window || mode < 0 || mode > 1) return fail(h, GP_ERR_ARG, "bad arguments");
     if (mode >= modes_of(h)) return fail(h, GP_ERR_STATE, "no real-time tables on a GP_REAL field");
-    for (int ax = 0; ax < 3; ++ax) window[ax] = h->coef[mode][ax].window;
+    for (int ax = 0; ax < 3; ++ax) window[ax] = h->window[mode][ax];
     return GP_OK;
 }
 
@@ -905,17 +744,39 @@ gp_status gp_set_window(gp_handle h, int window) {
     if (window > 0) {
         for (int mode = 0; mode < modes_of(h); ++mode)
             for (int ax = 0; ax < 3; ++ax) {
-                const CoefSet &cs = h->coef[mode][ax];
-                if (cs.min_window == 0 || window < cs.min_window)
+                const AxisTables &at = h->tab.ax[mode][ax];
+                if (at.min_window == 0 || window < at.min_window)
                     return fail(h, GP_ERR_ARG, "window too small for the accuracy of this dt");
             }
     }
     for (int mode = 0; mode < modes_of(h); ++mode)
-        for (int ax = 0; ax < 3; ++ax) {
-            CoefSet &cs = h->coef[mode][ax];
-            cs.window = window >= 0 ? window : (h->prec == GP_F32 ? cs.min_window : 0);
-        }
+        for (int ax = 0; ax < 3; ++ax)
+            h->window[mode][ax] = window >= 0 ? window : default_window(h->tab.ax[mode][ax], h->prec == GP_F32);
     h->forced_window = window;
+    drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_set_axis_window(gp_handle h, int axis, int window) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (axis < 0 || axis > 2) return fail(h, GP_ERR_ARG, "bad axis");
+    if (window != -1 && window != 0 && window != 4 && window != 8 && window != 16)
+        return fail(h, GP_ERR_ARG, "window must be -1 (automatic), 0, 4, 8 or 16");
+    for (int mode = 0; mode < modes_of(h); ++mode) {
+        const AxisTables &at = h->tab.ax[mode][axis];
+        if (window > 0 && (at.min_window == 0 || window < at.min_window))
+            return fail(h, GP_ERR_ARG, "window too small for the accuracy of this dt");
+    }
+    for (int mode = 0; mode < modes_of(h); ++mode)
+        h->window[mode][axis] = window >= 0 ? window : default_window(h->tab.ax[mode][axis], h->prec == GP_F32);
+    drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_set_pair_lines(gp_handle h, int on) {
+    if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    h->pair_lines = on != 0;
     drop_graphs(h);
     return GP_OK;
 }
@@ -940,8 +801,7 @@ gp_status gp_set_segments(gp_handle h, int axis, int seg_len) {
 gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]) {
     if (!h || !seg_len || !n_seg || mode < 0 || mode > 1) return fail(h, GP_ERR_ARG, "bad arguments");
     if (mode >= modes_of(h)) return fail(h, GP_ERR_STATE, "no real-time tables on a GP_REAL field");
-    for (int ax = 0; ax < 3; ++ax)
-        segments(h, ax, h->coef[mode][ax].window, sweep_lines(h, ax), &seg_len[ax], &n_seg[ax]);
+    for (int ax = 0; ax < 3; ++ax) segments(h, ax, h->window[mode][ax], &seg_len[ax], &n_seg[ax]);
     return GP_OK;
 }
 

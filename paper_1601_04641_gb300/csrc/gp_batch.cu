@@ -1,0 +1,580 @@
+// gp_batch.cu -- many independent condensates (uneven grids, traps and g)
+// advanced together: every imaginary-time step is three launches (kick + x,
+// y, z + norm) that each cover all active instances, with per-instance
+// argument blocks, norm partials and completion counters; blocks of steps
+// are replayed from captured CUDA graphs; converged instances drop out of
+// the launches.
+#include "gp.h"
+#include "gp_host.h"
+#include "gp_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace gpcn;
+
+namespace {
+
+struct Inst {
+    Geometry G;
+    Tables tab;
+    size_t psi_off = 0;     // byte offset in each packed psi buffer
+    size_t sites = 0, bytes = 0;
+    size_t part_off = 0;    // offset (doubles) of the partials region
+    int seg_len[3] = {0, 0, 0}, n_seg[3] = {0, 0, 0};
+    int cur = 0;            // which packed buffer holds psi
+    long long step = 0;
+    double t = 0.0;
+    bool active = true;
+};
+
+// Device tables of one launch configuration (a set of instances, a parity).
+struct LaunchSet {
+    SweepArgs *args[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    unsigned *first[3] = {nullptr, nullptr, nullptr};
+    unsigned *gridx[3] = {nullptr, nullptr, nullptr};
+    unsigned total[3] = {0, 0, 0};
+    FieldArgs *fargs = nullptr;   // observables of the instances, for their current parity
+    unsigned *ofirst = nullptr;
+    unsigned ototal = 0;
+    std::vector<int> members;
+    int parity = 0;               // steps taken by the members since the tables were built, mod 2
+};
+
+constexpr int kSweepThreads = kBatchLineThreads;  // both batched sweep kernels use 64 threads
+constexpr int kInitNormBlocks = 152 * 4;
+
+}  // namespace
+
+struct gp_batch_s {
+    int device = 0;
+    int n = 0;
+    gp_precision prec = GP_F32;
+    gp_field field = GP_COMPLEX;
+    size_t elem = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<Inst> inst;
+    char *d_psi[2] = {nullptr, nullptr};
+    size_t psi_bytes = 0;
+    char *d_tab = nullptr;
+    double *d_scal = nullptr;      // per instance: [scale, norm]
+    double *d_obs = nullptr;       // per instance: O_COUNT values
+    double *d_partials = nullptr;
+    unsigned int *d_counters = nullptr;
+    int window[3] = {0, 0, 0};
+    bool contiguous_z = false;
+    LaunchSet act;                 // the active instances
+    bool dirty = true;
+    int graph_block = 16;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, steps)
+    std::vector<void *> scratch;   // device allocations of the launch sets
+    std::string err;
+};
+
+namespace {
+
+gp_status bfail(gp_batch b, gp_status st, const std::string &m) {
+    if (b) b->err = m;
+    else set_thread_error(m.c_str());
+    return st;
+}
+
+#define GPB_CK(b, call)                                                                          \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return bfail((b), GP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+void free_set(gp_batch b) {
+    for (void *p : b->scratch) cudaFree(p);
+    b->scratch.clear();
+    b->act = LaunchSet();
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+template <typename T> gp_status upload(gp_batch b, const std::vector<T> &v, T **out) {
+    *out = nullptr;
+    if (v.empty()) return GP_OK;
+    void *p = nullptr;
+    if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, GP_ERR_NOMEM, "cudaMalloc of batch launch tables failed");
+    }
+    b->scratch.push_back(p);
+    GPB_CK(b, cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream));
+    *out = static_cast<T *>(p);
+    return GP_OK;
+}
+
+unsigned sweep_gridx(gp_batch b, const Inst &I, int ax) {
+    const long long lines = axis_lines(I.G, ax);
+    (void)b;
+    return (unsigned)((lines + kSweepThreads - 1) / kSweepThreads);
+}
+
+FieldArgs inst_field_args(gp_batch b, int i) {
+    const Inst &I = b->inst[i];
+    return field_args(I.G, b->d_psi[I.cur] + I.psi_off, b->d_scal + 2 * i, b->d_partials + I.part_off,
+                      b->d_counters + i, b->d_obs + (size_t)i * O_COUNT, b->d_scal + 2 * i,
+                      b->d_scal + 2 * i + 1);
+}
+
+// Device tables for the active instances at their current parity.
+gp_status build_set(gp_batch b) {
+    free_set(b);
+    LaunchSet &S = b->act;
+    for (int i = 0; i < b->n; ++i)
+        if (b->inst[i].active) S.members.push_back(i);
+    for (int k = 0; k < 3; ++k) {
+        std::vector<SweepArgs> args[2];
+        std::vector<unsigned> first{0}, gridx;
+        for (int i : S.members) {
+            const Inst &I = b->inst[i];
+            for (int p = 0; p < 2; ++p) {
+                // sweep k of a step that starts with psi in buffer I.cur ^ p
+                const int in = I.cur ^ p ^ (k & 1);
+                args[p].push_back(sweep_args(I.G, k, false, b->d_psi[in] + I.psi_off,
+                                             b->d_psi[in ^ 1] + I.psi_off, b->d_tab, I.tab, I.seg_len[k],
+                                             I.n_seg[k], b->d_scal + 2 * i, b->d_partials + I.part_off,
+                                             b->d_counters + i, b->d_scal + 2 * i + 1, b->d_scal + 2 * i));
+            }
+            const unsigned gx = sweep_gridx(b, I, k);
+            gridx.push_back(gx);
+            first.push_back(first.back() + gx * (unsigned)I.n_seg[k]);
+        }
+        S.total[k] = first.back();
+        gp_status st;
+        if ((st = upload(b, args[0], &S.args[k][0])) != GP_OK) return st;
+        if ((st = upload(b, args[1], &S.args[k][1])) != GP_OK) return st;
+        if ((st = upload(b, first, &S.first[k])) != GP_OK) return st;
+        if ((st = upload(b, gridx, &S.gridx[k])) != GP_OK) return st;
+    }
+    std::vector<FieldArgs> fa;
+    std::vector<unsigned> of{0};
+    for (int i : S.members) {
+        fa.push_back(inst_field_args(b, i));
+        of.push_back(of.back() + (unsigned)observables_blocks(fa.back()));
+    }
+    S.ototal = of.back();
+    gp_status st;
+    if ((st = upload(b, fa, &S.fargs)) != GP_OK) return st;
+    if ((st = upload(b, of, &S.ofirst)) != GP_OK) return st;
+    S.parity = 0;
+    b->dirty = false;
+    return GP_OK;
+}
+
+gp_status launch_step(gp_batch b, cudaStream_t s, int parity) {
+    LaunchSet &S = b->act;
+    for (int k = 0; k < 3; ++k) {
+        SweepLaunch L;
+        L.prec = b->prec == GP_F32 ? P_F32 : P_F64;
+        L.form = b->field == GP_REAL ? F_IMAG_REAL : F_IMAG_CPLX;
+        L.kind = static_cast<Kind>(k);
+        L.window = b->window[k];
+        L.threads = kSweepThreads;
+        L.lpt = 1;
+        L.contiguous = (k == 2 && b->contiguous_z) ? 1 : 0;
+        BatchLaunch bl{S.args[k][parity], S.first[k], S.gridx[k], (int)S.members.size(), S.total[k]};
+        GPB_CK(b, launch_sweep_batch(L, bl, s));
+    }
+    return GP_OK;
+}
+
+// After n steps of the active instances.
+void advance(gp_batch b, int n) {
+    for (int i : b->act.members) {
+        Inst &I = b->inst[i];
+        if (n % 2) I.cur ^= 1;  // three sweeps per step
+        I.step += n;
+        for (int k = 0; k < n; ++k) I.t += I.G.dt;
+    }
+    b->act.parity = (b->act.parity + n) & 1;
+}
+
+gp_status run_graph(gp_batch b, int g) {
+    const auto key = std::make_pair(b->act.parity, g);
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        if (!b->cap_stream && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        gp_status st = GP_OK;
+        for (int s = 0; s < g && st == GP_OK; ++s) st = launch_step(b, b->cap_stream, (b->act.parity + s) & 1);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        const bool ok = st == GP_OK && ec == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            return GP_ERR_STATE;
+        }
+        it = b->graphs.emplace(key, exec).first;
+    }
+    GPB_CK(b, cudaGraphLaunch(it->second, b->stream));
+    return GP_OK;
+}
+
+gp_status step_active(gp_batch b, int nsteps) {
+    if (b->dirty) {
+        gp_status st = build_set(b);
+        if (st != GP_OK) return st;
+    }
+    if (b->act.members.empty()) return GP_OK;
+    while (nsteps > 0) {
+        const int g = std::min(nsteps, std::max(1, b->graph_block));
+        gp_status st = GP_ERR_STATE;
+        if (g > 1) st = run_graph(b, g);
+        if (st == GP_ERR_STATE) {
+            for (int s = 0; s < g; ++s) {
+                st = launch_step(b, b->stream, (b->act.parity + s) & 1);
+                if (st != GP_OK) return st;
+            }
+        } else if (st != GP_OK) {
+            return st;
+        }
+        advance(b, g);
+        nsteps -= g;
+    }
+    return GP_OK;
+}
+
+// Observables of the active instances into host memory (one record per instance).
+gp_status observe_active(gp_batch b, std::vector<double> &host) {
+    LaunchSet &S = b->act;
+    if (S.members.empty()) return GP_OK;
+    // the field arguments follow each instance's current buffer
+    std::vector<FieldArgs> fa;
+    for (int i : S.members) fa.push_back(inst_field_args(b, i));
+    GPB_CK(b, cudaMemcpyAsync(S.fargs, fa.data(), fa.size() * sizeof(FieldArgs), cudaMemcpyHostToDevice, b->stream));
+    GPB_CK(b, launch_observables_batch(b->prec == GP_F32 ? P_F32 : P_F64, b->field == GP_COMPLEX, S.fargs, S.ofirst,
+                                       (int)S.members.size(), S.ototal, b->stream));
+    host.assign((size_t)b->n * O_COUNT, 0.0);
+    GPB_CK(b, cudaMemcpyAsync(host.data(), b->d_obs, host.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    return GP_OK;
+}
+
+void release_batch(gp_batch b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_set(b);
+    cudaFree(b->d_psi[0]);
+    cudaFree(b->d_psi[1]);
+    cudaFree(b->d_tab);
+    cudaFree(b->d_scal);
+    cudaFree(b->d_obs);
+    cudaFree(b->d_partials);
+    cudaFree(b->d_counters);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaGetLastError();
+    delete b;
+}
+
+gp_status benter(gp_batch b) {
+    if (!b) return bfail(nullptr, GP_ERR_ARG, "NULL batch");
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, GP_ERR_CUDA, "cudaSetDevice failed");
+    }
+    return GP_OK;
+}
+
+void fill_obs(const double *o, const Inst &I, gp_obs *out) {
+    out->norm = o[O_NORM];
+    out->mu = o[O_MU];
+    out->energy = o[O_E];
+    out->rms_x = o[O_RMSX];
+    out->rms_y = o[O_RMSY];
+    out->rms_z = o[O_RMSZ];
+    out->step = I.step;
+    out->t = I.t;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const double *dt, const double *gamma,
+                          const double *nu, const double *lambda, const double *g, gp_precision prec,
+                          gp_field field, void *cuda_stream) {
+    if (!out) return bfail(nullptr, GP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !grids || !dt || !gamma || !nu || !lambda || !g)
+        return bfail(nullptr, GP_ERR_ARG, "need n >= 1 and all parameter arrays");
+    if (prec != GP_F64 && prec != GP_F32) return bfail(nullptr, GP_ERR_ARG, "unknown precision");
+    if (field != GP_COMPLEX && field != GP_REAL) return bfail(nullptr, GP_ERR_ARG, "unknown field");
+    for (int i = 0; i < n; ++i) {
+        const int nn[3] = {grids[i].nx, grids[i].ny, grids[i].nz};
+        const double dd[3] = {grids[i].dx, grids[i].dy, grids[i].dz};
+        for (int a = 0; a < 3; ++a)
+            if (nn[a] < 3 || !(dd[a] > 0.0) || !std::isfinite(dd[a]))
+                return bfail(nullptr, GP_ERR_ARG, "instance " + std::to_string(i) + ": bad grid");
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i]) || !std::isfinite(g[i]))
+            return bfail(nullptr, GP_ERR_ARG, "instance " + std::to_string(i) + ": bad dt or g");
+        const double w[3] = {gamma[i], nu[i], lambda[i]};
+        for (double x : w)
+            if (!std::isfinite(x) || x < 0.0)
+                return bfail(nullptr, GP_ERR_ARG, "instance " + std::to_string(i) + ": bad trap frequency");
+    }
+    gp_batch b = new (std::nothrow) gp_batch_s();
+    if (!b) return bfail(nullptr, GP_ERR_NOMEM, "host allocation failed");
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bfail(nullptr, GP_ERR_CUDA, "no CUDA device");
+    }
+    b->n = n;
+    b->prec = prec;
+    b->field = field;
+    b->elem = (prec == GP_F64 ? 8 : 4) * (field == GP_COMPLEX ? 2 : 1);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->inst.resize(n);
+    const bool f32 = prec == GP_F32;
+    std::vector<char> host;
+    size_t psi = 0, parts = 0;
+    for (int i = 0; i < n; ++i) {
+        Inst &I = b->inst[i];
+        I.G.n[0] = grids[i].nx;
+        I.G.n[1] = grids[i].ny;
+        I.G.n[2] = grids[i].nz;
+        I.G.d[0] = grids[i].dx;
+        I.G.d[1] = grids[i].dy;
+        I.G.d[2] = grids[i].dz;
+        I.G.dt = dt[i];
+        I.G.w[0] = gamma[i];
+        I.G.w[1] = nu[i];
+        I.G.w[2] = lambda[i];
+        I.G.g = g[i];
+        append_tables(I.G, f32, 1, host, I.tab);
+        I.sites = (size_t)grids[i].nx * grids[i].ny * grids[i].nz;
+        I.bytes = I.sites * b->elem;
+        I.psi_off = psi;
+        psi = align_up(psi + I.bytes, 256);
+    }
+    // one window per axis for the whole batch: the largest of the instances'
+    // smallest admissible windows (0 if any instance admits none, or FP64)
+    for (int ax = 0; ax < 3; ++ax) {
+        int w = 0;
+        bool all = f32;
+        for (int i = 0; i < n && all; ++i) {
+            const int m = b->inst[i].tab.ax[0][ax].min_window;
+            if (m == 0) all = false;
+            w = std::max(w, m);
+        }
+        b->window[ax] = all ? w : 0;
+    }
+    b->contiguous_z = b->window[2] > 0;
+    for (int i = 0; i < n; ++i) {
+        Inst &I = b->inst[i];
+        size_t cap = kInitNormBlocks;
+        for (int ax = 0; ax < 3; ++ax) {
+            choose_segments(I.G, ax, b->window[ax], 1, (int)b->elem, ax == 2 && b->contiguous_z, 0,
+                            &I.seg_len[ax], &I.n_seg[ax]);
+            cap = std::max(cap, (size_t)sweep_gridx(b, I, ax) * I.n_seg[ax]);
+        }
+        FieldArgs fa = field_args(I.G, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
+        I.part_off = parts;
+        parts += align_up(cap, 32);
+    }
+    b->psi_bytes = psi;
+    if (cudaMalloc(&b->d_psi[0], psi) != cudaSuccess || cudaMalloc(&b->d_psi[1], psi) != cudaSuccess ||
+        cudaMalloc(&b->d_tab, host.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_scal, 2 * n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_obs, (size_t)n * O_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_partials, parts * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_counters, n * sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        release_batch(b);
+        return bfail(nullptr, GP_ERR_NOMEM, "device allocation of the batch failed");
+    }
+    std::vector<double> scal(2 * n, 1.0);
+    if (cudaMemcpyAsync(b->d_tab, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_scal, scal.data(), scal.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(b->d_counters, 0, n * sizeof(unsigned int), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->d_psi[0], 0, psi, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        release_batch(b);
+        return bfail(nullptr, GP_ERR_CUDA, "initialising the batch failed");
+    }
+    *out = b;
+    return GP_OK;
+}
+
+void gp_batch_destroy(gp_batch b) { release_batch(b); }
+
+gp_status gp_batch_init_gaussian(gp_batch b) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    const Prec p = b->prec == GP_F32 ? P_F32 : P_F64;
+    const bool cplx = b->field == GP_COMPLEX;
+    for (int i = 0; i < b->n; ++i) {
+        FieldArgs a = inst_field_args(b, i);
+        GPB_CK(b, launch_gaussian(p, cplx, a, b->stream));
+        GPB_CK(b, launch_norm(p, cplx, a, kInitNormBlocks, b->stream));
+        b->inst[i].step = 0;
+        b->inst[i].t = 0.0;
+    }
+    b->dirty = true;
+    return GP_OK;
+}
+
+gp_status gp_batch_set_psi(gp_batch b, int i, const void *psi, int on_device) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (i < 0 || i >= b->n || !psi) return bfail(b, GP_ERR_ARG, "bad instance or NULL psi");
+    Inst &I = b->inst[i];
+    GPB_CK(b, cudaMemcpyAsync(b->d_psi[I.cur] + I.psi_off, psi, I.bytes,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+    const double one = 1.0;
+    GPB_CK(b, cudaMemcpyAsync(b->d_scal + 2 * i, &one, sizeof(one), cudaMemcpyHostToDevice, b->stream));
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    I.step = 0;
+    I.t = 0.0;
+    return GP_OK;
+}
+
+gp_status gp_batch_get_psi(gp_batch b, int i, void *psi, int on_device) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (i < 0 || i >= b->n || !psi) return bfail(b, GP_ERR_ARG, "bad instance or NULL psi");
+    Inst &I = b->inst[i];
+    FieldArgs a = inst_field_args(b, i);
+    const Prec p = b->prec == GP_F32 ? P_F32 : P_F64;
+    const bool cplx = b->field == GP_COMPLEX;
+    if (on_device) {
+        GPB_CK(b, launch_apply_scale(p, cplx, a, psi, b->stream));
+        return GP_OK;
+    }
+    // apply the pending factor into the other buffer, copy it out
+    char *tmp = b->d_psi[I.cur ^ 1] + I.psi_off;
+    GPB_CK(b, launch_apply_scale(p, cplx, a, tmp, b->stream));
+    GPB_CK(b, cudaMemcpyAsync(psi, tmp, I.bytes, cudaMemcpyDeviceToHost, b->stream));
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    return GP_OK;
+}
+
+gp_status gp_batch_step_imag(gp_batch b, int nsteps) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (nsteps < 0) return bfail(b, GP_ERR_ARG, "nsteps < 0");
+    return step_active(b, nsteps);
+}
+
+gp_status gp_batch_observables(gp_batch b, gp_obs *out) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (!out) return bfail(b, GP_ERR_ARG, "out is NULL");
+    const Prec p = b->prec == GP_F32 ? P_F32 : P_F64;
+    const bool cplx = b->field == GP_COMPLEX;
+    for (int i = 0; i < b->n; ++i) {
+        FieldArgs a = inst_field_args(b, i);
+        GPB_CK(b, launch_observables(p, cplx, a, b->stream));
+    }
+    std::vector<double> host((size_t)b->n * O_COUNT);
+    GPB_CK(b, cudaMemcpyAsync(host.data(), b->d_obs, host.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    bool finite = true;
+    for (int i = 0; i < b->n; ++i) {
+        fill_obs(host.data() + (size_t)i * O_COUNT, b->inst[i], out + i);
+        finite = finite && host[(size_t)i * O_COUNT + O_FINITE] == 1.0;
+    }
+    if (!finite) return bfail(b, GP_ERR_NONFINITE, "an instance's psi holds NaN or Inf");
+    return GP_OK;
+}
+
+gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, int max_steps, int *steps_taken) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (!(mu_tol > 0.0) || check_every < 1 || max_steps < 0)
+        return bfail(b, GP_ERR_ARG, "need mu_tol > 0, check_every >= 1, max_steps >= 0");
+    for (int i = 0; i < b->n; ++i) b->inst[i].active = true;
+    b->dirty = true;
+    if ((st = build_set(b)) != GP_OK) return st;
+    std::vector<double> host;
+    if ((st = observe_active(b, host)) != GP_OK) return st;
+    std::vector<double> mu_prev(b->n);
+    std::vector<int> taken(b->n, 0);
+    for (int i = 0; i < b->n; ++i) mu_prev[i] = host[(size_t)i * O_COUNT + O_MU];
+    int done = 0;
+    while (done < max_steps && !b->act.members.empty()) {
+        const int n = std::min(check_every, max_steps - done);
+        if ((st = step_active(b, n)) != GP_OK) break;
+        done += n;
+        if ((st = observe_active(b, host)) != GP_OK) break;
+        bool changed = false;
+        for (int i : b->act.members) {
+            const double *o = host.data() + (size_t)i * O_COUNT;
+            taken[i] = done;
+            if (o[O_FINITE] != 1.0) {
+                st = bfail(b, GP_ERR_NONFINITE, "instance " + std::to_string(i) + " became non-finite");
+                break;
+            }
+            if (std::fabs(o[O_MU] - mu_prev[i]) < mu_tol) {
+                b->inst[i].active = false;
+                changed = true;
+            }
+            mu_prev[i] = o[O_MU];
+        }
+        if (st != GP_OK) break;
+        if (changed) {
+            b->dirty = true;
+            if ((st = build_set(b)) != GP_OK) break;
+        }
+    }
+    if (steps_taken)
+        for (int i = 0; i < b->n; ++i) steps_taken[i] = taken[i];
+    for (int i = 0; i < b->n; ++i) b->inst[i].active = true;
+    b->dirty = true;
+    return st;
+}
+
+gp_status gp_batch_get_window(gp_batch b, int window[3]) {
+    if (!b || !window) return bfail(b, GP_ERR_ARG, "bad arguments");
+    for (int ax = 0; ax < 3; ++ax) window[ax] = b->window[ax];
+    return GP_OK;
+}
+
+gp_status gp_batch_get_segments(gp_batch b, int i, int seg_len[3], int n_seg[3]) {
+    if (!b || !seg_len || !n_seg || i < 0 || i >= b->n) return bfail(b, GP_ERR_ARG, "bad arguments");
+    for (int ax = 0; ax < 3; ++ax) {
+        seg_len[ax] = b->inst[i].seg_len[ax];
+        n_seg[ax] = b->inst[i].n_seg[ax];
+    }
+    return GP_OK;
+}
+
+gp_status gp_batch_set_graph_block(gp_batch b, int steps) {
+    if (!b) return bfail(b, GP_ERR_ARG, "NULL batch");
+    if (steps < 0 || steps > 1024) return bfail(b, GP_ERR_ARG, "steps must be in [0, 1024]");
+    b->graph_block = steps;
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    return GP_OK;
+}
+
+const char *gp_batch_last_error(gp_batch b) {
+    if (!b) return gp_last_error(nullptr);
+    return b->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// gp_host.cu -- host-side helpers shared by the handle types (see gp_host.h).
+#include "gp_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+namespace gpcn {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+namespace {
+
+// FP64 Thomas coefficients of the CN matrix (-c, 1+2c, -c) on n interior
+// nodes: den[0] = 1+2c, den[t] = 1+2c + c cp[t-1], ip = 1/den, cp = -c ip.
+// The inverse pivot is returned as its deviation from one,
+// ipm1 = ip - 1 = (1 - den) / den, which the kernels apply as u + u ipm1.
+void thomas_coefficients(std::complex<double> c, int n, std::vector<std::complex<double>> &cp,
+                         std::vector<std::complex<double>> &ipm1) {
+    cp.assign(n, 0.0);
+    ipm1.assign(n, 0.0);
+    for (int t = 0; t < n; ++t) {
+        const std::complex<double> excess = 2.0 * c + (t == 0 ? 0.0 : c * cp[t - 1]);  // den - 1
+        const std::complex<double> den = 1.0 + excess;
+        ipm1[t] = -excess / den;
+        cp[t] = -c / den;
+    }
+}
+
+void put_real(char *dst, double v, bool f32) {
+    if (f32) {
+        const float f = (float)v;
+        std::memcpy(dst, &f, sizeof(f));
+    } else {
+        std::memcpy(dst, &v, sizeof(v));
+    }
+}
+
+}  // namespace
+
+void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &host, Tables &T) {
+    const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+    const double eps = f32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    size_t off = align_up(host.size(), 256);
+    for (int mode = 0; mode < modes; ++mode) {
+        for (int ax = 0; ax < 3; ++ax) {
+            const size_t esz = (mode == 1 ? 2 : 1) * rsz;
+            AxisTables &at = T.ax[mode][ax];
+            at.off_cp = off;
+            off = align_up(off + esz * (G.n[ax] - 2), 256);
+            at.off_ip = off;
+            off = align_up(off + esz * (G.n[ax] - 2), 256);
+        }
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        T.kick_off[ax] = off;
+        off = align_up(off + rsz * G.n[ax], 256);
+    }
+    host.resize(off, 0);
+    // exp(-dt w^2 a^2 / 2) per node of each axis: the trap part of the
+    // imaginary-time kick factorises over the axes.
+    for (int ax = 0; ax < 3; ++ax)
+        for (int i = 0; i < G.n[ax]; ++i) {
+            const double a = (i - 0.5 * (G.n[ax] - 1)) * G.d[ax];
+            put_real(host.data() + T.kick_off[ax] + i * rsz, std::exp(-G.dt * 0.5 * G.w[ax] * G.w[ax] * a * a), f32);
+        }
+    for (int mode = 0; mode < modes; ++mode) {
+        for (int ax = 0; ax < 3; ++ax) {
+            const int n = G.n[ax] - 2;
+            const double kap = G.dt / (4.0 * G.d[ax] * G.d[ax]);
+            const std::complex<double> c = mode == 1 ? std::complex<double>(0.0, kap)
+                                                     : std::complex<double>(kap, 0.0);
+            std::vector<std::complex<double>> cp, ip;
+            thomas_coefficients(c, n, cp, ip);
+            AxisTables &at = T.ax[mode][ax];
+            at.cp_max = 0.0;
+            for (int t = 0; t < n - 1; ++t) at.cp_max = std::max(at.cp_max, std::abs(cp[t]));
+            at.min_window = 0;
+            for (int w : {4, 8, 16}) {
+                if (std::pow(at.cp_max, w + 1) <= eps / 8.0) {
+                    at.min_window = w;
+                    break;
+                }
+            }
+            for (int t = 0; t < n; ++t) {
+                for (int which = 0; which < 2; ++which) {
+                    const std::complex<double> v = which == 0 ? cp[t] : ip[t];
+                    char *dst = host.data() + (which == 0 ? at.off_cp : at.off_ip);
+                    if (mode == 1) {
+                        put_real(dst + t * 2 * rsz, v.real(), f32);
+                        put_real(dst + t * 2 * rsz + rsz, v.imag(), f32);
+                    } else {
+                        put_real(dst + t * rsz, v.real(), f32);
+                    }
+                }
+            }
+        }
+    }
+}
+
+int default_window(const AxisTables &t, bool f32) {
+    // FP64 on this part runs at a small fraction of its FP32 rate, so the FP64
+    // forms are ALU-bound: the exact two-pass solve (fewer flops, twice the
+    // bytes) is faster there.  FP32 is bandwidth-bound and takes the
+    // windowed single-pass solve.
+    return f32 ? t.min_window : 0;
+}
+
+long long axis_lines(const Geometry &G, int ax) {
+    const long long nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    return ax == 0 ? ny * nz : ax == 1 ? nx * nz : nx * ny;
+}
+
+void choose_segments(const Geometry &G, int ax, int window, int lpt, int elem_bytes, bool contiguous_z,
+                     int override_len, int *seg_len, int *n_seg) {
+    const int n = G.n[ax] - 2;
+    const int chunk = (elem_bytes * lpt >= 16) ? 8 : 16;
+    int len = n;
+    if (window > 0) {
+        if (override_len > 0) {
+            len = std::min(n, override_len);
+        } else if (ax == 2 && contiguous_z) {
+            len = n;  // warp-tiled stride-1 axis: whole lines (measured best)
+        } else {
+            // about 128 nodes per segment (measured best on the strided axes),
+            // rounded to whole chunks
+            const int want = std::max(1, (n + 127) / 128);
+            len = (n + want - 1) / want;
+            len = (len + chunk - 1) / chunk * chunk;
+            len = std::min(len, n);
+        }
+    }
+    *seg_len = std::max(1, len);
+    *n_seg = (n + *seg_len - 1) / *seg_len;
+}
+
+SweepArgs sweep_args(const Geometry &G, int ax, bool realtime, const void *in, void *out,
+                     const char *tables, const Tables &T, int seg_len, int n_seg, const double *scale,
+                     double *partials, unsigned int *counter, double *norm_out, double *scale_out) {
+    SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const long long ny = G.n[1], nz = G.n[2];
+    const int mode = realtime ? 1 : 0;
+    a.psi = in;
+    a.psi_out = out;
+    a.cp = tables + T.ax[mode][ax].off_cp;
+    a.ip = tables + T.ax[mode][ax].off_ip;
+    a.n_lines = axis_lines(G, ax);
+    if (ax == 0) {
+        a.inner = ny * nz;
+        a.outer_stride = 0;
+        a.stride = ny * nz;
+    } else if (ax == 1) {
+        a.inner = nz;
+        a.outer_stride = ny * nz;
+        a.stride = nz;
+    } else {
+        a.inner = 1;
+        a.outer_stride = nz;
+        a.stride = 1;
+    }
+    a.N = G.n[ax];
+    a.seg_len = seg_len;
+    a.n_seg = n_seg;
+    a.kappa = G.dt / (4.0 * G.d[ax] * G.d[ax]);
+    a.scale = scale;
+    if (!realtime) {
+        a.kick_ex = tables + T.kick_off[0];
+        a.kick_ey = tables + T.kick_off[1];
+        a.kick_ez = tables + T.kick_off[2];
+    }
+    a.dt = G.dt;
+    a.g = G.g;
+    for (int q = 0; q < 3; ++q) {
+        a.half_w2[q] = 0.5 * G.w[q] * G.w[q];
+        a.origin[q] = -0.5 * (G.n[q] - 1) * G.d[q];
+        a.d[q] = G.d[q];
+    }
+    a.nz = (int)nz;
+    a.ny = (int)ny;
+    a.partials = partials;
+    a.counter = counter;
+    a.norm_out = norm_out;
+    a.scale_out = scale_out;
+    a.dV = G.d[0] * G.d[1] * G.d[2];
+    a.want_scale = realtime ? 0 : 1;
+    return a;
+}
+
+FieldArgs field_args(const Geometry &G, const void *psi, const double *scale, double *partials,
+                     unsigned int *counter, double *out, double *scale_out, double *norm_out) {
+    FieldArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = const_cast<void *>(psi);
+    for (int ax = 0; ax < 3; ++ax) {
+        a.n[ax] = G.n[ax];
+        a.d[ax] = G.d[ax];
+        a.origin[ax] = -0.5 * (G.n[ax] - 1) * G.d[ax];
+        a.w[ax] = G.w[ax];
+        a.half_w2[ax] = 0.5 * G.w[ax] * G.w[ax];
+    }
+    a.g = G.g;
+    a.scale = scale;
+    a.dV = G.d[0] * G.d[1] * G.d[2];
+    a.partials = partials;
+    a.counter = counter;
+    a.out = out;
+    a.scale_out = scale_out;
+    a.norm_out = norm_out;
+    a.sites = (long long)G.n[0] * G.n[1] * G.n[2];
+    return a;
+}
+
+}  // namespace gpcn

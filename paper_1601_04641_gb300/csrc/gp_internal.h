@@ -98,6 +98,22 @@ enum ObsSlot {
 };
 
 int observables_blocks(const FieldArgs &a);
+cudaError_t launch_observables_batch(Prec p, bool cplx, const FieldArgs *args, const unsigned *first, int n,
+                                     unsigned total_blocks, cudaStream_t s);
+
+// Batched sweep launch: instance i owns blocks [first[i], first[i+1]) of a
+// 1D grid of total_blocks, laid out as its own grid (gridx[i] blocks along x,
+// then the segment).  args, first, gridx are device arrays.
+struct BatchLaunch {
+    const SweepArgs *args;
+    const unsigned *first;
+    const unsigned *gridx;
+    int n;
+    unsigned total_blocks;
+};
+cudaError_t launch_sweep_batch(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s);
+// Threads per block of the batched kernels.
+constexpr int kBatchLineThreads = 64;
 void set_thread_error(const char *msg);
 constexpr int kReduceThreads = 256;
 

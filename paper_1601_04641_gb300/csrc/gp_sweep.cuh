@@ -269,14 +269,15 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 
 // Block partial of sum |phi|^2, then the last block to finish sums the
 // partials in block order and writes the norm (and the renormalisation
-// factor) -- deterministic whatever the block completion order.
-__device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a) {
+// factor) -- deterministic whatever the block completion order.  `block` and
+// `nblocks` number the blocks of one condensate (all of the grid for a single
+// condensate; one instance's share of a batched launch).
+__device__ __forceinline__ void norm_finalize(double v, const SweepArgs &a, unsigned block, unsigned nblocks) {
     __shared__ double red[32];
     __shared__ int is_last;
     double bsum = block_sum(v, red);
-    const unsigned nblocks = gridDim.x * gridDim.y;
     if (threadIdx.x == 0) {
-        a.partials[blockIdx.y * gridDim.x + blockIdx.x] = bsum;
+        a.partials[block] = bsum;
         __threadfence();
         unsigned prev = atomicAdd(a.counter, 1u);
         is_last = (prev == nblocks - 1);
@@ -570,13 +571,13 @@ template <class F> struct LinesPerThread<F, 2> { using M = FPair<F>; };
 // when LPT = 2; blockIdx.y is the segment.  Window 0 selects the exact
 // two-pass form over whole lines with direct access.
 template <class F, typename R, int W, int KIND, int LPT>
-__global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
+__device__ __forceinline__ double lines_body(const SweepArgs &a, unsigned bx, unsigned seg,
+                                             unsigned char *smem_raw) {
     using M = typename LinesPerThread<F, LPT>::M;
     using V = typename M::V;
     using C = typename F::C;
     constexpr int B = chunk_len<V>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const long long L = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * LPT;
+    const long long L = ((long long)bx * blockDim.x + threadIdx.x) * LPT;
     Acc<R> acc;
     if (L < a.n_lines) {
         const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
@@ -584,11 +585,10 @@ __global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
         V *out = reinterpret_cast<V *>(static_cast<typename F::V *>(a.psi_out) + off);
         const long long st = a.stride / LPT;  // stride in units of V
         const int n = a.N - 2;
-        const int seg = blockIdx.y;
         const C *cp = static_cast<const C *>(a.cp);
         const C *ipm1 = static_cast<const C *>(a.ip);
         if (seg == 0) out[0] = M::zero();
-        if (seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::zero();
+        if ((int)seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::zero();
         if constexpr (W > 0) {
             ColumnIO<F, M, R, B, KIND> io;
             io.in = in;
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
             io.hk.acc = &acc;
             io.hk.init(a, L);
             const int tb = seg * a.seg_len;
-            const int te = seg == a.n_seg - 1 ? n : tb + a.seg_len;
+            const int te = (int)seg == a.n_seg - 1 ? n : tb + a.seg_len;
             solve_segment<M, R, B, W>(n, tb, te, (R)a.kappa, cp, ipm1, io);
         } else {
             DirectIO<F, M, R, KIND> io;
@@ -613,7 +613,17 @@ __global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
             solve_line_exact<M, R>(n, (R)a.kappa, cp, ipm1, io);
         }
     }
-    if (KIND == K_Z) norm_finalize(acc.value(), a);
+    return acc.value();
+}
+
+// One thread per (line, segment), or per (pair of adjacent lines, segment)
+// when LPT = 2; blockIdx.y is the segment.  Window 0 selects the exact
+// two-pass form over whole lines with direct access.
+template <class F, typename R, int W, int KIND, int LPT>
+__global__ void __launch_bounds__(256, 1) sweep_lines_kernel(SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const double v = lines_body<F, R, W, KIND, LPT>(a, blockIdx.x, blockIdx.y, smem_raw);
+    if (KIND == K_Z) norm_finalize(v, a, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }
 
 template <typename V> __host__ __device__ constexpr size_t column_ring_bytes(int threads) {
@@ -717,14 +727,14 @@ template <typename V, int W> __host__ __device__ constexpr size_t tile_warp_byte
 constexpr int kTileWarps = 2;
 
 template <class F, typename R, int W>
-__global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_contig_kernel(SweepArgs a) {
+__device__ __forceinline__ double contig_body(const SweepArgs &a, unsigned bx, unsigned seg,
+                                              unsigned char *smem_raw) {
     using V = typename F::V;
     using C = typename F::C;
     constexpr int B = chunk_len<V>();
     using IO = TileIO<F, R, B, W>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long L0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+    const long long L0 = ((long long)bx * (blockDim.x >> 5) + warp) * 32;
     Acc<R> acc;
     if (L0 < a.n_lines) {
         IO io;
@@ -740,17 +750,69 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_contig_kernel(SweepA
         io.acc = &acc;
         io.csum = R(0);
         io.setup();
-        const int seg = blockIdx.y;
         if (lane < io.nvalid) {
             if (seg == 0) io.out0[(long long)lane * a.N] = F::zero();
-            if (seg == a.n_seg - 1) io.out0[(long long)lane * a.N + a.N - 1] = F::zero();
+            if ((int)seg == a.n_seg - 1) io.out0[(long long)lane * a.N + a.N - 1] = F::zero();
         }
         const int tb = seg * a.seg_len;
-        const int te = seg == a.n_seg - 1 ? io.n : tb + a.seg_len;
+        const int te = (int)seg == a.n_seg - 1 ? io.n : tb + a.seg_len;
         solve_segment<F, R, B, W>(io.n, tb, te, (R)a.kappa, static_cast<const C *>(a.cp),
                                   static_cast<const C *>(a.ip), io);
     }
-    norm_finalize(acc.value(), a);
+    return acc.value();
+}
+
+template <class F, typename R, int W>
+__global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_contig_kernel(SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const double v = contig_body<F, R, W>(a, blockIdx.x, blockIdx.y, smem_raw);
+    norm_finalize(v, a, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+}
+
+// ------------------------------------------------------------------ batched launches
+// Many condensates in one launch: instance i owns the blocks
+// [first[i], first[i+1]) of a 1D grid, laid out as its single-condensate grid
+// (bx fastest, then the segment).  Each instance has its own argument block
+// (buffers, sizes, coefficients, norm partials and counter).
+struct BatchDesc {
+    const SweepArgs *args;    // per instance
+    const unsigned *first;    // n + 1 prefix sums of blocks
+    const unsigned *gridx;    // per instance: blocks along x of its own grid
+    int n;
+};
+
+__device__ __forceinline__ int find_instance(const BatchDesc &d, unsigned b) {
+    int lo = 0, hi = d.n - 1;
+    while (lo < hi) {  // last i with first[i] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(d.first + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class F, typename R, int W, int KIND, int LPT>
+__global__ void __launch_bounds__(256, 1) batch_lines_kernel(BatchDesc d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int i = find_instance(d, blockIdx.x);
+    const SweepArgs a = d.args[i];
+    const unsigned local = blockIdx.x - __ldg(d.first + i);
+    const unsigned gx = __ldg(d.gridx + i);
+    const unsigned nblocks = __ldg(d.first + i + 1) - __ldg(d.first + i);
+    const double v = lines_body<F, R, W, KIND, LPT>(a, local % gx, local / gx, smem_raw);
+    if (KIND == K_Z) norm_finalize(v, a, local, nblocks);
+}
+
+template <class F, typename R, int W>
+__global__ void __launch_bounds__(kTileWarps * 32, 1) batch_contig_kernel(BatchDesc d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int i = find_instance(d, blockIdx.x);
+    const SweepArgs a = d.args[i];
+    const unsigned local = blockIdx.x - __ldg(d.first + i);
+    const unsigned gx = __ldg(d.gridx + i);
+    const unsigned nblocks = __ldg(d.first + i + 1) - __ldg(d.first + i);
+    const double v = contig_body<F, R, W>(a, local % gx, local / gx, smem_raw);
+    norm_finalize(v, a, local, nblocks);
 }
 
 }  // namespace gpcn

@@ -52,7 +52,8 @@ __global__ void gaussian_kernel(FieldArgs a) {
 // Reduce 9 FP64 values over the grid: block partials, then the last block
 // sums them in block order (deterministic) and calls `fin`.
 template <int NV, class Fin>
-__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs &a, Fin fin) {
+__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs &a, Fin fin,
+                                                unsigned block, unsigned nblocks) {
     __shared__ double red[32];
     __shared__ int is_last;
     double bs[NV];
@@ -60,10 +61,10 @@ __device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs
     for (int q = 0; q < NV; ++q) bs[q] = block_sum(v[q], red);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) a.partials[(long long)blockIdx.x * NV + q] = bs[q];
+        for (int q = 0; q < NV; ++q) a.partials[(long long)block * NV + q] = bs[q];
         __threadfence();
         unsigned prev = atomicAdd(a.counter, 1u);
-        is_last = (prev == gridDim.x - 1);
+        is_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return;
@@ -72,7 +73,7 @@ __device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         double s = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+        for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
             s += __ldcg(a.partials + (long long)b * NV + q);
         tot[q] = block_sum(s, red);
     }
@@ -90,11 +91,14 @@ __global__ void __launch_bounds__(kReduceThreads) norm_kernel(FieldArgs a) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < a.sites; s += grid_stride())
         acc += E::abs2(psi[s]);
     double v[1] = {acc};
-    reduce_finalize<1>(v, a, [&](const double *tot) {
-        const double nrm = a.dV * tot[0];
-        *a.norm_out = nrm;
-        *a.scale_out = 1.0 / sqrt(nrm);
-    });
+    reduce_finalize<1>(
+        v, a,
+        [&](const double *tot) {
+            const double nrm = a.dV * tot[0];
+            *a.norm_out = nrm;
+            *a.scale_out = 1.0 / sqrt(nrm);
+        },
+        blockIdx.x, gridDim.x);
 }
 
 // Observables: one thread per (j, k) walks along i.  Per site it adds |psi|^2,
@@ -102,12 +106,12 @@ __global__ void __launch_bounds__(kReduceThreads) norm_kernel(FieldArgs a) {
 // forward differences to the +x, +y and +z neighbours (links that leave the
 // grid do not exist).  psi is read through the pending scale.
 template <typename R, bool CPLX>
-__global__ void __launch_bounds__(kReduceThreads) observables_kernel(FieldArgs a) {
+__device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned block, unsigned nblocks) {
     using E = Elem<R, CPLX>;
     using V = typename E::V;
     const V *psi = static_cast<const V *>(a.psi);
     const long long plane = (long long)a.n[1] * a.n[2];
-    const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long L = (long long)block * blockDim.x + threadIdx.x;
     Acc<R> acc[9];
     if (L < plane) {
         const int j = (int)(L / a.n[2]), k = (int)(L % a.n[2]);
@@ -182,7 +186,27 @@ __global__ void __launch_bounds__(kReduceThreads) observables_kernel(FieldArgs a
         bool fin = true;
         for (int q = 0; q < 15; ++q) fin = fin && isfinite(o[q]);
         o[O_FINITE] = fin ? 1.0 : 0.0;
-    });
+    }, block, nblocks);
+}
+
+template <typename R, bool CPLX>
+__global__ void __launch_bounds__(kReduceThreads) observables_kernel(FieldArgs a) {
+    observables_body<R, CPLX>(a, blockIdx.x, gridDim.x);
+}
+
+// Many condensates in one launch: instance i owns blocks [first[i], first[i+1]).
+template <typename R, bool CPLX>
+__global__ void __launch_bounds__(kReduceThreads) observables_batch_kernel(const FieldArgs *args,
+                                                                           const unsigned *first, int n) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(first + mid) <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const FieldArgs a = args[lo];
+    const unsigned f = __ldg(first + lo);
+    observables_body<R, CPLX>(a, blockIdx.x - f, __ldg(first + lo + 1) - f);
 }
 
 template <typename R, bool CPLX>
@@ -222,6 +246,19 @@ cudaError_t dispatch_all(Prec p, bool cplx, int what, const FieldArgs &a, int bl
 }
 
 }  // namespace
+
+cudaError_t launch_observables_batch(Prec p, bool cplx, const FieldArgs *args, const unsigned *first, int n,
+                                     unsigned total_blocks, cudaStream_t s) {
+    if (total_blocks == 0) return cudaSuccess;
+    if (p == P_F64) {
+        if (cplx) observables_batch_kernel<double, true><<<total_blocks, kReduceThreads, 0, s>>>(args, first, n);
+        else observables_batch_kernel<double, false><<<total_blocks, kReduceThreads, 0, s>>>(args, first, n);
+    } else {
+        if (cplx) observables_batch_kernel<float, true><<<total_blocks, kReduceThreads, 0, s>>>(args, first, n);
+        else observables_batch_kernel<float, false><<<total_blocks, kReduceThreads, 0, s>>>(args, first, n);
+    }
+    return cudaGetLastError();
+}
 
 int observables_blocks(const FieldArgs &a) {
     const long long plane = (long long)a.n[1] * a.n[2];

@@ -5,4 +5,7 @@ namespace gpcn {
 cudaError_t launch_sweep_f32_ic(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     return launch_form<FImagCplx<float>, float>(L, a, s);
 }
+cudaError_t launch_sweep_f32_ic_batch(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    return launch_batch_form<FImagCplx<float>, float>(L, b, s);
+}
 }  // namespace gpcn

@@ -71,6 +71,70 @@ static cudaError_t launch_kind(const SweepLaunch &L, const SweepArgs &a, cudaStr
     }
 }
 
+// ---------------------------------------------------------------- batched
+template <class F, typename R, int W, int KIND>
+static cudaError_t launch_batch_lines_w(const BatchLaunch &b, cudaStream_t s) {
+    using V = typename F::V;
+    const unsigned threads = kBatchLineThreads;
+    const size_t smem = W > 0 ? column_ring_bytes<V>(threads) : 0;
+    static bool attr = false;
+    if (!attr && smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(batch_lines_kernel<F, R, W, KIND, 1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    BatchDesc d{b.args, b.first, b.gridx, b.n};
+    batch_lines_kernel<F, R, W, KIND, 1><<<b.total_blocks, threads, smem, s>>>(d);
+    return cudaGetLastError();
+}
+
+template <class F, typename R, int W>
+static cudaError_t launch_batch_contig_w(const BatchLaunch &b, cudaStream_t s) {
+    using V = typename F::V;
+    const size_t smem = kTileWarps * tile_warp_bytes<V, W>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(batch_contig_kernel<F, R, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    BatchDesc d{b.args, b.first, b.gridx, b.n};
+    batch_contig_kernel<F, R, W><<<b.total_blocks, 32 * kTileWarps, smem, s>>>(d);
+    return cudaGetLastError();
+}
+
+template <class F, typename R, int KIND>
+static cudaError_t launch_batch_kind(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    if (KIND == K_Z && L.contiguous) {
+        switch (L.window) {
+        case 4: return launch_batch_contig_w<F, R, 4>(b, s);
+        case 8: return launch_batch_contig_w<F, R, 8>(b, s);
+        case 16: return launch_batch_contig_w<F, R, 16>(b, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (L.window) {
+    case 0: return launch_batch_lines_w<F, R, 0, KIND>(b, s);
+    case 4: return launch_batch_lines_w<F, R, 4, KIND>(b, s);
+    case 8: return launch_batch_lines_w<F, R, 8, KIND>(b, s);
+    case 16: return launch_batch_lines_w<F, R, 16, KIND>(b, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class F, typename R>
+static cudaError_t launch_batch_form(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    if (b.total_blocks == 0) return cudaSuccess;
+    switch (L.kind) {
+    case K_X: return launch_batch_kind<F, R, K_X>(L, b, s);
+    case K_Y: return launch_batch_kind<F, R, K_Y>(L, b, s);
+    case K_Z: return launch_batch_kind<F, R, K_Z>(L, b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <class F, typename R>
 static cudaError_t launch_form(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     if (a.n_lines <= 0) return cudaSuccess;

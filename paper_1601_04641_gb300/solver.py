@@ -163,5 +163,101 @@ class GP:
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_set_graph_block(self.h, int(steps)))
 
+    def set_axis_window(self, axis, window):
+        self._ck(self.lib.gp_set_axis_window(self.h, int(axis), int(window)))
+
+    def set_pair_lines(self, on):
+        self._ck(self.lib.gp_set_pair_lines(self.h, int(bool(on))))
+
     def set_threads(self, axis, threads):
         self._ck(self.lib.gp_set_threads(self.h, int(axis), int(threads)))
+
+
+class Batch:
+    """Many independent condensates advanced together in imaginary time.
+
+    problems: sequence of objects with .shape, .d, .dt, .omega, .g (e.g.
+    paper_1601_04641_gb300.inputs.Problem).  All share precision and field.
+    """
+
+    def __init__(self, problems, precision="f32", field="complex", device=None):
+        import torch
+        self._torch = torch
+        self.lib = N.load()
+        self.problems = list(problems)
+        n = len(self.problems)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.np_dtype = _NP_DTYPES[(precision, field)]
+        grids = (N.Grid * n)(*[N.Grid(*p.shape, *p.d) for p in self.problems])
+        arr = lambda vals: (ctypes.c_double * n)(*[float(v) for v in vals])
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            h = N.Handle()
+            st = self.lib.gp_batch_create(ctypes.byref(h), n, grids, arr(p.dt for p in self.problems),
+                                          arr(p.omega[0] for p in self.problems),
+                                          arr(p.omega[1] for p in self.problems),
+                                          arr(p.omega[2] for p in self.problems),
+                                          arr(p.g for p in self.problems),
+                                          N.GP_F64 if precision == "f64" else N.GP_F32,
+                                          N.GP_COMPLEX if field == "complex" else N.GP_REAL,
+                                          ctypes.c_void_p(self.stream.cuda_stream))
+            N.check(st, None, batch=True)
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        N.check(st, self.h, batch=True)
+
+    def init_gaussian(self):
+        self._ck(self.lib.gp_batch_init_gaussian(self.h))
+
+    def set_psi(self, i, arr):
+        a = np.ascontiguousarray(np.asarray(arr), dtype=self.np_dtype)
+        if a.shape != tuple(self.problems[i].shape):
+            raise ValueError("shape mismatch")
+        self._ck(self.lib.gp_batch_set_psi(self.h, int(i), a.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def get_psi(self, i):
+        out = np.empty(tuple(self.problems[i].shape), dtype=self.np_dtype)
+        self._ck(self.lib.gp_batch_get_psi(self.h, int(i), out.ctypes.data_as(ctypes.c_void_p), 0))
+        return out
+
+    def step_imag(self, nsteps=1):
+        self._ck(self.lib.gp_batch_step_imag(self.h, int(nsteps)))
+
+    def observables(self):
+        buf = (N.Obs * self.n)()
+        self._ck(self.lib.gp_batch_observables(self.h, buf))
+        return [{"norm": o.norm, "mu": o.mu, "energy": o.energy, "rms_x": o.rms_x, "rms_y": o.rms_y,
+                 "rms_z": o.rms_z, "step": o.step, "t": o.t} for o in buf]
+
+    def run_imag_until(self, mu_tol, check_every=10, max_steps=100000):
+        taken = (ctypes.c_int * self.n)()
+        self._ck(self.lib.gp_batch_run_imag_until(self.h, float(mu_tol), int(check_every), int(max_steps),
+                                                  taken))
+        return list(taken)
+
+    def window(self):
+        w = (ctypes.c_int * 3)()
+        self._ck(self.lib.gp_batch_get_window(self.h, w))
+        return tuple(w)
+
+    def segments(self, i):
+        a = (ctypes.c_int * 3)()
+        b = (ctypes.c_int * 3)()
+        self._ck(self.lib.gp_batch_get_segments(self.h, int(i), a, b))
+        return tuple(a), tuple(b)
+
+    def set_graph_block(self, steps):
+        self._ck(self.lib.gp_batch_set_graph_block(self.h, int(steps)))

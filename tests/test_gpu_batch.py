@@ -1,0 +1,88 @@
+"""Batched form (GPU): many uneven condensates advanced by one launch per
+sweep covering all instances.  Each instance must equal the single-condensate
+path configured the same way, bit for bit, and the batched convergence loop
+must reach the oracle's ground states."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_04641_gb300 import build, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def uneven(count, seed, scale=0.5, g_max=200.0):
+    """A small uneven batch with the recipe of the 64-instance workload
+    (grids shrunk by `scale` so the oracle stays fast)."""
+    ps = inputs.batch_problems(count, seed=seed, g_max=g_max)
+    out = []
+    for p in ps:
+        shape = tuple(max(5, int(n * scale)) for n in p.shape)
+        q = inputs.sized_box(shape, p.omega, p.g)
+        q.name = p.name
+        out.append(q)
+    return out
+
+
+@pytest.mark.parametrize("prec,field", [("f32", "complex"), ("f64", "real"), ("f32", "real")])
+def test_batch_instances_equal_single_runs(prec, field):
+    from paper_1601_04641_gb300.solver import GP, Batch
+    probs = uneven(7, seed=5)
+    b = Batch(probs, prec, field)
+    b.init_gaussian()
+    b.step_imag(23)                       # graph blocks of 16, then 7 single launches
+    w = b.window()
+    for i, p in enumerate(probs):
+        gp = GP(p.shape, p.d, p.dt, p.omega, p.g, prec, field)
+        gp.set_pair_lines(False)
+        seg, _ = b.segments(i)
+        for ax in range(3):
+            gp.set_axis_window(ax, w[ax])
+            gp.set_segments(ax, seg[ax])
+        gp.init_gaussian()
+        gp.step_imag(23)
+        assert np.array_equal(b.get_psi(i), gp.get_psi()), p.name
+        gp.close()
+    obs = b.observables()
+    assert all(o["step"] == 23 for o in obs)
+    b.close()
+
+
+def test_batch_convergence_matches_oracle_fp64():
+    """FP64 batch run to |dmu| < 1e-9: every instance takes the oracle's
+    number of steps and reaches its mu to 1e-12."""
+    from paper_1601_04641_gb300.solver import Batch
+    probs = uneven(5, seed=9, scale=0.3)
+    b = Batch(probs, "f64", "real")
+    b.init_gaussian()
+    steps = b.run_imag_until(1e-9, 10, 4000)
+    obs = b.observables()
+    for i, p in enumerate(probs):
+        psi = oracle.gaussian(p.shape, p.d, p.omega)
+        n_ref, mu_ref = oracle.run_imag_until(psi, p.d, p.dt, p.omega, p.g, 1e-9, 10, 4000)
+        assert steps[i] == n_ref, (p.name, steps[i], n_ref)
+        assert abs(obs[i]["mu"] - mu_ref) <= 1e-12 * mu_ref
+    b.close()
+
+
+def test_batch_fp32_ground_states_match_oracle():
+    """FP32 complex batch (the 64-instance workload's form) run to
+    |dmu| < 1e-6: mu within 1e-5 of the FP64 oracle run with the same stop
+    rule from the same start."""
+    from paper_1601_04641_gb300.solver import Batch
+    probs = uneven(6, seed=3, scale=0.35)
+    b = Batch(probs, "f32", "complex")
+    b.init_gaussian()
+    steps = b.run_imag_until(1e-6, 10, 20000)
+    obs = b.observables()
+    for i, p in enumerate(probs):
+        psi = oracle.gaussian(p.shape, p.d, p.omega)
+        _, mu_ref = oracle.run_imag_until(psi, p.d, p.dt, p.omega, p.g, 1e-6, 10, 20000)
+        assert steps[i] < 20000
+        assert abs(obs[i]["mu"] - mu_ref) <= 1e-5 * mu_ref, (p.name, obs[i]["mu"], mu_ref)
+    b.close()
