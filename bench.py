@@ -37,6 +37,7 @@ TRACK_EVERY = 10
 WORKLOADS = {
     # name: (problem factory, precision, field, real time, g used to prepare the start state)
     "real_large": (inputs.real_large, "f32", "complex", True),
+    "real_large_half": (inputs.real_large_half, "f32", "complex", True),
     "real_medium": (inputs.real_medium, "f64", "complex", True),
     "imag_small": (inputs.imag_small, "f64", "real", False),
 }
@@ -323,6 +324,44 @@ def e2e_region(torch, res, steps, dist):
     return el, nbytes / steps, (nbytes + obs_bytes) / steps
 
 
+def time_to_ground_state(torch, dev, count, tol, max_steps=20000):
+    """The 64-condensate workload (uneven grids, traps, g) run to
+    |mu(n) - mu(n-10)| < tol: the FP32 batched form against the plain method
+    (FP64, one condensate at a time, same stop rule), both from the Gaussian."""
+    from paper_1601_04641_gb300.solver import GP, Batch
+    probs = inputs.batch_problems(count, seed=0)
+    sites = sum(p.sites for p in probs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = Batch(probs, "f32", "complex", device=dev)
+    b.init_gaussian()
+    steps_b = b.run_imag_until(tol, 10, max_steps)
+    obs_b = b.observables()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    t_plain, steps_p, mu_p = 0.0, [], []
+    for p in probs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gp = GP(p.shape, p.d, p.dt, p.omega, p.g, "f64", "real", device=dev)
+        gp.init_gaussian()
+        steps_p.append(gp.run_imag_until(tol, 10, max_steps))
+        mu_p.append(gp.observables()["mu"])
+        torch.cuda.synchronize()
+        t_plain += time.perf_counter() - t0
+        gp.close()
+    rel = [abs(o["mu"] - m) / m for o, m in zip(obs_b, mu_p)]
+    return {"workload": "%d uneven condensates (seed 0), imaginary time to |dmu| < %g" % (count, tol),
+            "sites_total": sites, "batched_fp32_s": t_batch, "plain_fp64_s": t_plain,
+            "speedup_vs_plain": t_plain / t_batch,
+            "steps_batched": {"min": min(steps_b), "median": sorted(steps_b)[len(steps_b) // 2],
+                              "max": max(steps_b)},
+            "steps_plain": {"min": min(steps_p), "median": sorted(steps_p)[len(steps_p) // 2],
+                            "max": max(steps_p)},
+            "mu_rel_diff_max": max(rel), "converged": sum(s < max_steps for s in steps_b)}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -407,6 +446,8 @@ def run_ours(args):
                               "kernel_ms": {k: 1e3 * v for k, v in kb2.items()}}
                 r2["gp"].close()
         line["also"] = also
+    if args.gs and world == 1:
+        line["time_to_ground_state"] = time_to_ground_state(torch, local, args.gs, 1e-6)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_rate(p, res["realtime"], args.cpu_budget)
     if rank == 0:
@@ -427,6 +468,8 @@ def main():
                     help="comma-separated secondary workloads timed after the main one")
     ap.add_argument("--also-steps", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--gs", type=int, default=64,
+                    help="condensates in the time-to-ground-state comparison (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -55,6 +55,15 @@ def real_large() -> Problem:
                    meta={"steps": 500, "g_prepare": 20.0})
 
 
+def real_large_half() -> Problem:
+    """480x400x160 slab of the 480x400x320 workload (same spacing, dt and
+    trap): a capture-sized case (246 MB complex64, still above L2) for
+    profiling the same kernels."""
+    p = real_large()
+    return Problem((480, 400, 160), p.d, p.dt, p.omega, p.g,
+                   name="real 480x400x160 complex64 (half-depth profiling case)", meta=dict(p.meta))
+
+
 def sized_box(shape, omega, g, dt_factor=0.1) -> Problem:
     """Grid spacing that holds both the g = 0 Gaussian (6 oscillator lengths)
     and 1.3x the Thomas-Fermi radius in the half-box, per axis."""
