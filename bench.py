@@ -45,7 +45,13 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch from `ncu` of each kernel, with the
 # sha256 prefix of the kernel sources they were taken from; a figure whose
 # sources have changed since is reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full of the 480x400x160 half-depth case (profiles/), scaled x2
+    # by sites to a full 480x400x320 launch: (read + write) bytes per launch
+    ("real_large", "zsweep_norm"): (2 * (259.118592e6 + 201.145856e6), "bb1275334eaf72f5"),
+    ("real_large", "kick_xsweep"): (2 * (257.135616e6 + 192.614144e6), "bb1275334eaf72f5"),
+    ("real_large", "ysweep"): (2 * (252.750080e6 + 194.210816e6), "bb1275334eaf72f5"),
+}
 
 
 def kernel_source_hash() -> str:
