@@ -209,6 +209,17 @@ gp_status gp_set_segments(gp_handle h, int axis, int seg_len);
  * real-time (mode 1) step will use. */
 gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]);
 
+/* Autotuner: for each axis, time the line-solve kernel of the imaginary-
+ * (realtime = 0) or real-time (1) step on this handle's grid under every
+ * candidate launch setting -- threads per block (64, 128), segment length
+ * (automatic, 64, 128, 256, whole line) and one or two lines per thread --
+ * with CUDA events over `reps` launches after a warm-up, and keep the
+ * fastest.  psi is left unchanged (the trials run on a copy).  Choices are
+ * cached as text lines "key threads seg pair" in cache_path (NULL: the
+ * GP_AUTOTUNE_CACHE environment variable; unset: no cache); a cached key is
+ * applied without timing.  Synchronises. */
+gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_path);
+
 /* Steps per CUDA graph: gp_step_imag / gp_step_real capture blocks of this
  * many steps into a graph once and replay it (default 16; 0 or 1 launches
  * kernel by kernel).  With tracking on, blocks are track_every steps long.

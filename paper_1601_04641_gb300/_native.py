@@ -62,6 +62,7 @@ SIGNATURES = {
     "gp_set_threads": (_i, [Handle, _i, _i]),
     "gp_set_segments": (_i, [Handle, _i, _i]),
     "gp_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "gp_autotune": (_i, [Handle, _i, _i, ctypes.c_char_p]),
     "gp_set_graph_block": (_i, [Handle, _i]),
     "gp_psi_device_ptr": (_i, [Handle, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
     "gp_observables_noalloc": (_i, [_vp, Grid, _i, _i, _d, _d, _d, _d, _d, _vp, _vp]),

@@ -6,6 +6,10 @@
 #include "gp_internal.h"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -79,7 +83,7 @@ void gpcn::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; 
 namespace {
 
 // Device scalars of a handle.
-enum Scalar { S_SCALE = 0, S_ONE = 1, S_NORM_SWEEP = 2, S_NORM_INIT = 3, S_COUNT = 8 };
+enum Scalar { S_SCALE = 0, S_ONE = 1, S_NORM_SWEEP = 2, S_NORM_INIT = 3, S_SAVE = 4, S_COUNT = 8 };
 
 }  // namespace
 
@@ -810,6 +814,118 @@ gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
     *ptr = h->buf[h->cur];
     if (pending_scale) *pending_scale = h->scale_pending ? 1 : 0;
     return GP_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+namespace {
+
+struct TuneChoice {
+    int threads, seg, pair;
+};
+
+std::string tune_key(gp_handle h, int realtime, int ax) {
+    std::ostringstream k;
+    k << h->n[0] << "x" << h->n[1] << "x" << h->n[2] << (h->prec == GP_F32 ? "/f32" : "/f64")
+      << (h->field == GP_COMPLEX ? "/c" : "/r") << (realtime ? "/rt" : "/it") << "/w" << h->window[realtime][ax]
+      << "/ax" << ax;
+    return k.str();
+}
+
+// Cache file: one "key threads seg pair" line per tuned (grid, form, axis).
+bool cache_lookup(const char *path, const std::string &key, TuneChoice *c) {
+    if (!path || !*path) return false;
+    std::ifstream f(path);
+    std::string k;
+    TuneChoice t;
+    bool found = false;
+    while (f >> k >> t.threads >> t.seg >> t.pair)
+        if (k == key) {
+            *c = t;
+            found = true;
+        }
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const TuneChoice &c) {
+    if (!path || !*path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << " " << c.threads << " " << c.seg << " " << c.pair << "\n";
+}
+
+}  // namespace
+
+gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_path) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (realtime && h->field != GP_COMPLEX) return fail(h, GP_ERR_STATE, "real time needs a GP_COMPLEX field");
+    if (reps < 1) return fail(h, GP_ERR_ARG, "reps must be >= 1");
+    const char *path = cache_path ? cache_path : std::getenv("GP_AUTOTUNE_CACHE");
+    const int mode = realtime ? 1 : 0;
+    // A stage reads buf[cur] and writes only buf[cur ^ 1] (free between
+    // steps), so trials started from cur0 leave psi intact; the z stage of
+    // imaginary time also writes the pending renormalisation factor, which
+    // is saved in a spare scalar slot and restored.
+    const int cur0 = h->cur;
+    const bool pend0 = h->scale_pending;
+    GP_CK(h, cudaMemcpyAsync(h->d_scal + S_SAVE, h->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    cudaEvent_t e0, e1;
+    GP_CK(h, cudaEventCreate(&e0));
+    GP_CK(h, cudaEventCreate(&e1));
+    for (int ax = 0; ax < 3 && st == GP_OK; ++ax) {
+        const std::string key = tune_key(h, realtime, ax);
+        TuneChoice best{h->threads[ax], h->seg_override[ax], h->pair_lines ? 1 : 0};
+        if (cache_lookup(path, key, &best)) {
+            h->threads[ax] = best.threads;
+            h->seg_override[ax] = best.seg;
+            if (ax < 2) h->pair_lines = best.pair != 0;
+            continue;
+        }
+        const int n = h->n[ax] - 2;
+        std::vector<TuneChoice> cands;
+        const int segs[] = {0, 64, 128, 256, n};
+        for (int th : {64, 128})
+            for (int sg : segs)
+                for (int pr : {1, 0}) {
+                    if (ax == 2 && pr == 0) continue;  // pairs apply to the strided axes only
+                    if (h->window[mode][ax] == 0 && sg != 0) continue;  // the exact solve has no segments
+                    cands.push_back({th, sg, pr});
+                }
+        float best_ms = 1e30f;
+        for (const TuneChoice &c : cands) {
+            h->threads[ax] = c.threads;
+            h->seg_override[ax] = c.seg;
+            if (ax < 2) h->pair_lines = c.pair != 0;
+            float ms = 0.f;
+            for (int r = 0; r <= reps && st == GP_OK; ++r) {  // r = 0 warms up
+                h->cur = cur0;
+                h->scale_pending = pend0;
+                if (r == 1) GP_CK(h, cudaEventRecord(e0, h->stream));
+                st = run_stage(h, ax, realtime);
+            }
+            if (st != GP_OK) break;
+            GP_CK(h, cudaEventRecord(e1, h->stream));
+            GP_CK(h, cudaEventSynchronize(e1));
+            GP_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        h->threads[ax] = best.threads;
+        h->seg_override[ax] = best.seg;
+        if (ax < 2) h->pair_lines = best.pair != 0;
+        cache_store(path, key, best);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cur = cur0;
+    h->scale_pending = pend0;
+    GP_CK(h, cudaMemcpyAsync(h->d_scal, h->d_scal + S_SAVE, 4 * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    return st;
 }
 
 gp_status gp_set_graph_block(gp_handle h, int steps) {

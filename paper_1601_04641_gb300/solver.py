@@ -160,6 +160,11 @@ class GP:
         self._ck(self.lib.gp_get_segments(self.h, int(mode), a, b))
         return tuple(a), tuple(b)
 
+    def autotune(self, realtime=False, reps=5, cache_path=None):
+        """Time candidate launch settings per axis and keep the fastest."""
+        self._ck(self.lib.gp_autotune(self.h, int(bool(realtime)), int(reps),
+                                      cache_path.encode() if cache_path else None))
+
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_set_graph_block(self.h, int(steps)))
 
@@ -258,6 +263,11 @@ class Batch:
         b = (ctypes.c_int * 3)()
         self._ck(self.lib.gp_batch_get_segments(self.h, int(i), a, b))
         return tuple(a), tuple(b)
+
+    def autotune(self, realtime=False, reps=5, cache_path=None):
+        """Time candidate launch settings per axis and keep the fastest."""
+        self._ck(self.lib.gp_autotune(self.h, int(bool(realtime)), int(reps),
+                                      cache_path.encode() if cache_path else None))
 
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_batch_set_graph_block(self.h, int(steps)))

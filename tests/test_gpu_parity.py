@@ -223,6 +223,27 @@ def test_graph_blocks_equal_single_launches(realtime):
         assert track == runs[0][1]
 
 
+def test_autotune_keeps_results_and_caches(tmp_path):
+    """The autotuner leaves psi unchanged, its choice gives the oracle's step,
+    and a second handle reads the choice back from the cache file."""
+    dt, g = 0.004, 12.0
+    psi0 = inputs.random_field(EVEN, seed=41)
+    cache = str(tmp_path / "tune.txt")
+    gp = make(EVEN, D, dt, OMEGA, g, "f32")
+    gp.set_psi(psi0.astype(np.complex64))
+    gp.autotune(True, 2, cache)
+    assert np.array_equal(gp.get_psi(), psi0.astype(np.complex64))
+    gp.step_real(2)
+    ref = psi0.astype(np.complex64).astype(np.complex128)
+    oracle.step(ref, D, dt, OMEGA, g, True, 2)
+    assert rel_max(gp.get_psi().astype(np.complex128), ref) <= 2e-6
+    lines = open(cache).read().split("\n")
+    assert len([ln for ln in lines if ln.strip()]) == 3
+    gp2 = make(EVEN, D, dt, OMEGA, g, "f32")
+    gp2.autotune(True, 2, cache)
+    assert len([ln for ln in open(cache).read().split("\n") if ln.strip()]) == 3
+
+
 # ---------------------------------------------------------------- observables
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
 def test_observables_of_a_random_field(prec, tol):
