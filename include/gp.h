@@ -298,6 +298,52 @@ gp_status gp_batch_set_graph_block(gp_batch b, int steps);
 /* Last error of the batch (NULL: as gp_last_error(NULL)). */
 const char *gp_batch_last_error(gp_batch b);
 
+/* ------------------------------------------------------------------ warm start
+ * A learned initial state for imaginary time (no counterpart in the paper,
+ * which starts from a Gaussian): a conditioned coordinate MLP maps a grid
+ * node x of a condensate with trap (gamma, nu, lambda) and nonlinearity g to
+ * an amplitude.  Features: x_a sqrt(w_a)/4; min(sum (x_a/R_a)^2, 4)/2 - 1
+ * with the Thomas-Fermi radii R_a = sqrt(2 mu_TF)/w_a, mu_TF =
+ * (15 g w_x w_y w_z / 4 pi)^(2/5)/2; min(sum w_a x_a^2, 16)/8 - 1;
+ * (ln g - 3.1)/3.1; (w_a - 1.75)/1.25 (9 used, padded to 16).  Layers: three
+ * 64-wide tanh layers, then softplus(h . w3 + b3).  Parameters, FP32 master,
+ * in this order ([in][out] row-major): W0 16x64, b0, W1 64x64, b1, W2 64x64,
+ * b2, w3 64, b3 (gp_nn_param_count() floats).  Forward, backward and the
+ * Adam step run on the GPU; the matrix layers use BF16 tensor-core
+ * operands with FP32 accumulation. */
+typedef struct gp_nn_s *gp_nn;
+
+int gp_nn_param_count(void);
+/* Glorot-uniform weights from SplitMix64(seed), zero biases. */
+gp_status gp_nn_create(gp_nn *out, unsigned long long seed, void *cuda_stream);
+void gp_nn_destroy(gp_nn net);
+/* Set / get the FP32 master parameters (host arrays of gp_nn_param_count()).
+ * Setting resets the Adam state. */
+gp_status gp_nn_set_params(gp_nn net, const float *params, int count);
+gp_status gp_nn_get_params(gp_nn net, float *params, int count);
+/* Training set: n condensates (grid, trap, g) whose target amplitudes are
+ * float32 arrays in the psi layout inside the caller's device buffer
+ * dev_data (kept alive by the caller), instance i at element offsets[i];
+ * the target of a node is its amplitude divided by psi_max[i]. */
+gp_status gp_nn_set_data(gp_nn net, int n, const gp_grid *grids, const double *gamma,
+                         const double *nu, const double *lambda, const double *g,
+                         const float *dev_data, const long long *offsets, const float *psi_max);
+/* `steps` Adam steps (learning rate lr) on the mean squared error of
+ * `points` nodes per step (a multiple of 128) drawn uniformly over the
+ * instances and their nodes by SplitMix64 from seed; *loss (may be NULL)
+ * receives the last step's loss. */
+gp_status gp_nn_train(gp_nn net, int steps, int points, float lr, unsigned long long seed, float *loss);
+/* Loss and gradient (host array of gp_nn_param_count()) on explicit samples
+ * (instance index, node index), count a multiple of 128; no update. */
+gp_status gp_nn_loss_grad(gp_nn net, int count, const int *instance, const long long *site,
+                          float *loss, float *grad);
+/* psi <- the network's prediction on the handle's grid (boundary nodes 0),
+ * normalised; resets step and t. */
+gp_status gp_nn_predict(gp_nn net, gp_handle h);
+/* The same for every instance of a batch. */
+gp_status gp_nn_predict_batch(gp_nn net, gp_batch b);
+const char *gp_nn_last_error(gp_nn net);
+
 /* Last error message for this handle (or for the calling thread's last
  * failed create, or failed gp_observables_noalloc, when h is NULL).  Never
  * NULL. */

@@ -80,6 +80,20 @@ SIGNATURES = {
     "gp_batch_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_batch_set_graph_block": (_i, [Handle, _i]),
     "gp_batch_last_error": (ctypes.c_char_p, [Handle]),
+    "gp_nn_param_count": (_i, []),
+    "gp_nn_create": (_i, [ctypes.POINTER(Handle), ctypes.c_ulonglong, _vp]),
+    "gp_nn_destroy": (None, [Handle]),
+    "gp_nn_set_params": (_i, [Handle, ctypes.POINTER(ctypes.c_float), _i]),
+    "gp_nn_get_params": (_i, [Handle, ctypes.POINTER(ctypes.c_float), _i]),
+    "gp_nn_set_data": (_i, [Handle, _i, ctypes.POINTER(Grid), ctypes.POINTER(_d), ctypes.POINTER(_d),
+                            ctypes.POINTER(_d), ctypes.POINTER(_d), _vp, ctypes.POINTER(ctypes.c_longlong),
+                            ctypes.POINTER(ctypes.c_float)]),
+    "gp_nn_train": (_i, [Handle, _i, _i, ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
+    "gp_nn_loss_grad": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "gp_nn_predict": (_i, [Handle, Handle]),
+    "gp_nn_predict_batch": (_i, [Handle, Handle]),
+    "gp_nn_last_error": (ctypes.c_char_p, [Handle]),
     "gp_last_error": (ctypes.c_char_p, [Handle]),
     "gp_version": (ctypes.c_char_p, []),
 }
@@ -111,8 +125,13 @@ def load():
     return _lib
 
 
-def check(status, handle=None, batch=False):
+def check(status, handle=None, batch=False, nn=False):
     if status != GP_OK:
         lib = load()
-        msg = lib.gp_batch_last_error(handle) if batch else lib.gp_last_error(handle)
+        if nn:
+            msg = lib.gp_nn_last_error(handle)
+        elif batch:
+            msg = lib.gp_batch_last_error(handle)
+        else:
+            msg = lib.gp_last_error(handle)
         raise GPError(status, msg.decode() if msg else "")

@@ -4,6 +4,7 @@
 #include "gp.h"
 #include "gp_host.h"
 #include "gp_internal.h"
+#include "gp_nn_internal.h"
 
 #include <algorithm>
 #include <cstdio>
@@ -926,6 +927,21 @@ gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_pat
     GP_CK(h, cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     return st;
+}
+
+gp_status gp_nn_predict(gp_nn net, gp_handle h) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    const NNParams *P = nn_params(net);
+    if (!P) return fail(h, GP_ERR_ARG, "NULL network");
+    const NNInstance I = make_nn_instance(h->n, h->d, h->w, h->g);
+    GP_CK(h, nn_launch_predict(*P, I, h->buf[h->cur], h->prec == GP_F32, h->field == GP_COMPLEX, h->stream));
+    FieldArgs a = handle_field_args(h);
+    GP_CK(h, launch_norm(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
+    h->scale_pending = true;
+    h->step = 0;
+    h->t = 0.0;
+    return GP_OK;
 }
 
 gp_status gp_set_graph_block(gp_handle h, int steps) {

@@ -7,6 +7,7 @@
 #include "gp.h"
 #include "gp_host.h"
 #include "gp_internal.h"
+#include "gp_nn_internal.h"
 
 #include <algorithm>
 #include <cmath>
@@ -559,6 +560,25 @@ gp_status gp_batch_get_segments(gp_batch b, int i, int seg_len[3], int n_seg[3])
     for (int ax = 0; ax < 3; ++ax) {
         seg_len[ax] = b->inst[i].seg_len[ax];
         n_seg[ax] = b->inst[i].n_seg[ax];
+    }
+    return GP_OK;
+}
+
+gp_status gp_nn_predict_batch(gp_nn net, gp_batch b) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    const NNParams *P = nn_params(net);
+    if (!P) return bfail(b, GP_ERR_ARG, "NULL network");
+    const Prec p = b->prec == GP_F32 ? P_F32 : P_F64;
+    const bool cplx = b->field == GP_COMPLEX;
+    for (int i = 0; i < b->n; ++i) {
+        Inst &I = b->inst[i];
+        const NNInstance ni = make_nn_instance(I.G.n, I.G.d, I.G.w, I.G.g);
+        GPB_CK(b, nn_launch_predict(*P, ni, b->d_psi[I.cur] + I.psi_off, b->prec == GP_F32, cplx, b->stream));
+        FieldArgs a = inst_field_args(b, i);
+        GPB_CK(b, launch_norm(p, cplx, a, kInitNormBlocks, b->stream));
+        I.step = 0;
+        I.t = 0.0;
     }
     return GP_OK;
 }
