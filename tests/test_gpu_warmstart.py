@@ -99,7 +99,9 @@ def test_training_reduces_the_loss():
 def test_warm_start_gain_on_held_out_condensates():
     """Trained on the method's own ground states, the network's start reaches
     |dmu| < 1e-7 in fewer imaginary-time steps than the Gaussian on held-out
-    parameters, and both starts converge to the same mu."""
+    parameters, and both starts reach the same mu (to 1e-5 relative: the stop
+    rule leaves a residual of about tol r / (1 - r) for a contraction r per
+    check, so two starts stop up to a few tol apart)."""
     from paper_1601_04641_gb300 import warmstart as W
     shape = (40, 32, 28)
     train_p = [inputs.sized_box(shape, p.omega, p.g) for p in inputs.batch_problems(96, seed=21, g_max=500.0)]
@@ -109,10 +111,12 @@ def test_warm_start_gain_on_held_out_condensates():
     net.set_data(train_p, data, offsets, pmax)
     W.train(net, 3000, points=16384)
     r = W.run_from_starts(net, held, 1e-7)
-    gain = np.median(np.array(r["steps_gauss"]) / np.array(r["steps_nn"]))
-    assert gain > 1.2, r
+    ratio = np.array(r["steps_gauss"]) / np.array(r["steps_nn"])
+    print("warm-start step ratio (gauss / nn): median %.2f min %.2f max %.2f, fallbacks %d" %
+          (np.median(ratio), ratio.min(), ratio.max(), sum(r["fallback"])))
+    assert np.median(ratio) > 1.2, r
     for a, b in zip(r["mu_gauss"], r["mu_nn"]):
-        assert abs(a - b) <= 1e-6 * abs(a)
+        assert abs(a - b) <= 1e-5 * abs(a)
     net.close()
 
 
