@@ -368,6 +368,43 @@ def time_to_ground_state(torch, dev, count, tol, max_steps=20000):
             "mu_rel_diff_max": max(rel), "converged": sum(s < max_steps for s in steps_b)}
 
 
+def warm_start(torch, dev, n_train, n_held, steps, tol=1e-7):
+    """The learned warm start on 128x96x80 condensates: targets from the
+    batched FP32 solver (|dmu| < 1e-6), GPU training, then FP64 imaginary time
+    to |dmu| < tol on held-out parameters from the Gaussian and from the
+    network's prediction (energy fallback)."""
+    import numpy as np
+    from paper_1601_04641_gb300 import warmstart as W
+    shape = (128, 96, 80)
+    tp = [inputs.sized_box(shape, p.omega, p.g) for p in inputs.batch_problems(n_train, seed=1, g_max=500.0)]
+    hp = [inputs.sized_box(shape, p.omega, p.g) for p in inputs.batch_problems(n_held, seed=2, g_max=500.0)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    data, offs, pmax, _ = W.ground_states(tp, 1e-6, max_steps=30000, device=dev)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = W.Net(seed=0, device=dev)
+    net.set_data(tp, data, offs, pmax)
+    t0 = time.perf_counter()
+    losses = W.train(net, steps, points=32768, lr=(3e-3, 1e-4))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    r = W.run_from_starts(net, hp, tol, precision="f64", field="real", device=dev)
+    net.close()
+    del data
+    ratio = np.array(r["steps_gauss"], dtype=float) / np.array(r["steps_nn"], dtype=float)
+    mu_rel = max(abs(a - b) / abs(a) for a, b in zip(r["mu_gauss"], r["mu_nn"]))
+    return {"workload": "128x96x80 condensates, gamma,nu,lambda ~ U[0.5,3], log g ~ U[0, ln 500]; "
+                        "%d training ground states (FP32 batched, |dmu| < 1e-6), %d held-out, FP64 imaginary "
+                        "time to |dmu| < %g" % (n_train, n_held, tol),
+            "data_s": t_data, "train_s": t_train, "train_steps": steps, "final_loss": losses[-1],
+            "steps_ratio_gauss_over_nn": {"median": float(np.median(ratio)), "mean": float(ratio.mean()),
+                                          "min": float(ratio.min()), "max": float(ratio.max())},
+            "time_gauss_s": r["time_gauss_s"], "time_nn_s": r["time_nn_s"],
+            "time_speedup": r["time_gauss_s"] / r["time_nn_s"], "fallbacks": int(sum(r["fallback"])),
+            "mu_rel_diff_max": mu_rel}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -454,6 +491,8 @@ def run_ours(args):
         line["also"] = also
     if args.gs and world == 1:
         line["time_to_ground_state"] = time_to_ground_state(torch, local, args.gs, 1e-6)
+    if args.ws_train and world == 1:
+        line["warm_start"] = warm_start(torch, local, args.ws_train, args.ws_held, args.ws_steps)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_rate(p, res["realtime"], args.cpu_budget)
     if rank == 0:
@@ -476,6 +515,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--gs", type=int, default=64,
                     help="condensates in the time-to-ground-state comparison (0: skip)")
+    ap.add_argument("--ws-train", type=int, default=400,
+                    help="training ground states of the warm-start comparison (0: skip; 2000 = full set)")
+    ap.add_argument("--ws-held", type=int, default=50, help="held-out condensates (200 = full set)")
+    ap.add_argument("--ws-steps", type=int, default=8000, help="Adam steps")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
