@@ -173,7 +173,9 @@ gp_status gp_step_stage(gp_handle h, int stage, int realtime);
  * default stream). */
 gp_status gp_set_stream(gp_handle h, void *cuda_stream);
 
-/* Block until the handle's queued work is done. */
+/* Block until the handle's queued work is done.  Returns GP_ERR_CUDA if a
+ * sweep kernel gave up waiting for its TMA copies (each wait is bounded to
+ * about a second); gp_observables reports the same. */
 gp_status gp_sync(gp_handle h);
 
 /* Window of the windowed back substitution per axis for imaginary (mode 0)
@@ -195,6 +197,18 @@ gp_status gp_set_axis_window(gp_handle h, int axis, int window);
 /* Two adjacent lines per thread on the strided axes (1, the default, where
  * the layout allows it) or one (0).  The arithmetic per line is the same. */
 gp_status gp_set_pair_lines(gp_handle h, int on);
+
+/* The z sweep (stride-1 axis) through tensor-memory-accelerator tiles: one
+ * bulk tensor copy per 64 lines x 64 bytes, two lines per thread (1, the
+ * default), or through per-thread asynchronous copies (0).  The TMA form is
+ * taken where the rows allow it: 4- or 8-byte elements, nz * element size a
+ * multiple of 16 bytes, a window > 0, whole lines, and nz - 2 at least one
+ * chunk (64 bytes of nodes) plus the window plus 2; elsewhere the other form
+ * runs.  The arithmetic per line is the same in both.  gp_get_tma reports
+ * whether the handle's buffers have tensor maps and the form is selected
+ * (the per-launch conditions above still apply). */
+gp_status gp_set_tma(gp_handle h, int on);
+gp_status gp_get_tma(gp_handle h, int *in_use);
 
 /* Threads per block of the line-solve kernel of one axis (multiple of 32,
  * 32..256). */

@@ -59,6 +59,8 @@ SIGNATURES = {
     "gp_set_window": (_i, [Handle, _i]),
     "gp_set_axis_window": (_i, [Handle, _i, _i]),
     "gp_set_pair_lines": (_i, [Handle, _i]),
+    "gp_set_tma": (_i, [Handle, _i]),
+    "gp_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_set_threads": (_i, [Handle, _i, _i]),
     "gp_set_segments": (_i, [Handle, _i, _i]),
     "gp_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),

@@ -115,6 +115,10 @@ struct gp_handle_s {
     double t = 0;
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
+    bool tma_z = true;         // ... through TMA tiles where the grid allows it
+    bool zmap_ok = false;      // zmap[b]: tensor map of buf[b] as n_lines rows of nz elements
+    CUtensorMap zmap[2];
+    unsigned int *d_status = nullptr;  // nonzero after a kernel's bounded wait expired
     bool pair_lines = true;    // two lines per thread on the strided axes when possible
     int seg_override[3] = {0, 0, 0};  // interior nodes per segment, 0 = automatic
     // observables history queued during stepping
@@ -234,14 +238,15 @@ gp_status alloc_scratch(gp_handle h) {
     if (cudaMalloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_scal, S_COUNT * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_obs, O_COUNT * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->d_counter, sizeof(unsigned int)) != cudaSuccess) {
+        cudaMalloc(&h->d_counter, 2 * sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         return fail(h, GP_ERR_NOMEM, "cudaMalloc of reduction scratch failed");
     }
     h->partial_cap = cap;
+    h->d_status = h->d_counter + 1;
     double init[S_COUNT] = {1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     GP_CK(h, cudaMemcpyAsync(h->d_scal, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-    GP_CK(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned int), h->stream));
+    GP_CK(h, cudaMemsetAsync(h->d_counter, 0, 2 * sizeof(unsigned int), h->stream));
     GP_CK(h, cudaStreamSynchronize(h->stream));
     return GP_OK;
 }
@@ -323,6 +328,11 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
     }
     st = alloc_scratch(h);
     if (st == GP_OK) st = build_coefficients(h);
+    {
+        const long long rows = (long long)grid.nx * grid.ny;
+        h->zmap_ok = encode_z_map(&h->zmap[0], h->buf[0], grid.nz, rows, (int)h->elem) &&
+                     encode_z_map(&h->zmap[1], h->buf[1], grid.nz, rows, (int)h->elem);
+    }
     if (st != GP_OK) {
         g_create_error = h->err;
         release(h);
@@ -342,6 +352,17 @@ gp_status enter(gp_handle h) {
 }
 
 gp_status queue_observables(gp_handle h, double *dst);
+
+// After a synchronisation: a kernel whose bounded wait expired left a flag.
+gp_status check_status(gp_handle h) {
+    unsigned int flag = 0;
+    GP_CK(h, cudaMemcpy(&flag, h->d_status, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(h->d_status, 0, sizeof(flag));
+        return fail(h, GP_ERR_CUDA, "a sweep kernel's wait for its TMA copies expired; psi is not trustworthy");
+    }
+    return GP_OK;
+}
 
 // Two adjacent lines per thread on the strided axes when every pair is
 // adjacent in memory and 2-element aligned: an even number of lines and,
@@ -373,10 +394,17 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     L.contiguous = (ax == 2 && h->contiguous_z && L.window > 0) ? 1 : 0;
     int seg_len = 0, n_seg = 0;
     segments(h, ax, L.window, &seg_len, &n_seg);
-    const SweepArgs a = sweep_args(geom(h), ax, realtime, h->buf[h->cur], h->buf[h->cur ^ 1], h->d_coef,
-                                   h->tab, seg_len, n_seg,
-                                   h->d_scal + (h->scale_pending ? S_SCALE : S_ONE), h->d_partials,
-                                   h->d_counter, h->d_scal + S_NORM_SWEEP, h->d_scal + S_SCALE);
+    SweepArgs a = sweep_args(geom(h), ax, realtime, h->buf[h->cur], h->buf[h->cur ^ 1], h->d_coef,
+                             h->tab, seg_len, n_seg,
+                             h->d_scal + (h->scale_pending ? S_SCALE : S_ONE), h->d_partials,
+                             h->d_counter, h->d_scal + S_NORM_SWEEP, h->d_scal + S_SCALE);
+    a.status = h->d_status;
+    TmaMaps maps;
+    if (L.contiguous && h->tma_z && h->zmap_ok) {
+        maps.in = h->zmap[h->cur];
+        maps.out = h->zmap[h->cur ^ 1];
+        L.tma = &maps;
+    }
     const int zthreads = L.contiguous ? 32 : L.threads;
     if (stage == 2 && blocks_for(a.n_lines, zthreads) * (size_t)a.n_seg > h->partial_cap)
         return fail(h, GP_ERR_STATE, "z sweep grid exceeds the partials buffer");
@@ -531,6 +559,8 @@ gp_status observables(gp_handle h, gp_obs *out) {
     GP_CK(h, cudaMemcpyAsync(o, h->d_obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
     GP_CK(h, cudaStreamSynchronize(h->stream));
     if (out) fill_obs(o, h->step, h->t, out);
+    st = check_status(h);
+    if (st != GP_OK) return st;
     if (o[O_FINITE] != 1.0) return fail(h, GP_ERR_NONFINITE, "psi holds NaN or Inf");
     return GP_OK;
 }
@@ -731,7 +761,7 @@ gp_status gp_sync(gp_handle h) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     GP_CK(h, cudaStreamSynchronize(h->stream));
-    return GP_OK;
+    return check_status(h);
 }
 
 gp_status gp_get_window(gp_handle h, int mode, int window[3]) {
@@ -783,6 +813,19 @@ gp_status gp_set_pair_lines(gp_handle h, int on) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
     h->pair_lines = on != 0;
     drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_set_tma(gp_handle h, int on) {
+    if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    h->tma_z = on != 0;
+    drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_get_tma(gp_handle h, int *in_use) {
+    if (!h || !in_use) return fail(h, GP_ERR_ARG, "bad arguments");
+    *in_use = (h->tma_z && h->zmap_ok && h->contiguous_z) ? 1 : 0;
     return GP_OK;
 }
 

@@ -212,4 +212,45 @@ FieldArgs field_args(const Geometry &G, const void *psi, const double *scale, do
     return a;
 }
 
+// ------------------------------------------------------------------ TMA maps
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+}  // namespace
+
+// Boxes of 64 bytes of a row x 64 rows, 64-byte swizzle, zero fill outside
+// the array (the layout gp_sweep_tma.cuh reads and writes).
+bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, int elem_bytes) {
+    if (elem_bytes != 4 && elem_bytes != 8) return false;
+    if (((long long)N * elem_bytes) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+    if (n_lines <= 0 || n_lines > 0x7fffffffLL || N <= 0) return false;
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)n_lines};
+    const cuuint64_t strides[1] = {(cuuint64_t)N * (cuuint64_t)elem_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(64 / elem_bytes), 64u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUtensorMapDataType dt = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return enc(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace gpcn

@@ -2,6 +2,7 @@
 // the kernel translation units.  Host-visible plain structs only.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -50,6 +51,13 @@ struct SweepArgs {
     double *scale_out;     // 1 / sqrt(norm) when want_scale
     double dV;
     int want_scale;
+    unsigned int *status;  // set to nonzero by a kernel whose bounded wait expired (may be null)
+};
+
+// Tensor maps of the z sweep's input and output arrays, each a 2D array of
+// n_lines rows of N elements (see gp_sweep_tma.cuh).
+struct TmaMaps {
+    CUtensorMap in, out;
 };
 
 struct SweepLaunch {
@@ -60,6 +68,7 @@ struct SweepLaunch {
     int threads;           // threads per block
     int lpt;               // lines per thread of the strided kernel (1, or 2 adjacent lines)
     int contiguous;        // 1: warp-tiled kernel for the stride-1 axis
+    const TmaMaps *tma = nullptr;  // z sweep through TMA tiles where the grid allows it
 };
 
 cudaError_t launch_sweep(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s);
@@ -115,6 +124,10 @@ cudaError_t launch_sweep_batch(const SweepLaunch &L, const BatchLaunch &b, cudaS
 // Threads per block of the batched kernels.
 constexpr int kBatchLineThreads = 64;
 void set_thread_error(const char *msg);
+// Encode the tensor map of an array of n_lines rows of N elements of
+// elem_bytes (4 or 8) for the TMA z sweep; false if the layout does not allow
+// one (row pitch or base not 16-byte aligned) or the driver has no encoder.
+bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, int elem_bytes);
 constexpr int kReduceThreads = 256;
 
 }  // namespace gpcn

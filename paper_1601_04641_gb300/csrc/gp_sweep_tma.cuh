@@ -1,0 +1,329 @@
+// gp_sweep_tma.cuh -- z sweep (the stride-1 axis) through the tensor memory
+// accelerator.
+//
+// With x slowest and z fastest, the z lines are the rows of a 2D array
+// [n_lines][N].  A warp owns 64 consecutive rows and advances two of them
+// per lane (rows lane and lane + 32, as one FPair), walking them in boxes of
+// B nodes x 64 rows, where B nodes fill 64 bytes of a row (8 complex64 or 16
+// float values).  One lane issues each box as a cp.async.bulk.tensor load
+// into a four-slot ring of shared memory (one mbarrier per slot); the box
+// being read and the next one are resident while two more are in flight.
+// Boxes land in the 64-byte swizzled layout (the 16-byte unit u of row r is
+// stored at unit u ^ ((r / 2) mod 4)), so the 8 lanes of a quarter warp
+// reading one column of their own rows hit 8 different bank groups.
+//
+// Each chunk of B results goes back the same way: written into a swizzled
+// output tile and stored by one TMA instruction.  A TMA row must start on a
+// 16-byte boundary and the first interior node is node 1, so tile k holds
+// nodes [kB, kB + B): the chunk's last result is carried in registers into
+// slot 0 of the next tile, and node 0 and node N-1 (the Dirichlet ends) are
+// written as zeros.  Rows past the last line read zeros (TMA fill) and are
+// clipped on store; so are nodes past N-1.
+//
+// Every wait on an mbarrier is bounded (about a second of clock cycles);
+// on expiry the warp stops waiting, finishes without trusting its data and
+// raises SweepArgs::status, which the host checks when it synchronises.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+#include "gp_sweep.cuh"
+
+namespace gpcn {
+
+constexpr int kTmaWarps = 2;                         // warps per block
+constexpr int kTmaRows = 64;                         // lines per warp (two per lane)
+constexpr int kTmaRowBytes = 64;                     // one box row = one swizzle span
+constexpr int kTmaBoxBytes = kTmaRows * kTmaRowBytes;
+constexpr int kTmaSlots = 4;                         // input ring
+constexpr int kTmaWarpBytes = (kTmaSlots + 1) * kTmaBoxBytes;  // ring + output tile
+constexpr size_t kTmaSmemBytes = 1024 + (size_t)kTmaWarps * kTmaWarpBytes + kTmaWarps * kTmaSlots * 8;
+constexpr long long kTmaSpinCycles = 1LL << 31;
+
+template <typename E> __host__ __device__ constexpr int tma_chunk() { return kTmaRowBytes / (int)sizeof(E); }
+
+// Whether a z sweep can take the TMA kernel: 4- or 8-byte elements, whole
+// lines (one segment), rows that start on 16-byte boundaries, and lines of
+// at least one full chunk plus its window and two nodes.
+template <class F, int W> inline bool tma_usable(const SweepArgs &a) {
+    using E = typename F::V;
+    if constexpr (sizeof(E) != 4 && sizeof(E) != 8) {
+        return false;
+    } else {
+        return a.n_seg == 1 && a.N - 2 >= tma_chunk<E>() + W + 2 && ((long long)a.N * sizeof(E)) % 16 == 0 &&
+               a.n_lines <= 0x7fffffffLL;
+    }
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of `bar` with the given parity, for at most `limit`
+// clock cycles (none at all once `ok` is false).  Returns false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, bool ok) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (!ok) return false;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kTmaSpinCycles) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, unsigned src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// Generic-proxy writes to shared memory become visible to later TMA reads.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+template <typename E> struct __align__(2 * sizeof(E)) E2 { E x, y; };
+
+// One warp's 64 lines, whole lines, window W.  Returns the lane's partial
+// sum of |phi|^2 over its two lines.
+template <class F, typename R, int W>
+__device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap *tin, const CUtensorMap *tout,
+                                           unsigned char *wbase, unsigned bar0, int y0) {
+    using E = typename F::V;
+    using M = FPair<F>;
+    using V = typename M::V;
+    using C = typename F::C;
+    constexpr int B = tma_chunk<E>();
+    constexpr int ES = sizeof(E);
+    static_assert(W % 2 == 0 && B % 2 == 0, "node pairs must not straddle a 16-byte unit");
+    const int lane = threadIdx.x & 31;
+    const int N = a.N, n = N - 2;
+    const int nbox = (N - 1) / B + 1;  // boxes covering nodes 0 .. N-1
+    const C *cp = static_cast<const C *>(a.cp);
+    const C *ipm1 = static_cast<const C *>(a.ip);
+    const R kap = (R)a.kappa;
+    const unsigned ring = smem_u32(wbase);
+    unsigned char *const otile = wbase + kTmaSlots * kTmaBoxBytes;
+    const unsigned otile_s = ring + kTmaSlots * kTmaBoxBytes;
+    const unsigned xm = ((lane >> 1) & 3) << 4;  // swizzle of rows lane and lane + 32
+    const unsigned ra = lane * kTmaRowBytes, rb = (lane + 32) * kTmaRowBytes;
+
+    if (lane == 0) {
+        for (int s = 0; s < kTmaSlots; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    auto issue = [&](int b) {
+        const unsigned s = b & (kTmaSlots - 1);
+        mbar_arrive_expect_tx(bar0 + 8 * s, kTmaBoxBytes);
+        tma_load_2d(ring + s * kTmaBoxBytes, tin, bar0 + 8 * s, b * B, y0);
+    };
+    int issued = min(3, nbox), waited = 0;
+    bool ok = true;
+    if (lane == 0)
+        for (int b = 0; b < issued; ++b) issue(b);
+    // Make box k readable and keep boxes up to k + 2 in flight.  Box k + 2
+    // reuses the slot of box k - 2, so no read of a box below k - 1 may
+    // follow this call.
+    auto need = [&](int k) {
+        if (k < waited) return;
+        for (; waited <= k; ++waited)
+            ok = mbar_wait_bounded(bar0 + 8 * (waited & (kTmaSlots - 1)), (waited / kTmaSlots) & 1, ok) && ok;
+        __syncwarp();
+        const int lim = min(k + 3, nbox);
+        if (lane == 0)
+            for (int b = issued; b < lim; ++b) issue(b);
+        issued = max(issued, lim);
+    };
+    // Nodes c, c+1 (c even) of box k, for both of the lane's rows.
+    auto rd2 = [&](int k, int c, V &v0, V &v1) {
+        const unsigned char *slot = wbase + (k & (kTmaSlots - 1)) * kTmaBoxBytes;
+        const unsigned off = (unsigned)(c * ES) ^ xm;
+        const E2<E> pa = *reinterpret_cast<const E2<E> *>(slot + ra + off);
+        const E2<E> pb = *reinterpret_cast<const E2<E> *>(slot + rb + off);
+        v0 = V{pa.x, pb.x};
+        v1 = V{pa.y, pb.y};
+    };
+    auto wr = [&](int s, V v) {  // slot s of the output tile
+        const unsigned off = (unsigned)(s * ES) ^ xm;
+        *reinterpret_cast<E *>(otile + ra + off) = v.a;
+        *reinterpret_cast<E *>(otile + rb + off) = v.b;
+    };
+    auto tile_free = [&]() {  // the previous tile store has read the tile
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp();
+    };
+    auto store_tile = [&](int x) {
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            tma_store_2d(tout, otile_s, x, y0);
+            bulk_commit();
+        }
+    };
+
+    Acc<R> acc;
+    V carry = M::zero();  // slot 0 of the next tile (node 0 for the first)
+    V D[B + W];
+    V pm = M::zero(), p0, p1, p1n;
+    V dprev = M::zero();
+    // warm-up: dp[0 .. W-1]; dp[t] reads nodes t, t+1, t+2
+    need(0);
+    rd2(0, 0, p1n, p0);  // node 0 is the Dirichlet end: pm stays zero
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        if ((t & 1) == 0) {
+            need((t + 2) / B);
+            rd2((t + 2) / B, (t + 2) % B, p1, p1n);
+        } else {
+            p1 = p1n;
+        }
+        dprev = M::fwd(M::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t));
+        D[t] = dprev;
+        pm = p0;
+        p0 = p1;
+    }
+    int t0 = 0;
+    for (; t0 + B + W <= n; t0 += B) {
+        const int j = t0 / B;
+        need(j + (W + B + 1) / B);
+        const bool last_full = t0 + B + W == n;  // the chunk's last read is node N-1
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            if ((q & 1) == 0) {
+                rd2(j + (W + 2 + q) / B, (W + 2 + q) % B, p1, p1n);
+                if (q == B - 2 && last_full) p1n = M::zero();
+            } else {
+                p1 = p1n;
+            }
+            dprev = M::fwd(M::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + W + q));
+            D[W + q] = dprev;
+            pm = p0;
+            p0 = p1;
+        }
+        tile_free();
+        V phi = D[B + W - 1];
+#pragma unroll
+        for (int q = B + W - 2; q >= B; --q) phi = M::back(D[q], ldc(cp + t0 + q), phi);
+        R csum = R(0);
+        V next = M::zero();
+#pragma unroll
+        for (int q = B - 1; q >= 0; --q) {
+            phi = M::back(D[q], ldc(cp + t0 + q), phi);
+            csum += M::abs2(phi);
+            if (q == B - 1) next = phi;
+            else wr(q + 1, phi);
+        }
+        wr(0, carry);
+        carry = next;
+        acc.add(csum);
+        store_tile(t0);
+#pragma unroll
+        for (int q = 0; q < W; ++q) D[q] = D[B + q];
+    }
+    // last chunk: W <= rem < B + W positions left; exact from phi[n-1] = dp[n-1]
+    {
+        const int j = t0 / B;
+        const int rem = n - t0;
+        need(nbox - 1);
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            if (q < rem - W) {
+                if ((q & 1) == 0) {
+                    // nodes t0+W+2+q (even, at most N-2) and t0+W+3+q (at most N-1)
+                    rd2(j + (W + 2 + q) / B, (W + 2 + q) % B, p1, p1n);
+                    if (q == rem - W - 2) p1n = M::zero();
+                } else {
+                    p1 = p1n;
+                }
+                if (q == rem - W - 1 && (q & 1) == 0) p1 = M::zero();
+                dprev = M::fwd(M::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + W + q));
+                D[W + q] = dprev;
+                pm = p0;
+                p0 = p1;
+            }
+        }
+        V phi = M::zero();
+        R csum = R(0);
+#pragma unroll
+        for (int q = B + W - 1; q >= 0; --q) {
+            if (q < rem) {
+                phi = M::back(D[q], ldc(cp + t0 + q), (q == rem - 1) ? M::zero() : phi);
+                D[q] = phi;
+                csum += M::abs2(phi);
+            }
+        }
+        acc.add(csum);
+        // tiles j, j+1, ... up to the one holding node N-1 = t0 + rem + 1
+        constexpr int NT = (B + W) / B + 1;
+#pragma unroll
+        for (int kt = 0; kt < NT; ++kt) {
+            if ((j + kt) * B <= N - 1) {
+                tile_free();
+#pragma unroll
+                for (int s = 0; s < B; ++s) {
+                    const int q = kt * B + s - 1;  // node t0 + 1 + q
+                    V v = M::zero();
+                    if (q < 0) v = carry;
+                    else if (q < B + W && q < rem) v = D[q < B + W ? q : 0];
+                    wr(s, v);
+                }
+                store_tile((j + kt) * B);
+            }
+        }
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+    if (!ok) {
+        // give copies that may still be landing a fresh bound before the
+        // block's shared memory is released
+        for (int b = max(0, issued - kTmaSlots); b < issued; ++b)
+            mbar_wait_bounded(bar0 + 8 * (b & (kTmaSlots - 1)), (b / kTmaSlots) & 1, true);
+        if (lane == 0 && a.status) atomicOr(a.status, 1u);
+    }
+    return acc.value();
+}
+
+template <class F, typename R, int W>
+__global__ void __launch_bounds__(kTmaWarps * 32, 1) sweep_tma_kernel(SweepArgs a, const __grid_constant__ TmaMaps maps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                            ~static_cast<uintptr_t>(1023));
+    const int warp = threadIdx.x >> 5;
+    const long long L0 = ((long long)blockIdx.x * kTmaWarps + warp) * kTmaRows;
+    double v = 0.0;
+    if (L0 < a.n_lines)
+        v = tma_body<F, R, W>(a, &maps.in, &maps.out, base + warp * kTmaWarpBytes,
+                              smem_u32(base + kTmaWarps * kTmaWarpBytes) + 8 * kTmaSlots * warp, (int)L0);
+    norm_finalize(v, a, blockIdx.x, gridDim.x);
+}
+
+}  // namespace gpcn

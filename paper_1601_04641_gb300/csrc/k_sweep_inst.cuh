@@ -3,6 +3,7 @@
 #pragma once
 
 #include "gp_sweep.cuh"
+#include "gp_sweep_tma.cuh"
 
 namespace gpcn {
 
@@ -23,12 +24,37 @@ static cudaError_t launch_contig_w(const SweepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <class F, typename R, int W>
+static cudaError_t launch_tma_w(const SweepArgs &a, const TmaMaps &m, cudaStream_t s) {
+    if constexpr (sizeof(typename F::V) == 4 || sizeof(typename F::V) == 8) {
+        const long long rows = (long long)kTmaWarps * kTmaRows;
+        const unsigned grid = (unsigned)((a.n_lines + rows - 1) / rows);
+        static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<F, R, W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        sweep_tma_kernel<F, R, W><<<grid, kTmaWarps * 32, kTmaSmemBytes, s>>>(a, m);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <class F, typename R, int W>
+static cudaError_t launch_contig_or_tma(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    if (L.tma && tma_usable<F, W>(a)) return launch_tma_w<F, R, W>(a, *L.tma, s);
+    return launch_contig_w<F, R, W>(a, s);
+}
+
 template <class F, typename R>
 static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     switch (L.window) {
-    case 4: return launch_contig_w<F, R, 4>(a, s);
-    case 8: return launch_contig_w<F, R, 8>(a, s);
-    case 16: return launch_contig_w<F, R, 16>(a, s);
+    case 4: return launch_contig_or_tma<F, R, 4>(L, a, s);
+    case 8: return launch_contig_or_tma<F, R, 8>(L, a, s);
+    case 16: return launch_contig_or_tma<F, R, 16>(L, a, s);
     default: return cudaErrorInvalidValue;
     }
 }

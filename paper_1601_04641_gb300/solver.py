@@ -174,6 +174,15 @@ class GP:
     def set_pair_lines(self, on):
         self._ck(self.lib.gp_set_pair_lines(self.h, int(bool(on))))
 
+    def set_tma(self, on):
+        """z sweep through TMA tiles (default where the grid allows it)."""
+        self._ck(self.lib.gp_set_tma(self.h, int(bool(on))))
+
+    def tma_in_use(self):
+        v = ctypes.c_int(0)
+        self._ck(self.lib.gp_get_tma(self.h, ctypes.byref(v)))
+        return bool(v.value)
+
     def set_threads(self, axis, threads):
         self._ck(self.lib.gp_set_threads(self.h, int(axis), int(threads)))
 

@@ -40,6 +40,7 @@ def test_batch_instances_equal_single_runs(prec, field):
     for i, p in enumerate(probs):
         gp = GP(p.shape, p.d, p.dt, p.omega, p.g, prec, field)
         gp.set_pair_lines(False)
+        gp.set_tma(False)  # the batched z sweep uses per-thread copies (same norm order)
         seg, _ = b.segments(i)
         for ax in range(3):
             gp.set_axis_window(ax, w[ax])
