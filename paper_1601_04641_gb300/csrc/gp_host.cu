@@ -56,14 +56,19 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
     for (int ax = 0; ax < 3; ++ax) {
         T.kick_off[ax] = off;
         off = align_up(off + rsz * G.n[ax], 256);
+        T.phase_off[ax] = off;
+        off = align_up(off + rsz * G.n[ax], 256);
     }
     host.resize(off, 0);
     // exp(-dt w^2 a^2 / 2) per node of each axis: the trap part of the
-    // imaginary-time kick factorises over the axes.
+    // imaginary-time kick factorises over the axes; its phase dt w^2 a^2 / 2
+    // is the trap part of the real-time kick's angle, a sum over the axes.
     for (int ax = 0; ax < 3; ++ax)
         for (int i = 0; i < G.n[ax]; ++i) {
             const double a = (i - 0.5 * (G.n[ax] - 1)) * G.d[ax];
-            put_real(host.data() + T.kick_off[ax] + i * rsz, std::exp(-G.dt * 0.5 * G.w[ax] * G.w[ax] * a * a), f32);
+            const double dv = G.dt * 0.5 * G.w[ax] * G.w[ax] * a * a;
+            put_real(host.data() + T.kick_off[ax] + i * rsz, std::exp(-dv), f32);
+            put_real(host.data() + T.phase_off[ax] + i * rsz, dv, f32);
         }
     for (int mode = 0; mode < modes; ++mode) {
         for (int ax = 0; ax < 3; ++ax) {
@@ -169,6 +174,10 @@ SweepArgs sweep_args(const Geometry &G, int ax, bool realtime, const void *in, v
         a.kick_ex = tables + T.kick_off[0];
         a.kick_ey = tables + T.kick_off[1];
         a.kick_ez = tables + T.kick_off[2];
+    } else {
+        a.phase_ex = tables + T.phase_off[0];
+        a.phase_ey = tables + T.phase_off[1];
+        a.phase_ez = tables + T.phase_off[2];
     }
     a.dt = G.dt;
     a.g = G.g;

@@ -28,7 +28,8 @@ struct AxisTables {
 
 struct Tables {
     AxisTables ax[2][3];   // [mode: 0 imaginary, 1 real][axis]
-    size_t kick_off[3] = {0, 0, 0};  // exp(-dt w^2 a^2 / 2) per node (imaginary time)
+    size_t kick_off[3] = {0, 0, 0};   // exp(-dt w^2 a^2 / 2) per node (imaginary time)
+    size_t phase_off[3] = {0, 0, 0};  // dt w^2 a^2 / 2 per node (real time)
 };
 
 // Append the tables of G (modes = 1: imaginary time only, 2: both) to `host`

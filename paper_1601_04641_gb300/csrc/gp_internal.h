@@ -39,6 +39,9 @@ struct SweepArgs {
     const void *kick_ex;   // imaginary time: exp(-dt V_x(i)) per x node (else null)
     const void *kick_ey;   //                 exp(-dt V_y(j)) per y node
     const void *kick_ez;   //                 exp(-dt V_z(k)) per z node
+    const void *phase_ex;  // real time: dt V_x(i) per x node (else null)
+    const void *phase_ey;  //            dt V_y(j) per y node
+    const void *phase_ez;  //            dt V_z(k) per z node
     double dt, g;
     double half_w2[3];     // (gamma^2, nu^2, lambda^2) / 2
     double origin[3];      // coordinate of node 0 per axis

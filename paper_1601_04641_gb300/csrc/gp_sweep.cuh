@@ -102,24 +102,40 @@ template <> struct Series<double> {
                                   0.5), -1.0), 1.0);
     }
 };
+// The library functions are called out of line: every load site of the x
+// sweep inlines the kick, and inlined full-range sincos / exp code at each of
+// them would crowd the instruction cache for a path that is rarely taken.
+template <typename R> __device__ __noinline__ cx<R> sincos_full(R x) {
+    cx<R> r;
+    g_sincos(x, &r.im, &r.re);
+    return r;
+}
+template <typename R> __device__ __noinline__ R expm_full(R y) { return g_exp(-y); }
 template <typename R> __device__ __forceinline__ void kick_sincos(R x, R *sn, R *cs) {
-    if (fabs(x) <= Series<R>::kTrig) Series<R>::sincos(x, sn, cs);
-    else g_sincos(x, sn, cs);
+    if (fabs(x) <= Series<R>::kTrig) {
+        Series<R>::sincos(x, sn, cs);
+    } else {
+        const cx<R> r = sincos_full(x);
+        *sn = r.im;
+        *cs = r.re;
+    }
 }
 template <typename R> __device__ __forceinline__ R kick_expm(R y) {
-    return fabs(y) <= Series<R>::kExp ? Series<R>::expm(y) : g_exp(-y);
+    return fabs(y) <= Series<R>::kExp ? Series<R>::expm(y) : expm_full(y);
 }
 
 // Per-site kick state of one x line.  Imaginary time: exp(-dt V) is the
 // product of per-axis factors exp(-dt V_x(i)) (a table) and
 // exp(-dt (V_y(j) + V_z(k))) (fixed along the line), times exp(-dt g |psi|^2).
-// Real time: theta = dt (V + g |psi|^2) and exp(-i theta).
+// Real time: theta = dt V_x(i) (a table) + dt (V_y(j) + V_z(k)) (fixed along
+// the line) + dt g |psi|^2, and exp(-i theta).
 template <typename R> struct KickState {
     R s;              // pending renormalisation factor
     R dtg;            // dt * g
     R eyz;            // exp(-dt (V_y + V_z)) of the line (imaginary time)
     const R *ex;      // exp(-dt V_x(i)) per node (imaginary time)
-    R dt, hx, x0, dx, vyz;  // real time: V = hx x^2 + vyz, x = x0 + i dx
+    R pyz;            // dt (V_y + V_z) of the line (real time)
+    const R *px;      // dt V_x(i) per node (real time)
 };
 
 // Per-thread sum: plain FP64, or FP32 with an error-free two-sum
@@ -142,8 +158,19 @@ template <> struct Acc<float> {
 };
 
 // ------------------------------------------------------------------ forms
+// A form gives the arithmetic of one step of the recurrences on values of
+// type V, and how V maps to the element layout in memory (MemV): identity
+// for one line; the packed pair forms keep the two lines' values in
+// component-wise float2 registers.
+template <typename V_> struct LineForm {
+    static constexpr bool kPair = false;
+    using MemV = V_;
+    __device__ __forceinline__ static V_ load(MemV m) { return m; }
+    __device__ __forceinline__ static MemV store(V_ v) { return v; }
+};
+
 // Imaginary time, real field: c = kappa, coefficients real.
-template <typename R> struct FImagReal {
+template <typename R> struct FImagReal : LineForm<R> {
     using Real = R;
     using V = R;
     using C = R;
@@ -164,7 +191,7 @@ template <typename R> struct FImagReal {
 };
 
 // Imaginary time, complex field: c = kappa real, applied to both parts.
-template <typename R> struct FImagCplx {
+template <typename R> struct FImagCplx : LineForm<cx<R>> {
     using Real = R;
     using V = cx<R>;
     using C = R;
@@ -189,7 +216,7 @@ template <typename R> struct FImagCplx {
 };
 
 // Real time, complex field: c = i kappa, coefficients complex.
-template <typename R> struct FRealTime {
+template <typename R> struct FRealTime : LineForm<cx<R>> {
     using Real = R;
     using V = cx<R>;
     using C = cx<R>;
@@ -215,8 +242,7 @@ template <typename R> struct FRealTime {
     __device__ __forceinline__ static R abs2(V v) { return fma(v.re, v.re, v.im * v.im); }
     __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
         const V q{p.re * k.s, p.im * k.s};
-        const R x = fma((R)node, k.dx, k.x0);
-        const R theta = fma(k.dtg, abs2(q), k.dt * fma(k.hx * x, x, k.vyz));
+        const R theta = fma(k.dtg, abs2(q), __ldg(k.px + node) + k.pyz);
         R sn, cs;
         kick_sincos(theta, &sn, &cs);
         // exp(-i theta) q
@@ -232,6 +258,10 @@ template <class F> struct FPair {
     using E = typename F::V;
     struct __align__(2 * sizeof(E)) V { E a, b; };
     using C = typename F::C;
+    static constexpr bool kPair = true;
+    using MemV = V;
+    __device__ __forceinline__ static V load(MemV m) { return m; }
+    __device__ __forceinline__ static MemV store(V v) { return v; }
     __device__ __forceinline__ static V zero() { return V{F::zero(), F::zero()}; }
     __device__ __forceinline__ static V rhs(V pm, V p0, V p1, Real k) {
         return V{F::rhs(pm.a, p0.a, p1.a, k), F::rhs(pm.b, p0.b, p1.b, k)};
@@ -243,7 +273,82 @@ template <class F> struct FPair {
         return V{F::back(dp.a, cp, phi.a), F::back(dp.b, cp, phi.b)};
     }
     __device__ __forceinline__ static Real abs2(V v) { return F::abs2(v.a) + F::abs2(v.b); }
+    __device__ __forceinline__ static V kick2(V v, const KickState<Real> &ka, const KickState<Real> &kb, int node) {
+        return V{F::kick(v.a, ka, node), F::kick(v.b, kb, node)};
+    }
 };
+
+// Packed FP32 pairs: the two lines' values of each component share one
+// float2, and each FP32 operation of the scalar form becomes one paired
+// operation (fma / mul / add .f32x2, round to nearest) on both lines, in the
+// same order, so the results equal the scalar form's.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+struct PRealTimeF {
+    using Real = float;
+    using F = FRealTime<float>;
+    using C = cx<float>;
+    struct __align__(16) V { float2 re, im; };  // (line a, line b) per component
+    using MemV = typename FPair<F>::V;
+    static constexpr bool kPair = true;
+    __device__ __forceinline__ static V load(MemV m) {
+        return V{make_float2(m.a.re, m.b.re), make_float2(m.a.im, m.b.im)};
+    }
+    __device__ __forceinline__ static MemV store(V v) {
+        MemV m;
+        m.a = cx<float>{v.re.x, v.im.x};
+        m.b = cx<float>{v.re.y, v.im.y};
+        return m;
+    }
+    __device__ __forceinline__ static V zero() { return V{dup2(0.f), dup2(0.f)}; }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, float k) {
+        const float2 dre = fma2(dup2(-2.f), p0.re, add2(pm.re, p1.re));
+        const float2 dim = fma2(dup2(-2.f), p0.im, add2(pm.im, p1.im));
+        return V{fma2(dup2(-k), dim, p0.re), fma2(dup2(k), dre, p0.im)};
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, float k, C ipm1) {
+        const float2 ure = fma2(dup2(-k), dprev.im, r.re);
+        const float2 uim = fma2(dup2(k), dprev.re, r.im);
+        return V{fma2(ure, dup2(ipm1.re), fma2(uim, dup2(-ipm1.im), ure)),
+                 fma2(ure, dup2(ipm1.im), fma2(uim, dup2(ipm1.re), uim))};
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) {
+        const float2 pre = fma2(dup2(cp.re), phi.re, mul2(dup2(-cp.im), phi.im));
+        const float2 pim = fma2(dup2(cp.re), phi.im, mul2(dup2(cp.im), phi.re));
+        return V{sub2(dp.re, pre), sub2(dp.im, pim)};
+    }
+    __device__ __forceinline__ static float abs2(V v) {
+        const float2 s = fma2(v.re, v.re, mul2(v.im, v.im));
+        return s.x + s.y;
+    }
+    // Kick of both lines: shared scale, dt g and x table; per-line dt (V_y + V_z).
+    __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
+                                              int node) {
+        const float2 s = dup2(ka.s);
+        const float2 qre = mul2(p.re, s), qim = mul2(p.im, s);
+        const float2 a2 = fma2(qre, qre, mul2(qim, qim));
+        const float2 base = add2(dup2(__ldg(ka.px + node)), make_float2(ka.pyz, kb.pyz));
+        const float2 th = fma2(dup2(ka.dtg), a2, base);
+        float2 sn, cs;
+        if (fabsf(th.x) <= Series<float>::kTrig && fabsf(th.y) <= Series<float>::kTrig) {
+            const float2 x2 = mul2(th, th);
+            sn = mul2(th, fma2(x2, fma2(x2, dup2(1.f / 120.f), dup2(-1.f / 6.f)), dup2(1.f)));
+            cs = fma2(x2, fma2(x2, fma2(x2, dup2(-1.f / 720.f), dup2(1.f / 24.f)), dup2(-0.5f)), dup2(1.f));
+        } else {
+            kick_sincos(th.x, &sn.x, &cs.x);
+            kick_sincos(th.y, &sn.y, &cs.y);
+        }
+        return V{fma2(cs, qre, mul2(sn, qim)), fma2(cs, qim, mul2(make_float2(-sn.x, -sn.y), qre))};
+    }
+};
+
+// The paired form of a single-line form.
+template <class F> struct PairForm { using type = FPair<F>; };
+template <> struct PairForm<FRealTime<float>> { using type = PRealTimeF; };
 
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
@@ -452,69 +557,53 @@ template <typename R, int KIND> __device__ __forceinline__ void kick_init(KickSt
     k.ex = static_cast<const R *>(a.kick_ex);
     k.eyz = a.kick_ex ? __ldg(static_cast<const R *>(a.kick_ey) + j) * __ldg(static_cast<const R *>(a.kick_ez) + kk)
                       : R(1);
-    const double y = a.origin[1] + j * a.d[1];
-    const double z = a.origin[2] + kk * a.d[2];
-    k.dt = (R)a.dt;
-    k.vyz = (R)(a.half_w2[1] * y * y + a.half_w2[2] * z * z);
-    k.hx = (R)a.half_w2[0];
-    k.x0 = (R)a.origin[0];
-    k.dx = (R)a.d[0];
+    k.px = static_cast<const R *>(a.phase_ex);
+    k.pyz = a.phase_ex ? __ldg(static_cast<const R *>(a.phase_ey) + j) + __ldg(static_cast<const R *>(a.phase_ez) + kk)
+                       : R(0);
 }
 
-// F is the single-line form; M is F (one line per thread) or FPair<F>.
-template <class F, class M, typename R, int KIND> struct Hooks;
-template <class F, typename R, int KIND> struct Hooks<F, F, R, KIND> {
-    using V = typename F::V;
-    KickState<R> k;
-    Acc<R> *acc;
-    __device__ __forceinline__ void init(const SweepArgs &a, long long L) {
-        if (KIND == K_X) kick_init<R, KIND>(k, a, L);
-    }
-    __device__ __forceinline__ V on_load(int p, V v) const {
-        if (KIND == K_X) v = F::kick(v, k, p + 1);
-        return v;
-    }
-    __device__ __forceinline__ void on_store(V v) const {
-        if (KIND == K_Z) acc->add(F::abs2(v));
-    }
-};
-template <class F, typename R, int KIND> struct Hooks<F, FPair<F>, R, KIND> {
-    using V = typename FPair<F>::V;
+// F is the single-line form; M is F (one line per thread) or its pair form.
+template <class F, class M, typename R, int KIND> struct Hooks {
+    using V = typename M::V;
     KickState<R> ka, kb;
     Acc<R> *acc;
     __device__ __forceinline__ void init(const SweepArgs &a, long long L) {
         if (KIND == K_X) {
             kick_init<R, KIND>(ka, a, L);
-            kick_init<R, KIND>(kb, a, L + 1);
+            if constexpr (M::kPair) kick_init<R, KIND>(kb, a, L + 1);
         }
     }
     __device__ __forceinline__ V on_load(int p, V v) const {
-        if (KIND == K_X) v = V{F::kick(v.a, ka, p + 1), F::kick(v.b, kb, p + 1)};
+        if constexpr (KIND == K_X) {
+            if constexpr (M::kPair) v = M::kick2(v, ka, kb, p + 1);
+            else v = F::kick(v, ka, p + 1);
+        }
         return v;
     }
     __device__ __forceinline__ void on_store(V v) const {
-        if (KIND == K_Z) acc->add(FPair<F>::abs2(v));
+        if (KIND == K_Z) acc->add(M::abs2(v));
     }
 };
 
 // Direct per-thread access, for the exact two-pass form.
 template <class F, class M, typename R, int KIND> struct DirectIO {
     using V = typename M::V;
-    const V *in;
-    V *out;
+    using MV = typename M::MemV;
+    const MV *in;
+    MV *out;
     long long st;
     int n;
     Hooks<F, M, R, KIND> hk;
     __device__ __forceinline__ V load1(int t) const {
         if (t < 0 || t >= n) return M::zero();
-        return hk.on_load(t, in[(long long)(t + 1) * st]);
+        return hk.on_load(t, M::load(in[(long long)(t + 1) * st]));
     }
     __device__ __forceinline__ void put1(int t, V v) const {
-        out[(long long)(t + 1) * st] = v;
+        out[(long long)(t + 1) * st] = M::store(v);
         hk.on_store(v);
     }
-    __device__ __forceinline__ void stage(int t, V v) const { out[(long long)(t + 1) * st] = v; }
-    __device__ __forceinline__ V unstage(int t) const { return out[(long long)(t + 1) * st]; }
+    __device__ __forceinline__ void stage(int t, V v) const { out[(long long)(t + 1) * st] = M::store(v); }
+    __device__ __forceinline__ V unstage(int t) const { return M::load(out[(long long)(t + 1) * st]); }
 };
 
 // ------------------------------------------------------------------ strided axes
@@ -525,10 +614,11 @@ template <class F, class M, typename R, int KIND> struct DirectIO {
 // while one chunk is consumed the next two are in flight.
 template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
     using V = typename M::V;
+    using MV = typename M::MemV;
     static constexpr int RL = kRingChunks * B;  // ring length (power of two)
-    const V *in;
-    V *out;
-    V *ring;      // this thread's column: element p at ring[(p - s0) % RL * T]
+    const MV *in;
+    MV *out;
+    MV *ring;     // this thread's column: element p at ring[(p - s0) % RL * T]
     long long st;
     int n, T, s0, limit, issued, ready;
     Hooks<F, M, R, KIND> hk;
@@ -538,7 +628,7 @@ template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
         for (int e = 0; e < B; ++e) {
             const int p = pb + e;
             const bool ok = p >= 0 && p < n;
-            cp_async<sizeof(V)>(ring + ((p - s0) & (RL - 1)) * T, ok ? in + (long long)(p + 1) * st : in, ok);
+            cp_async<sizeof(MV)>(ring + ((p - s0) & (RL - 1)) * T, ok ? in + (long long)(p + 1) * st : in, ok);
         }
         cp_async_commit();
         ++issued;
@@ -556,16 +646,18 @@ template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
         ready = c + 1;
         while (issued <= c + kRingChunks - 2 && s0 + issued * B < limit) issue();
     }
-    __device__ __forceinline__ V val(int p) const { return hk.on_load(p, ring[((p - s0) & (RL - 1)) * T]); }
+    __device__ __forceinline__ V val(int p) const {
+        return hk.on_load(p, M::load(ring[((p - s0) & (RL - 1)) * T]));
+    }
     __device__ __forceinline__ void put(int t0, int q, V v) const {
-        out[(long long)(t0 + q + 1) * st] = v;
+        out[(long long)(t0 + q + 1) * st] = M::store(v);
         hk.on_store(v);
     }
     __device__ __forceinline__ void flush(int, int) const {}
 };
 
 template <class F, int LPT> struct LinesPerThread { using M = F; };
-template <class F> struct LinesPerThread<F, 2> { using M = FPair<F>; };
+template <class F> struct LinesPerThread<F, 2> { using M = typename PairForm<F>::type; };
 
 // One thread per (line, segment), or per (pair of adjacent lines, segment)
 // when LPT = 2; blockIdx.y is the segment.  Window 0 selects the exact
@@ -575,20 +667,21 @@ __device__ __forceinline__ double lines_body(const SweepArgs &a, unsigned bx, un
                                              unsigned char *smem_raw) {
     using M = typename LinesPerThread<F, LPT>::M;
     using V = typename M::V;
+    using MV = typename M::MemV;
     using C = typename F::C;
-    constexpr int B = chunk_len<V>();
+    constexpr int B = chunk_len<MV>();
     const long long L = ((long long)bx * blockDim.x + threadIdx.x) * LPT;
     Acc<R> acc;
     if (L < a.n_lines) {
         const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
-        const V *in = reinterpret_cast<const V *>(static_cast<const typename F::V *>(a.psi) + off);
-        V *out = reinterpret_cast<V *>(static_cast<typename F::V *>(a.psi_out) + off);
-        const long long st = a.stride / LPT;  // stride in units of V
+        const MV *in = reinterpret_cast<const MV *>(static_cast<const typename F::V *>(a.psi) + off);
+        MV *out = reinterpret_cast<MV *>(static_cast<typename F::V *>(a.psi_out) + off);
+        const long long st = a.stride / LPT;  // stride in units of MV
         const int n = a.N - 2;
         const C *cp = static_cast<const C *>(a.cp);
         const C *ipm1 = static_cast<const C *>(a.ip);
-        if (seg == 0) out[0] = M::zero();
-        if ((int)seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::zero();
+        if (seg == 0) out[0] = M::store(M::zero());
+        if ((int)seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::store(M::zero());
         if constexpr (W > 0) {
             ColumnIO<F, M, R, B, KIND> io;
             io.in = in;
@@ -596,7 +689,7 @@ __device__ __forceinline__ double lines_body(const SweepArgs &a, unsigned bx, un
             io.st = st;
             io.n = n;
             io.T = blockDim.x;
-            io.ring = reinterpret_cast<V *>(smem_raw) + threadIdx.x;
+            io.ring = reinterpret_cast<MV *>(smem_raw) + threadIdx.x;
             io.hk.acc = &acc;
             io.hk.init(a, L);
             const int tb = seg * a.seg_len;

@@ -3,7 +3,7 @@
 //
 // With x slowest and z fastest, the z lines are the rows of a 2D array
 // [n_lines][N].  A warp owns 64 consecutive rows and advances two of them
-// per lane (rows lane and lane + 32, as one FPair), walking them in boxes of
+// per lane (rows lane and lane + 32, as one pair form), walking them in boxes of
 // B nodes x 64 rows, where B nodes fill 64 bytes of a row (8 complex64 or 16
 // float values).  One lane issues each box as a cp.async.bulk.tensor load
 // into a four-slot ring of shared memory (one mbarrier per slot); the box
@@ -81,8 +81,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
         : "memory");
     return done != 0;
 }
-// Wait for the phase of `bar` with the given parity, for at most `limit`
-// clock cycles (none at all once `ok` is false).  Returns false on expiry.
+// Wait for the phase of `bar` with the given parity, for at most
+// kTmaSpinCycles clock cycles (none at all once `ok` is false).  Returns
+// false on expiry.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, bool ok) {
     if (mbar_try_wait(bar, parity)) return true;
     if (!ok) return false;
@@ -118,8 +119,9 @@ template <class F, typename R, int W>
 __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap *tin, const CUtensorMap *tout,
                                            unsigned char *wbase, unsigned bar0, int y0) {
     using E = typename F::V;
-    using M = FPair<F>;
+    using M = typename PairForm<F>::type;
     using V = typename M::V;
+    using MV = typename M::MemV;
     using C = typename F::C;
     constexpr int B = tma_chunk<E>();
     constexpr int ES = sizeof(E);
@@ -169,13 +171,14 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
         const unsigned off = (unsigned)(c * ES) ^ xm;
         const E2<E> pa = *reinterpret_cast<const E2<E> *>(slot + ra + off);
         const E2<E> pb = *reinterpret_cast<const E2<E> *>(slot + rb + off);
-        v0 = V{pa.x, pb.x};
-        v1 = V{pa.y, pb.y};
+        v0 = M::load(MV{pa.x, pb.x});
+        v1 = M::load(MV{pa.y, pb.y});
     };
     auto wr = [&](int s, V v) {  // slot s of the output tile
         const unsigned off = (unsigned)(s * ES) ^ xm;
-        *reinterpret_cast<E *>(otile + ra + off) = v.a;
-        *reinterpret_cast<E *>(otile + rb + off) = v.b;
+        const MV m = M::store(v);
+        *reinterpret_cast<E *>(otile + ra + off) = m.a;
+        *reinterpret_cast<E *>(otile + rb + off) = m.b;
     };
     auto tile_free = [&]() {  // the previous tile store has read the tile
         if (lane == 0) bulk_wait_read_all();

@@ -61,7 +61,7 @@ static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaS
 
 template <class F, typename R, int W, int KIND, int LPT>
 static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
-    using V = typename LinesPerThread<F, LPT>::M::V;
+    using V = typename LinesPerThread<F, LPT>::M::MemV;
     const unsigned threads = (unsigned)L.threads;
     const long long units = (a.n_lines + LPT - 1) / LPT;
     const dim3 grid((unsigned)((units + threads - 1) / threads), (unsigned)a.n_seg);
