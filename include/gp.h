@@ -202,9 +202,10 @@ gp_status gp_set_pair_lines(gp_handle h, int on);
  * bulk tensor copy per 64 lines x 64 bytes, two lines per thread (1, the
  * default), or through per-thread asynchronous copies (0).  The TMA form is
  * taken where the rows allow it: 4- or 8-byte elements, nz * element size a
- * multiple of 16 bytes, a window > 0, whole lines, and nz - 2 at least one
- * chunk (64 bytes of nodes) plus the window plus 2; elsewhere the other form
- * runs.  The arithmetic per line is the same in both.  gp_get_tma reports
+ * multiple of 16 bytes, a window > 0 with (chunk + window) pair values in
+ * at most 256 bytes (chunk = 64 bytes of nodes: every window for FP32 real
+ * fields, windows 4 and 8 for 8-byte elements), whole lines, and nz - 2 at
+ * least one chunk plus the window plus 2; elsewhere the other form runs.  The arithmetic per line is the same in both.  gp_get_tma reports
  * whether the handle's buffers have tensor maps and the form is selected
  * (the per-launch conditions above still apply). */
 gp_status gp_set_tma(gp_handle h, int on);

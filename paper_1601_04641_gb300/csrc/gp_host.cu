@@ -100,6 +100,14 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
                     }
                 }
             }
+            // the stored entries settle to the line's last ones (bit for bit)
+            // a few nodes in; kernels read them once from there on
+            const size_t esz = (mode == 1 ? 2 : 1) * rsz;
+            const char *tc = host.data() + at.off_cp, *ti = host.data() + at.off_ip;
+            at.t_const = n;
+            while (at.t_const > 0 && std::memcmp(tc + (at.t_const - 1) * esz, tc + (n - 1) * esz, esz) == 0 &&
+                   std::memcmp(ti + (at.t_const - 1) * esz, ti + (n - 1) * esz, esz) == 0)
+                --at.t_const;
         }
     }
 }
@@ -166,6 +174,7 @@ SweepArgs sweep_args(const Geometry &G, int ax, bool realtime, const void *in, v
         a.stride = 1;
     }
     a.N = G.n[ax];
+    a.t_const = T.ax[mode][ax].t_const;
     a.seg_len = seg_len;
     a.n_seg = n_seg;
     a.kappa = G.dt / (4.0 * G.d[ax] * G.d[ax]);

@@ -23,6 +23,7 @@ struct Geometry {
 struct AxisTables {
     size_t off_cp = 0, off_ip = 0;
     int min_window = 0;   // 4, 8 or 16; 0 when none is admissible
+    int t_const = 0;      // first index from which both stored tables are constant
     double cp_max = 0.0;
 };
 

@@ -33,6 +33,7 @@ struct SweepArgs {
     int N;                 // nodes along the line (interior N - 2)
     int seg_len;           // interior nodes per segment (a multiple of the chunk length)
     int n_seg;             // segments per line (grid.y); one thread per (line, segment)
+    int t_const;           // cp[t], ip[t] equal cp[N-3], ip[N-3] (stored bits) for t >= t_const
     double kappa;          // |c| = dt / (4 d^2)
     // kick (K_X): site (i, j, k) with i along the line, (j, k) = (L / nz, L % nz)
     const double *scale;   // pending renormalisation factor applied on load

@@ -435,15 +435,52 @@ template <typename V> __host__ __device__ constexpr int chunk_len() { return siz
 constexpr int kRingChunks = 4;
 
 // Windowed Thomas solve of the interior nodes [tb, te) of a line of n
+// interior unknowns; the coefficient tables hold their last values from
+// tconst on.
 // interior unknowns.  Inputs are read by interior position p (node p+1;
 // positions outside [0, n) read 0) after io.need(p_end) has made the
 // positions [p_end - B, p_end) readable; outputs go through io.put(t0, q, v)
 // (position t0 + q) and io.flush(t0, count).
+// One full chunk: dp[t0+W .. t0+W+B-1] forward, then phi[t0 .. t0+B-1] by
+// the windowed backward sweep.  SETTLED: every coefficient the chunk uses
+// equals the table's last entry (cp and ip reach their fixed point a few
+// nodes into the line and stay there to FP rounding), so they are read once
+// per thread instead of once per node.
+template <class F, typename R, int B, int W, bool SETTLED, class IO>
+__device__ __forceinline__ void window_chunk(int t0, typename F::V (&D)[B + W], typename F::V &pm, typename F::V &p0,
+                                             typename F::V &p1, typename F::V &dprev, R kap,
+                                             const typename F::C *__restrict__ cp,
+                                             const typename F::C *__restrict__ ipm1, typename F::C cps,
+                                             typename F::C ips, IO &io) {
+    using V = typename F::V;
+    io.need(t0 + W + 2 + B);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, SETTLED ? ips : ldc(ipm1 + t0 + W + q));
+        D[W + q] = dprev;
+        pm = p0;
+        p0 = p1;
+        p1 = io.val(t0 + W + 2 + q);
+    }
+    V phi = D[B + W - 1];
+#pragma unroll
+    for (int q = B + W - 2; q >= B; --q) phi = F::back(D[q], SETTLED ? cps : ldc(cp + t0 + q), phi);
+#pragma unroll
+    for (int q = B - 1; q >= 0; --q) {
+        phi = F::back(D[q], SETTLED ? cps : ldc(cp + t0 + q), phi);
+        io.put(t0, q, phi);
+    }
+    io.flush(t0, B);
+#pragma unroll
+    for (int q = 0; q < W; ++q) D[q] = D[B + q];
+}
+
 template <class F, typename R, int B, int W, class IO>
-__device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
+__device__ __forceinline__ void solve_segment(int n, int tb, int te, int tconst, R kap,
                                               const typename F::C *__restrict__ cp,
                                               const typename F::C *__restrict__ ipm1, IO &io) {
     using V = typename F::V;
+    using C = typename F::C;
     // forward warm-up from dp = 0 at tw (exact when tw == 0: node 0 is 0)
     const int tw = tb > W + 1 ? tb - (W + 1) : 0;
     // the segment behaves as a line ending at e: W look-ahead values beyond
@@ -476,28 +513,13 @@ __device__ __forceinline__ void solve_segment(int n, int tb, int te, R kap,
         }
     }
     int t0 = tb;
-    for (; t0 + B + W <= e; t0 += B) {
-        io.need(t0 + W + 2 + B);
-#pragma unroll
-        for (int q = 0; q < B; ++q) {
-            dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + W + q));
-            D[W + q] = dprev;
-            pm = p0;
-            p0 = p1;
-            p1 = io.val(t0 + W + 2 + q);
-        }
-        V phi = D[B + W - 1];
-#pragma unroll
-        for (int q = B + W - 2; q >= B; --q) phi = F::back(D[q], ldc(cp + t0 + q), phi);
-#pragma unroll
-        for (int q = B - 1; q >= 0; --q) {
-            phi = F::back(D[q], ldc(cp + t0 + q), phi);
-            io.put(t0, q, phi);
-        }
-        io.flush(t0, B);
-#pragma unroll
-        for (int q = 0; q < W; ++q) D[q] = D[B + q];
-    }
+    // chunks before the coefficients settle read the tables; the rest keep
+    // the settled values in registers
+    const C cps = ldc(cp + n - 1), ips = ldc(ipm1 + n - 1);
+    for (; t0 + B + W <= e && t0 < tconst; t0 += B)
+        window_chunk<F, R, B, W, false>(t0, D, pm, p0, p1, dprev, kap, cp, ipm1, cps, ips, io);
+    for (; t0 + B + W <= e; t0 += B)
+        window_chunk<F, R, B, W, true>(t0, D, pm, p0, p1, dprev, kap, cp, ipm1, cps, ips, io);
     const int rem = e - t0;  // 0 <= rem < B + W: finish from dp[e-1]
     io.need(e + 2);
 #pragma unroll
@@ -694,7 +716,7 @@ __device__ __forceinline__ double lines_body(const SweepArgs &a, unsigned bx, un
             io.hk.init(a, L);
             const int tb = seg * a.seg_len;
             const int te = (int)seg == a.n_seg - 1 ? n : tb + a.seg_len;
-            solve_segment<M, R, B, W>(n, tb, te, (R)a.kappa, cp, ipm1, io);
+            solve_segment<M, R, B, W>(n, tb, te, a.t_const, (R)a.kappa, cp, ipm1, io);
         } else {
             DirectIO<F, M, R, KIND> io;
             io.in = in;
@@ -849,7 +871,7 @@ __device__ __forceinline__ double contig_body(const SweepArgs &a, unsigned bx, u
         }
         const int tb = seg * a.seg_len;
         const int te = (int)seg == a.n_seg - 1 ? io.n : tb + a.seg_len;
-        solve_segment<F, R, B, W>(io.n, tb, te, (R)a.kappa, static_cast<const C *>(a.cp),
+        solve_segment<F, R, B, W>(io.n, tb, te, a.t_const, (R)a.kappa, static_cast<const C *>(a.cp),
                                   static_cast<const C *>(a.ip), io);
     }
     return acc.value();

@@ -28,6 +28,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "gp_sweep.cuh"
 
 namespace gpcn {
@@ -43,12 +45,21 @@ constexpr long long kTmaSpinCycles = 1LL << 31;
 
 template <typename E> __host__ __device__ constexpr int tma_chunk() { return kTmaRowBytes / (int)sizeof(E); }
 
-// Whether a z sweep can take the TMA kernel: 4- or 8-byte elements, whole
-// lines (one segment), rows that start on 16-byte boundaries, and lines of
-// at least one full chunk plus its window and two nodes.
+// Forms the TMA kernel is built for: 4- or 8-byte elements, and a register
+// ring of B + W pair values within 256 bytes per thread (beyond that the
+// kernel spills; the per-thread copy form runs instead).
+template <class F, int W> constexpr bool tma_supported() {
+    using E = typename F::V;
+    if constexpr (sizeof(E) != 4 && sizeof(E) != 8) return false;
+    else return (tma_chunk<E>() + W) * 2 * sizeof(E) <= 256;
+}
+
+// Whether a z sweep can take the TMA kernel: a supported form, whole lines
+// (one segment), rows that start on 16-byte boundaries, and lines of at
+// least one full chunk plus its window and two nodes.
 template <class F, int W> inline bool tma_usable(const SweepArgs &a) {
     using E = typename F::V;
-    if constexpr (sizeof(E) != 4 && sizeof(E) != 8) {
+    if constexpr (!tma_supported<F, W>()) {
         return false;
     } else {
         return a.n_seg == 1 && a.N - 2 >= tma_chunk<E>() + W + 2 && ((long long)a.N * sizeof(E)) % 16 == 0 &&
@@ -174,11 +185,11 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
         v0 = M::load(MV{pa.x, pb.x});
         v1 = M::load(MV{pa.y, pb.y});
     };
-    auto wr = [&](int s, V v) {  // slot s of the output tile
+    auto wr2 = [&](int s, V v0, V v1) {  // slots s, s+1 (s even) of the output tile
         const unsigned off = (unsigned)(s * ES) ^ xm;
-        const MV m = M::store(v);
-        *reinterpret_cast<E *>(otile + ra + off) = m.a;
-        *reinterpret_cast<E *>(otile + rb + off) = m.b;
+        const MV m0 = M::store(v0), m1 = M::store(v1);
+        *reinterpret_cast<E2<E> *>(otile + ra + off) = E2<E>{m0.a, m1.a};
+        *reinterpret_cast<E2<E> *>(otile + rb + off) = E2<E>{m0.b, m1.b};
     };
     auto tile_free = [&]() {  // the previous tile store has read the tile
         if (lane == 0) bulk_wait_read_all();
@@ -214,8 +225,11 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
         pm = p0;
         p0 = p1;
     }
-    int t0 = 0;
-    for (; t0 + B + W <= n; t0 += B) {
+    // One full chunk (outputs t0 .. t0+B-1).  Settled: the coefficients of
+    // the chunk all equal the tables' last entries and come from registers.
+    const C cps = ldc(cp + n - 1), ips = ldc(ipm1 + n - 1);
+    auto chunk = [&](int t0, auto settled) {
+        constexpr bool S = decltype(settled)::value;
         const int j = t0 / B;
         need(j + (W + B + 1) / B);
         const bool last_full = t0 + B + W == n;  // the chunk's last read is node N-1
@@ -227,7 +241,7 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
             } else {
                 p1 = p1n;
             }
-            dprev = M::fwd(M::rhs(pm, p0, p1, kap), dprev, kap, ldc(ipm1 + t0 + W + q));
+            dprev = M::fwd(M::rhs(pm, p0, p1, kap), dprev, kap, S ? ips : ldc(ipm1 + t0 + W + q));
             D[W + q] = dprev;
             pm = p0;
             p0 = p1;
@@ -235,23 +249,27 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
         tile_free();
         V phi = D[B + W - 1];
 #pragma unroll
-        for (int q = B + W - 2; q >= B; --q) phi = M::back(D[q], ldc(cp + t0 + q), phi);
+        for (int q = B + W - 2; q >= B; --q) phi = M::back(D[q], S ? cps : ldc(cp + t0 + q), phi);
         R csum = R(0);
-        V next = M::zero();
+        V next = M::zero(), hi = M::zero();
 #pragma unroll
-        for (int q = B - 1; q >= 0; --q) {
-            phi = M::back(D[q], ldc(cp + t0 + q), phi);
+        for (int q = B - 1; q >= 0; --q) {  // result q goes to tile slot q + 1
+            phi = M::back(D[q], S ? cps : ldc(cp + t0 + q), phi);
             csum += M::abs2(phi);
             if (q == B - 1) next = phi;
-            else wr(q + 1, phi);
+            else if ((q & 1) == 0) hi = phi;
+            else wr2(q + 1, phi, hi);
         }
-        wr(0, carry);
+        wr2(0, carry, hi);
         carry = next;
         acc.add(csum);
         store_tile(t0);
 #pragma unroll
         for (int q = 0; q < W; ++q) D[q] = D[B + q];
-    }
+    };
+    int t0 = 0;
+    for (; t0 + B + W <= n && t0 < a.t_const; t0 += B) chunk(t0, std::false_type{});
+    for (; t0 + B + W <= n; t0 += B) chunk(t0, std::true_type{});
     // last chunk: W <= rem < B + W positions left; exact from phi[n-1] = dp[n-1]
     {
         const int j = t0 / B;
@@ -291,14 +309,15 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
         for (int kt = 0; kt < NT; ++kt) {
             if ((j + kt) * B <= N - 1) {
                 tile_free();
-#pragma unroll
-                for (int s = 0; s < B; ++s) {
-                    const int q = kt * B + s - 1;  // node t0 + 1 + q
+                auto slot = [&](int s) {  // tile slot s holds node t0 + 1 + q
+                    const int q = kt * B + s - 1;
                     V v = M::zero();
                     if (q < 0) v = carry;
                     else if (q < B + W && q < rem) v = D[q < B + W ? q : 0];
-                    wr(s, v);
-                }
+                    return v;
+                };
+#pragma unroll
+                for (int s = 0; s < B; s += 2) wr2(s, slot(s), slot(s + 1));
                 store_tile((j + kt) * B);
             }
         }

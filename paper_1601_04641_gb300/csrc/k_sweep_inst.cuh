@@ -26,7 +26,7 @@ static cudaError_t launch_contig_w(const SweepArgs &a, cudaStream_t s) {
 
 template <class F, typename R, int W>
 static cudaError_t launch_tma_w(const SweepArgs &a, const TmaMaps &m, cudaStream_t s) {
-    if constexpr (sizeof(typename F::V) == 4 || sizeof(typename F::V) == 8) {
+    if constexpr (tma_supported<F, W>()) {
         const long long rows = (long long)kTmaWarps * kTmaRows;
         const unsigned grid = (unsigned)((a.n_lines + rows - 1) / rows);
         static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory
