@@ -13,6 +13,10 @@ template <typename R> struct Elem<R, false> {
     __device__ __forceinline__ static R abs2r(V v) { return v * v; }
     __device__ __forceinline__ static V from_real(double x) { return (R)x; }
     __device__ __forceinline__ static V scaled(V v, R s) { return v * s; }
+    __device__ __forceinline__ static R diff2(V a, V b) {
+        const R d = a - b;
+        return d * d;
+    }
 };
 template <typename R> struct Elem<R, true> {
     using V = cx<R>;
@@ -22,6 +26,10 @@ template <typename R> struct Elem<R, true> {
     __device__ __forceinline__ static R abs2r(V v) { return fma(v.re, v.re, v.im * v.im); }
     __device__ __forceinline__ static V from_real(double x) { return V{(R)x, R(0)}; }
     __device__ __forceinline__ static V scaled(V v, R s) { return V{v.re * s, v.im * s}; }
+    __device__ __forceinline__ static R diff2(V a, V b) {
+        const R dre = a.re - b.re, dim = a.im - b.im;
+        return dre * dre + dim * dim;
+    }
 };
 
 __device__ __forceinline__ long long grid_stride() { return (long long)gridDim.x * blockDim.x; }
@@ -49,16 +57,65 @@ __global__ void gaussian_kernel(FieldArgs a) {
     }
 }
 
-// Reduce 9 FP64 values over the grid: block partials, then the last block
-// sums them in block order (deterministic) and calls `fin`.
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Block sums of NV compensated FP32 pairs (s, c), combined by TwoSum at every
+// level of a fixed tree (warp butterfly, then the warps in order), converted
+// to FP64 once; valid in thread 0.  FP64 arithmetic is a small fraction of
+// the FP32 rate on this part, so the per-block reduction stays in FP32.
+template <int NV>
+__device__ __forceinline__ void block_sum_pairs(float (&s)[NV], float (&c)[NV], double (&out)[NV]) {
+    __shared__ float red_s[NV][32], red_c[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (int)((blockDim.x + 31) >> 5);
+    auto warp_pairs = [&]() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const float s2 = __shfl_xor_sync(0xffffffffu, s[q], o);
+                const float c2 = __shfl_xor_sync(0xffffffffu, c[q], o);
+                float t, e;
+                two_sum(s[q], s2, t, e);
+                s[q] = t;
+                c[q] = (c[q] + c2) + e;
+            }
+        }
+    };
+    warp_pairs();
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            red_s[q][wid] = s[q];
+            red_c[q][wid] = c[q];
+        }
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            s[q] = lane < nw ? red_s[q][lane] : 0.f;
+            c[q] = lane < nw ? red_c[q][lane] : 0.f;
+        }
+        warp_pairs();
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = (double)s[q] + (double)c[q];
+}
+
+// Block sums bs (valid in thread 0) -> partials; the last block to finish
+// sums the partials in block order (deterministic) and calls `fin`.
 template <int NV, class Fin>
-__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs &a, Fin fin,
-                                                unsigned block, unsigned nblocks) {
+__device__ __forceinline__ void finalize_partials(const double (&bs)[NV], const FieldArgs &a, Fin fin,
+                                                  unsigned block, unsigned nblocks) {
     __shared__ double red[32];
     __shared__ int is_last;
-    double bs[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) bs[q] = block_sum(v[q], red);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) a.partials[(long long)block * NV + q] = bs[q];
@@ -69,18 +126,31 @@ __device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double tot[NV];
+    double tot[NV], sum[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double s = 0.0;
-        for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
-            s += __ldcg(a.partials + (long long)b * NV + q);
-        tot[q] = block_sum(s, red);
+    for (int q = 0; q < NV; ++q) sum[q] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sum[q] += __ldcg(a.partials + (long long)b * NV + q);
     }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = block_sum(sum[q], red);
     if (threadIdx.x == 0) {
         fin(tot);
         *a.counter = 0u;
     }
+}
+
+// Reduce NV FP64 values over the grid: block partials, then the last block
+// sums them in block order (deterministic) and calls `fin`.
+template <int NV, class Fin>
+__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const FieldArgs &a, Fin fin,
+                                                unsigned block, unsigned nblocks) {
+    __shared__ double red[32];
+    double bs[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) bs[q] = block_sum(v[q], red);
+    finalize_partials<NV>(bs, a, fin, block, nblocks);
 }
 
 template <typename R, bool CPLX>
@@ -101,74 +171,119 @@ __global__ void __launch_bounds__(kReduceThreads) norm_kernel(FieldArgs a) {
         blockIdx.x, gridDim.x);
 }
 
-// Observables: one thread per (j, k) walks along i.  Per site it adds |psi|^2,
-// V|psi|^2, |psi|^4, x^2|psi|^2, y^2|psi|^2, z^2|psi|^2 and the squared
-// forward differences to the +x, +y and +z neighbours (links that leave the
-// grid do not exist).  psi is read through the pending scale.
+// Observables: one thread per (j, k) and segment of i (kObsSeg nodes) walks
+// along i.  The 9 sums (|psi|^2, V|psi|^2, |psi|^4, x^2|psi|^2, y^2|psi|^2,
+// z^2|psi|^2 and the squared forward differences to the +x, +y and +z
+// neighbours; links that leave the grid do not exist, and the +x link of
+// site i is counted at i + 1) come from 6 per-thread sums of the unscaled
+// field: y and z are fixed along a thread's walk, so its y^2 and z^2 sums
+// are y^2 and z^2 times its |psi|^2 sum, and V = gamma^2 x^2/2 +
+// (nu^2 y^2 + lambda^2 z^2)/2 splits the same way; the pending scale s
+// multiplies the quadratic sums by s^2 and |psi|^4 by s^4.  Sums run in the
+// field's precision over chunks of 8 sites and are added to a compensated
+// per-thread total (FP32) or a plain one (FP64).
+constexpr int kObsSeg = 128;
+
+template <typename R> __device__ __forceinline__ Acc<R> acc_scaled(const Acc<R> &a, R f) {
+    Acc<R> r;
+    if constexpr (sizeof(R) == 4) {
+        r.s = a.s * f;
+        r.c = a.c * f;
+    } else {
+        r.s = a.s * f;
+    }
+    return r;
+}
+template <typename R> __device__ __forceinline__ Acc<R> acc_sum(const Acc<R> &a, const Acc<R> &b) {
+    Acc<R> r = a;
+    r.add(b.s);
+    if constexpr (sizeof(R) == 4) r.c += b.c;
+    return r;
+}
+
 template <typename R, bool CPLX>
 __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned block, unsigned nblocks) {
     using E = Elem<R, CPLX>;
     using V = typename E::V;
     const V *psi = static_cast<const V *>(a.psi);
     const long long plane = (long long)a.n[1] * a.n[2];
-    const long long L = (long long)block * blockDim.x + threadIdx.x;
+    const unsigned pblocks = (unsigned)((plane + kReduceThreads - 1) / kReduceThreads);
+    const long long L = (long long)(block % pblocks) * blockDim.x + threadIdx.x;
+    const int i0 = (int)(block / pblocks) * kObsSeg;
+    const int i1 = min(i0 + kObsSeg, a.n[0]);
+    enum { S_RHO, S_X2, S_RHO2, S_LX, S_LY, S_LZ, S_N };
+    Acc<R> sum[S_N];
     Acc<R> acc[9];
     if (L < plane) {
         const int j = (int)(L / a.n[2]), k = (int)(L % a.n[2]);
-        const R s = (R)__ldg(a.scale);
+        const R x0 = (R)a.origin[0], dx = (R)a.d[0];
+        const bool has_y = j + 1 < a.n[1], has_z = k + 1 < a.n[2];
+        V prev = i0 > 0 ? psi[(i0 - 1) * plane + L] : E::from_real(0.0);
+        // chunks of 8 sites: all of a chunk's loads are issued before its sums
+        for (int c0 = i0; c0 < i1; c0 += 8) {
+            V p[8], qy[8], qz[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                p[u] = qy[u] = qz[u] = E::from_real(0.0);
+                if (c0 + u < i1) {
+                    const long long off = (c0 + u) * plane + L;
+                    p[u] = psi[off];
+                    if (has_y) qy[u] = psi[off + a.n[2]];
+                    if (has_z) qz[u] = psi[off + 1];
+                }
+            }
+            R part[S_N];
+#pragma unroll
+            for (int q = 0; q < S_N; ++q) part[q] = R(0);
+            const R fc0 = (R)c0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = c0 + u;
+                if (i < i1) {
+                    const R rho = E::abs2r(p[u]);
+                    const R x = fma(fc0 + (R)u, dx, x0);
+                    part[S_RHO] += rho;
+                    part[S_X2] = fma(x * x, rho, part[S_X2]);
+                    part[S_RHO2] = fma(rho, rho, part[S_RHO2]);
+                    if (i > 0) part[S_LX] += E::diff2(p[u], prev);
+                    if (has_y) part[S_LY] += E::diff2(qy[u], p[u]);
+                    if (has_z) part[S_LZ] += E::diff2(qz[u], p[u]);
+                    prev = p[u];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < S_N; ++q) sum[q].add(part[q]);
+        }
+        const R sc = (R)__ldg(a.scale);
+        const R s2 = sc * sc;
         const R y = (R)(a.origin[1] + j * a.d[1]);
         const R z = (R)(a.origin[2] + k * a.d[2]);
+        acc[O_RHO] = acc_scaled(sum[S_RHO], s2);
+        acc[O_X2] = acc_scaled(sum[S_X2], s2);
+        acc[O_RHO2] = acc_scaled(sum[S_RHO2], s2 * s2);
+        acc[O_LX] = acc_scaled(sum[S_LX], s2);
+        acc[O_LY] = acc_scaled(sum[S_LY], s2);
+        acc[O_LZ] = acc_scaled(sum[S_LZ], s2);
+        acc[O_Y2] = acc_scaled(acc[O_RHO], y * y);
+        acc[O_Z2] = acc_scaled(acc[O_RHO], z * z);
         const R vyz = (R)a.half_w2[1] * y * y + (R)a.half_w2[2] * z * z;
-        const R x0 = (R)a.origin[0], dx = (R)a.d[0], hx = (R)a.half_w2[0];
-        const bool has_y = j + 1 < a.n[1], has_z = k + 1 < a.n[2];
-        V prev = E::from_real(0.0);
-        for (int i = 0; i < a.n[0]; ++i) {
-            const long long off = i * plane + L;
-            const V p = E::scaled(psi[off], s);
-            const R rho = E::abs2r(p);
-            const R x = fma((R)i, dx, x0);
-            acc[O_RHO].add(rho);
-            acc[O_V].add(fma(hx * x, x, vyz) * rho);
-            acc[O_RHO2].add(rho * rho);
-            acc[O_X2].add(x * x * rho);
-            acc[O_Y2].add(y * y * rho);
-            acc[O_Z2].add(z * z * rho);
-            if (i > 0) {
-                if constexpr (CPLX) {
-                    const R dre = p.re - prev.re, dim = p.im - prev.im;
-                    acc[O_LX].add(dre * dre + dim * dim);
-                } else {
-                    const R df = p - prev;
-                    acc[O_LX].add(df * df);
-                }
-            }
-            if (has_y) {
-                const V q = E::scaled(psi[off + a.n[2]], s);
-                if constexpr (CPLX) {
-                    const R dre = q.re - p.re, dim = q.im - p.im;
-                    acc[O_LY].add(dre * dre + dim * dim);
-                } else {
-                    const R df = q - p;
-                    acc[O_LY].add(df * df);
-                }
-            }
-            if (has_z) {
-                const V q = E::scaled(psi[off + 1], s);
-                if constexpr (CPLX) {
-                    const R dre = q.re - p.re, dim = q.im - p.im;
-                    acc[O_LZ].add(dre * dre + dim * dim);
-                } else {
-                    const R df = q - p;
-                    acc[O_LZ].add(df * df);
-                }
-            }
-            prev = p;
-        }
+        acc[O_V] = acc_sum(acc_scaled(acc[O_X2], (R)a.half_w2[0]), acc_scaled(acc[O_RHO], vyz));
     }
-    double v[9];
+    double bs[9];
+    if constexpr (sizeof(R) == 4) {
+        float ps[9], pc[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] = acc[q].value();
-    reduce_finalize<9>(v, a, [&](const double *t) {
+        for (int q = 0; q < 9; ++q) {
+            ps[q] = acc[q].s;
+            pc[q] = acc[q].c;
+        }
+        block_sum_pairs<9>(ps, pc, bs);
+    } else {
+        __shared__ double red[32];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) bs[q] = block_sum(acc[q].value(), red);
+    }
+    finalize_partials<9>(bs, a, [&](const double *t) {
         double *o = a.out;
         for (int q = 0; q < 9; ++q) o[q] = t[q];
         const double dv = a.dV;
@@ -262,7 +377,8 @@ cudaError_t launch_observables_batch(Prec p, bool cplx, const FieldArgs *args, c
 
 int observables_blocks(const FieldArgs &a) {
     const long long plane = (long long)a.n[1] * a.n[2];
-    return (int)((plane + kReduceThreads - 1) / kReduceThreads);
+    const long long segs = (a.n[0] + kObsSeg - 1) / kObsSeg;
+    return (int)((plane + kReduceThreads - 1) / kReduceThreads * segs);
 }
 
 cudaError_t launch_gaussian(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s) {

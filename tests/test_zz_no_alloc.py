@@ -54,8 +54,11 @@ def test_noalloc_matches_handle_observables_on_two_calls(prec, field):
         torch.cuda.synchronize()
         o = out.cpu().numpy()
         assert o[15] == 1.0
+        # FP64: the same sums; FP32: the same compensated sums grouped
+        # differently (the handle path sums chunks of 8 sites per segment of x)
+        tol = 1e-12 if prec == "f64" else 1e-6
         for key, v in zip(KEYS, o[9:15]):
-            assert abs(v - ref[key]) <= 1e-12 * abs(ref[key]), (key, v, ref[key])
+            assert abs(v - ref[key]) <= tol * abs(ref[key]), (key, v, ref[key])
 
     # the read scale multiplies psi: the norm grows by its square, mu does not
     out.fill_(-1.0)
@@ -63,7 +66,7 @@ def test_noalloc_matches_handle_observables_on_two_calls(prec, field):
                                        ctypes.c_void_p(out.data_ptr()), stream)
     assert st == N.GP_OK
     torch.cuda.synchronize()
-    assert abs(out[9].item() - 4.0 * ref["norm"]) <= 1e-12 * 4.0 * ref["norm"]
+    assert abs(out[9].item() - 4.0 * ref["norm"]) <= tol * 4.0 * ref["norm"]
     gp.close()
 
 
