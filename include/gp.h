@@ -147,6 +147,15 @@ gp_status gp_step_real(gp_handle h, int nsteps);
 gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max_steps,
                             int *steps_taken);
 
+/* Stop rule of gp_run_imag_until: 0 (default) |mu(n) - mu(n-K)| < mu_tol,
+ * the program summary's convergence test on the chemical potential; 1 also
+ * requires |E(n) - E(n-K)| < mu_tol.  mu is not variational: from a start
+ * close to the ground state it can turn around on its way in, and at the
+ * turning point its change between checks drops below the tolerance long
+ * before convergence.  E decreases monotonically in imaginary time, so rule 1
+ * stops only where both have settled.  No effect on the steps themselves. */
+gp_status gp_set_stop_rule(gp_handle h, int rule);
+
 /* Compute the observables of the current psi into *out (synchronises).
  * GP_ERR_NONFINITE if any reduction is NaN or Inf. */
 gp_status gp_observables(gp_handle h, gp_obs *out);
@@ -304,6 +313,8 @@ gp_status gp_batch_observables(gp_batch b, gp_obs *out);
  * max_steps.  steps_taken[i] (may be NULL) receives each instance's steps. */
 gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, int max_steps,
                                   int *steps_taken);
+/* Stop rule of gp_batch_run_imag_until, as gp_set_stop_rule. */
+gp_status gp_batch_set_stop_rule(gp_batch b, int rule);
 /* The window per axis used for the whole batch. */
 gp_status gp_batch_get_window(gp_batch b, int window[3]);
 /* Segment length and count per axis of instance i. */

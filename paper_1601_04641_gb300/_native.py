@@ -60,6 +60,7 @@ SIGNATURES = {
     "gp_set_axis_window": (_i, [Handle, _i, _i]),
     "gp_set_pair_lines": (_i, [Handle, _i]),
     "gp_set_tma": (_i, [Handle, _i]),
+    "gp_set_stop_rule": (_i, [Handle, _i]),
     "gp_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_set_threads": (_i, [Handle, _i, _i]),
     "gp_set_segments": (_i, [Handle, _i, _i]),
@@ -81,6 +82,7 @@ SIGNATURES = {
     "gp_batch_get_window": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_batch_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_batch_set_graph_block": (_i, [Handle, _i]),
+    "gp_batch_set_stop_rule": (_i, [Handle, _i]),
     "gp_batch_last_error": (ctypes.c_char_p, [Handle]),
     "gp_nn_param_count": (_i, []),
     "gp_nn_create": (_i, [ctypes.POINTER(Handle), ctypes.c_ulonglong, _vp]),

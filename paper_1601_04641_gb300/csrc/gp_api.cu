@@ -116,6 +116,7 @@ struct gp_handle_s {
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     bool tma_z = true;         // ... through TMA tiles where the grid allows it
+    int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol
     bool zmap_ok = false;      // zmap[b]: tensor map of buf[b] as n_lines rows of nz elements
     CUtensorMap zmap[2];
     unsigned int *d_status = nullptr;  // nonzero after a kernel's bounded wait expired
@@ -672,7 +673,7 @@ gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max
     gp_obs o;
     st = observables(h, &o);
     if (st != GP_OK) return st;
-    double mu_prev = o.mu;
+    double mu_prev = o.mu, e_prev = o.energy;
     int taken = 0;
     while (taken < max_steps) {
         const int n = std::min(check_every, max_steps - taken);
@@ -681,11 +682,20 @@ gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max
         taken += n;
         st = observables(h, &o);
         if (st != GP_OK) break;
-        if (std::fabs(o.mu - mu_prev) < mu_tol) break;
+        if (std::fabs(o.mu - mu_prev) < mu_tol && (h->stop_rule == 0 || std::fabs(o.energy - e_prev) < mu_tol))
+            break;
         mu_prev = o.mu;
+        e_prev = o.energy;
     }
     if (steps_taken) *steps_taken = taken;
     return st;
+}
+
+gp_status gp_set_stop_rule(gp_handle h, int rule) {
+    if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    if (rule != 0 && rule != 1) return fail(h, GP_ERR_ARG, "rule must be 0 or 1");
+    h->stop_rule = rule;
+    return GP_OK;
 }
 
 gp_status gp_observables(gp_handle h, gp_obs *out) {

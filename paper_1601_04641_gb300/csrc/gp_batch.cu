@@ -73,6 +73,7 @@ struct gp_batch_s {
     LaunchSet act;                 // the active instances
     bool dirty = true;
     int graph_block = 16;
+    int stop_rule = 0;             // as gp_set_stop_rule
     cudaStream_t cap_stream = nullptr;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, steps)
     std::vector<void *> scratch;   // device allocations of the launch sets
@@ -513,9 +514,12 @@ gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, in
     if ((st = build_set(b)) != GP_OK) return st;
     std::vector<double> host;
     if ((st = observe_active(b, host)) != GP_OK) return st;
-    std::vector<double> mu_prev(b->n);
+    std::vector<double> mu_prev(b->n), e_prev(b->n);
     std::vector<int> taken(b->n, 0);
-    for (int i = 0; i < b->n; ++i) mu_prev[i] = host[(size_t)i * O_COUNT + O_MU];
+    for (int i = 0; i < b->n; ++i) {
+        mu_prev[i] = host[(size_t)i * O_COUNT + O_MU];
+        e_prev[i] = host[(size_t)i * O_COUNT + O_E];
+    }
     int done = 0;
     while (done < max_steps && !b->act.members.empty()) {
         const int n = std::min(check_every, max_steps - done);
@@ -530,11 +534,13 @@ gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, in
                 st = bfail(b, GP_ERR_NONFINITE, "instance " + std::to_string(i) + " became non-finite");
                 break;
             }
-            if (std::fabs(o[O_MU] - mu_prev[i]) < mu_tol) {
+            if (std::fabs(o[O_MU] - mu_prev[i]) < mu_tol &&
+                (b->stop_rule == 0 || std::fabs(o[O_E] - e_prev[i]) < mu_tol)) {
                 b->inst[i].active = false;
                 changed = true;
             }
             mu_prev[i] = o[O_MU];
+            e_prev[i] = o[O_E];
         }
         if (st != GP_OK) break;
         if (changed) {
@@ -580,6 +586,13 @@ gp_status gp_nn_predict_batch(gp_nn net, gp_batch b) {
         I.step = 0;
         I.t = 0.0;
     }
+    return GP_OK;
+}
+
+gp_status gp_batch_set_stop_rule(gp_batch b, int rule) {
+    if (!b) return bfail(b, GP_ERR_ARG, "NULL batch");
+    if (rule != 0 && rule != 1) return bfail(b, GP_ERR_ARG, "rule must be 0 or 1");
+    b->stop_rule = rule;
     return GP_OK;
 }
 

@@ -12,13 +12,16 @@
 // stored at unit u ^ ((r / 2) mod 4)), so the 8 lanes of a quarter warp
 // reading one column of their own rows hit 8 different bank groups.
 //
-// Each chunk of B results goes back the same way: written into a swizzled
-// output tile and stored by one TMA instruction.  A TMA row must start on a
-// 16-byte boundary and the first interior node is node 1, so tile k holds
-// nodes [kB, kB + B): the chunk's last result is carried in registers into
-// slot 0 of the next tile, and node 0 and node N-1 (the Dirichlet ends) are
-// written as zeros.  Rows past the last line read zeros (TMA fill) and are
-// clipped on store; so are nodes past N-1.
+// Each chunk of B results goes back the same way, stored by one TMA
+// instruction from a swizzled tile.  A TMA row must start on a 16-byte
+// boundary and the first interior node is node 1, so tile k holds nodes
+// [kB, kB + B): the chunk's last result is carried in registers into slot 0
+// of the next tile, and node 0 and node N-1 (the Dirichlet ends) are written
+// as zeros.  Tile k covers exactly the nodes of input box k, which no read
+// needs once chunk k's forward sweep is done, so the tile is written into
+// box k's ring slot; the slot is refilled only after the tile store has read
+// it.  Rows past the last line read zeros (TMA fill) and are clipped on
+// store; so are nodes past N-1.
 //
 // Every wait on an mbarrier is bounded (about a second of clock cycles);
 // on expiry the warp stops waiting, finishes without trusting its data and
@@ -38,12 +41,19 @@ constexpr int kTmaWarps = 2;                         // warps per block
 constexpr int kTmaRows = 64;                         // lines per warp (two per lane)
 constexpr int kTmaRowBytes = 64;                     // one box row = one swizzle span
 constexpr int kTmaBoxBytes = kTmaRows * kTmaRowBytes;
-constexpr int kTmaSlots = 4;                         // input ring
-constexpr int kTmaWarpBytes = (kTmaSlots + 1) * kTmaBoxBytes;  // ring + output tile
-constexpr size_t kTmaSmemBytes = 1024 + (size_t)kTmaWarps * kTmaWarpBytes + kTmaWarps * kTmaSlots * 8;
+constexpr int kTmaAhead = 2;                         // boxes in flight beyond the one needed
 constexpr long long kTmaSpinCycles = 1LL << 31;
 
 template <typename E> __host__ __device__ constexpr int tma_chunk() { return kTmaRowBytes / (int)sizeof(E); }
+// Ring slots: a chunk reads up to (W + B + 1) / B boxes past its own, two more
+// are in flight, and the chunk's own box holds its output tile until the
+// tile store has read it.
+template <typename E, int W> __host__ __device__ constexpr int tma_slots() {
+    return (W + tma_chunk<E>() + 1) / tma_chunk<E>() + kTmaAhead + 1;
+}
+template <typename E, int W> __host__ __device__ constexpr size_t tma_smem_bytes() {
+    return 1024 + (size_t)kTmaWarps * tma_slots<E, W>() * (kTmaBoxBytes + 8);
+}
 
 // Forms the TMA kernel is built for: 4- or 8-byte elements, and a register
 // ring of B + W pair values within 256 bytes per thread (beyond that the
@@ -117,7 +127,16 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, unsigned sr
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// Wait until at most `pending` of this thread's newest bulk groups still read
+// shared memory (more than 3 waits for 3).
+__device__ __forceinline__ void bulk_wait_read(int pending) {
+    switch (pending) {
+    case 0: asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.bulk.wait_group.read 2;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.bulk.wait_group.read 3;\n" ::: "memory"); break;
+    }
+}
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 // Generic-proxy writes to shared memory become visible to later TMA reads.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -136,6 +155,7 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
     using C = typename F::C;
     constexpr int B = tma_chunk<E>();
     constexpr int ES = sizeof(E);
+    constexpr int S = tma_slots<E, W>();
     static_assert(W % 2 == 0 && B % 2 == 0, "node pairs must not straddle a 16-byte unit");
     const int lane = threadIdx.x & 31;
     const int N = a.N, n = N - 2;
@@ -144,64 +164,64 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
     const C *ipm1 = static_cast<const C *>(a.ip);
     const R kap = (R)a.kappa;
     const unsigned ring = smem_u32(wbase);
-    unsigned char *const otile = wbase + kTmaSlots * kTmaBoxBytes;
-    const unsigned otile_s = ring + kTmaSlots * kTmaBoxBytes;
     const unsigned xm = ((lane >> 1) & 3) << 4;  // swizzle of rows lane and lane + 32
     const unsigned ra = lane * kTmaRowBytes, rb = (lane + 32) * kTmaRowBytes;
 
     if (lane == 0) {
-        for (int s = 0; s < kTmaSlots; ++s) mbar_init(bar0 + 8 * s, 1);
+        for (int s = 0; s < S; ++s) mbar_init(bar0 + 8 * s, 1);
         mbar_init_fence();
     }
     __syncwarp();
+    int stored = 0;  // tiles stored so far (tile k is bulk group k)
+    // Lane 0: load box b into its slot, after the store of the tile that
+    // slot held (tile b - S) has finished reading it.
     auto issue = [&](int b) {
-        const unsigned s = b & (kTmaSlots - 1);
+        const unsigned s = b % S;
+        // tile b - S was stored at the end of chunk b - S; later chunks
+        // have stored at most the tiles after it (S exceeds the boxes a
+        // chunk reads ahead plus the boxes in flight)
+        if (b >= S) bulk_wait_read(max(0, stored - 1 - (b - S)));
         mbar_arrive_expect_tx(bar0 + 8 * s, kTmaBoxBytes);
         tma_load_2d(ring + s * kTmaBoxBytes, tin, bar0 + 8 * s, b * B, y0);
     };
-    int issued = min(3, nbox), waited = 0;
+    int issued = min(kTmaAhead + 1, nbox), waited = 0;
     bool ok = true;
     if (lane == 0)
         for (int b = 0; b < issued; ++b) issue(b);
-    // Make box k readable and keep boxes up to k + 2 in flight.  Box k + 2
-    // reuses the slot of box k - 2, so no read of a box below k - 1 may
-    // follow this call.
+    // Make box k readable and keep kTmaAhead boxes beyond it in flight.
     auto need = [&](int k) {
         if (k < waited) return;
-        for (; waited <= k; ++waited)
-            ok = mbar_wait_bounded(bar0 + 8 * (waited & (kTmaSlots - 1)), (waited / kTmaSlots) & 1, ok) && ok;
+        for (; waited <= k; ++waited) ok = mbar_wait_bounded(bar0 + 8 * (waited % S), (waited / S) & 1, ok) && ok;
         __syncwarp();
-        const int lim = min(k + 3, nbox);
+        const int lim = min(k + kTmaAhead + 1, nbox);
         if (lane == 0)
             for (int b = issued; b < lim; ++b) issue(b);
         issued = max(issued, lim);
     };
     // Nodes c, c+1 (c even) of box k, for both of the lane's rows.
     auto rd2 = [&](int k, int c, V &v0, V &v1) {
-        const unsigned char *slot = wbase + (k & (kTmaSlots - 1)) * kTmaBoxBytes;
+        const unsigned char *slot = wbase + (k % S) * kTmaBoxBytes;
         const unsigned off = (unsigned)(c * ES) ^ xm;
         const E2<E> pa = *reinterpret_cast<const E2<E> *>(slot + ra + off);
         const E2<E> pb = *reinterpret_cast<const E2<E> *>(slot + rb + off);
         v0 = M::load(MV{pa.x, pb.x});
         v1 = M::load(MV{pa.y, pb.y});
     };
-    auto wr2 = [&](int s, V v0, V v1) {  // slots s, s+1 (s even) of the output tile
+    auto wr2 = [&](int k, int s, V v0, V v1) {  // nodes s, s+1 (s even) of tile k
+        unsigned char *tile = wbase + (k % S) * kTmaBoxBytes;
         const unsigned off = (unsigned)(s * ES) ^ xm;
         const MV m0 = M::store(v0), m1 = M::store(v1);
-        *reinterpret_cast<E2<E> *>(otile + ra + off) = E2<E>{m0.a, m1.a};
-        *reinterpret_cast<E2<E> *>(otile + rb + off) = E2<E>{m0.b, m1.b};
+        *reinterpret_cast<E2<E> *>(tile + ra + off) = E2<E>{m0.a, m1.a};
+        *reinterpret_cast<E2<E> *>(tile + rb + off) = E2<E>{m0.b, m1.b};
     };
-    auto tile_free = [&]() {  // the previous tile store has read the tile
-        if (lane == 0) bulk_wait_read_all();
-        __syncwarp();
-    };
-    auto store_tile = [&](int x) {
+    auto store_tile = [&](int k) {
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-            tma_store_2d(tout, otile_s, x, y0);
+            tma_store_2d(tout, ring + (k % S) * kTmaBoxBytes, k * B, y0);
             bulk_commit();
         }
+        ++stored;
     };
 
     Acc<R> acc;
@@ -246,7 +266,6 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
             pm = p0;
             p0 = p1;
         }
-        tile_free();
         V phi = D[B + W - 1];
 #pragma unroll
         for (int q = B + W - 2; q >= B; --q) phi = M::back(D[q], S ? cps : ldc(cp + t0 + q), phi);
@@ -258,12 +277,12 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
             csum += M::abs2(phi);
             if (q == B - 1) next = phi;
             else if ((q & 1) == 0) hi = phi;
-            else wr2(q + 1, phi, hi);
+            else wr2(j, q + 1, phi, hi);
         }
-        wr2(0, carry, hi);
+        wr2(j, 0, carry, hi);
         carry = next;
         acc.add(csum);
-        store_tile(t0);
+        store_tile(j);
 #pragma unroll
         for (int q = 0; q < W; ++q) D[q] = D[B + q];
     };
@@ -308,7 +327,6 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
 #pragma unroll
         for (int kt = 0; kt < NT; ++kt) {
             if ((j + kt) * B <= N - 1) {
-                tile_free();
                 auto slot = [&](int s) {  // tile slot s holds node t0 + 1 + q
                     const int q = kt * B + s - 1;
                     V v = M::zero();
@@ -317,8 +335,8 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
                     return v;
                 };
 #pragma unroll
-                for (int s = 0; s < B; s += 2) wr2(s, slot(s), slot(s + 1));
-                store_tile((j + kt) * B);
+                for (int s = 0; s < B; s += 2) wr2(j + kt, s, slot(s), slot(s + 1));
+                store_tile(j + kt);
             }
         }
     }
@@ -327,8 +345,7 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
     if (!ok) {
         // give copies that may still be landing a fresh bound before the
         // block's shared memory is released
-        for (int b = max(0, issued - kTmaSlots); b < issued; ++b)
-            mbar_wait_bounded(bar0 + 8 * (b & (kTmaSlots - 1)), (b / kTmaSlots) & 1, true);
+        for (int b = max(0, issued - S); b < issued; ++b) mbar_wait_bounded(bar0 + 8 * (b % S), (b / S) & 1, true);
         if (lane == 0 && a.status) atomicOr(a.status, 1u);
     }
     return acc.value();
@@ -339,12 +356,13 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) sweep_tma_kernel(SweepArgs 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                             ~static_cast<uintptr_t>(1023));
+    constexpr int S = tma_slots<typename F::V, W>();
     const int warp = threadIdx.x >> 5;
     const long long L0 = ((long long)blockIdx.x * kTmaWarps + warp) * kTmaRows;
     double v = 0.0;
     if (L0 < a.n_lines)
-        v = tma_body<F, R, W>(a, &maps.in, &maps.out, base + warp * kTmaWarpBytes,
-                              smem_u32(base + kTmaWarps * kTmaWarpBytes) + 8 * kTmaSlots * warp, (int)L0);
+        v = tma_body<F, R, W>(a, &maps.in, &maps.out, base + warp * S * kTmaBoxBytes,
+                              smem_u32(base + kTmaWarps * S * kTmaBoxBytes) + 8 * S * warp, (int)L0);
     norm_finalize(v, a, blockIdx.x, gridDim.x);
 }
 

@@ -29,14 +29,15 @@ static cudaError_t launch_tma_w(const SweepArgs &a, const TmaMaps &m, cudaStream
     if constexpr (tma_supported<F, W>()) {
         const long long rows = (long long)kTmaWarps * kTmaRows;
         const unsigned grid = (unsigned)((a.n_lines + rows - 1) / rows);
+        constexpr size_t smem = tma_smem_bytes<typename F::V, W>();
         static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory
         if (!attr) {
             cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<F, R, W>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        sweep_tma_kernel<F, R, W><<<grid, kTmaWarps * 32, kTmaSmemBytes, s>>>(a, m);
+        sweep_tma_kernel<F, R, W><<<grid, kTmaWarps * 32, smem, s>>>(a, m);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidValue;

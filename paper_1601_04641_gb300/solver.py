@@ -178,6 +178,10 @@ class GP:
         """z sweep through TMA tiles (default where the grid allows it)."""
         self._ck(self.lib.gp_set_tma(self.h, int(bool(on))))
 
+    def set_stop_rule(self, rule):
+        """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
+        self._ck(self.lib.gp_set_stop_rule(self.h, int(rule)))
+
     def tma_in_use(self):
         v = ctypes.c_int(0)
         self._ck(self.lib.gp_get_tma(self.h, ctypes.byref(v)))
@@ -273,10 +277,9 @@ class Batch:
         self._ck(self.lib.gp_batch_get_segments(self.h, int(i), a, b))
         return tuple(a), tuple(b)
 
-    def autotune(self, realtime=False, reps=5, cache_path=None):
-        """Time candidate launch settings per axis and keep the fastest."""
-        self._ck(self.lib.gp_autotune(self.h, int(bool(realtime)), int(reps),
-                                      cache_path.encode() if cache_path else None))
+    def set_stop_rule(self, rule):
+        """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
+        self._ck(self.lib.gp_batch_set_stop_rule(self.h, int(rule)))
 
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_batch_set_graph_block(self.h, int(steps)))

@@ -135,15 +135,18 @@ def train(net, steps, points=32768, lr=(3e-3, 3e-4), seed=0, report=None):
     return losses
 
 
-def run_from_starts(net, problems, tol, precision="f64", field="real", max_steps=40000, device=None):
-    """Imaginary time to |dmu| < tol from the Gaussian and from the network's
-    prediction (with the energy fallback), each as one batch.  Returns a dict
-    of per-instance steps, energies of the starts, converged mu and times."""
+def run_from_starts(net, problems, tol, precision="f64", field="real", max_steps=40000, device=None,
+                    stop_rule=1):
+    """Imaginary time to |dmu| < tol (and |dE| < tol with stop_rule 1, see
+    gp_set_stop_rule) from the Gaussian and from the network's prediction
+    (with the energy fallback), each as one batch.  Returns a dict of
+    per-instance steps, energies of the starts, converged mu and times."""
     import torch
     from .solver import GP, Batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     bg = Batch(problems, precision, field, device=device)
+    bg.set_stop_rule(stop_rule)
     bg.init_gaussian()
     e_gauss = [o["energy"] for o in bg.observables()]
     steps_g = bg.run_imag_until(tol, 10, max_steps)
@@ -154,6 +157,7 @@ def run_from_starts(net, problems, tol, precision="f64", field="real", max_steps
 
     t0 = time.perf_counter()
     bn = Batch(problems, precision, field, device=device)
+    bn.set_stop_rule(stop_rule)
     net.predict_batch(bn)
     try:
         e_nn = [o["energy"] for o in bn.observables()]

@@ -87,3 +87,33 @@ def test_batch_fp32_ground_states_match_oracle():
         assert steps[i] < 20000
         assert abs(obs[i]["mu"] - mu_ref) <= 1e-5 * mu_ref, (p.name, obs[i]["mu"], mu_ref)
     b.close()
+
+
+def test_stop_rule_with_energy_never_stops_earlier():
+    """Rule 1 (|dmu| < tol and |dE| < tol) takes at least as many steps as the
+    mu-only rule and ends at least as close to a tightly converged mu, for a
+    single handle and for a batch (same instances)."""
+    from paper_1601_04641_gb300.solver import GP, Batch
+    probs = uneven(4, seed=9)
+    out = {}
+    for rule in (0, 1):
+        b = Batch(probs, "f64", "real")
+        b.set_stop_rule(rule)
+        b.init_gaussian()
+        steps = b.run_imag_until(1e-7, 10, 50000)
+        out[rule] = (steps, [o["mu"] for o in b.observables()])
+        b.close()
+    for i, p in enumerate(probs):
+        gp = GP(p.shape, p.d, p.dt, p.omega, p.g, "f64", "real")
+        gp.init_gaussian()
+        gp.run_imag_until(1e-12, 10, 400000)
+        mu_ref = gp.observables()["mu"]
+        gp.set_stop_rule(1)
+        gp.init_gaussian()
+        gp.run_imag_until(1e-7, 10, 50000)
+        mu1 = gp.observables()["mu"]
+        gp.close()
+        assert out[1][0][i] >= out[0][0][i]
+        assert abs(out[1][1][i] - mu_ref) <= abs(out[0][1][i] - mu_ref) + 1e-12
+        assert abs(out[1][1][i] - mu_ref) <= 1e-5 * mu_ref
+        assert abs(mu1 - mu_ref) <= 1e-5 * mu_ref
