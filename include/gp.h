@@ -147,6 +147,16 @@ gp_status gp_step_real(gp_handle h, int nsteps);
 gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max_steps,
                             int *steps_taken);
 
+/* Imaginary time through `levels` steps: level l sets dt to the current dt
+ * times dt_scale[l] (coefficients rebuilt) and runs gp_run_imag_until with
+ * mu_tol[l]; dt is restored afterwards.  CN is stable at any dt and each
+ * dt's fixed point differs from the next by O(dt^2) in mu, so converging at a
+ * coarse dt first and finishing at the target dt (last level scale 1) reaches
+ * the target's fixed point in fewer steps than starting there.  max_steps
+ * bounds each level; *steps_taken (may be NULL) is their sum. */
+gp_status gp_run_imag_schedule(gp_handle h, int levels, const double *dt_scale, const double *mu_tol,
+                               int check_every, int max_steps, int *steps_taken);
+
 /* Stop rule of gp_run_imag_until: 0 (default) |mu(n) - mu(n-K)| < mu_tol,
  * the program summary's convergence test on the chemical potential; 1 also
  * requires |E(n) - E(n-K)| < mu_tol.  mu is not variational: from a start
@@ -315,6 +325,13 @@ gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, in
                                   int *steps_taken);
 /* Stop rule of gp_batch_run_imag_until, as gp_set_stop_rule. */
 gp_status gp_batch_set_stop_rule(gp_batch b, int rule);
+/* Every instance steps with its creation dt times `scale` (tables, windows
+ * and segments rebuilt; psi kept). */
+gp_status gp_batch_set_dt_scale(gp_batch b, double scale);
+/* As gp_run_imag_schedule, for every instance (scales relative to the
+ * current scale, which is restored afterwards); steps_taken[i] per instance. */
+gp_status gp_batch_run_imag_schedule(gp_batch b, int levels, const double *dt_scale, const double *mu_tol,
+                                     int check_every, int max_steps, int *steps_taken);
 /* The window per axis used for the whole batch. */
 gp_status gp_batch_get_window(gp_batch b, int window[3]);
 /* Segment length and count per axis of instance i. */

@@ -61,6 +61,8 @@ SIGNATURES = {
     "gp_set_pair_lines": (_i, [Handle, _i]),
     "gp_set_tma": (_i, [Handle, _i]),
     "gp_set_stop_rule": (_i, [Handle, _i]),
+    "gp_run_imag_schedule": (_i, [Handle, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, _i,
+                                  ctypes.POINTER(_i)]),
     "gp_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_set_threads": (_i, [Handle, _i, _i]),
     "gp_set_segments": (_i, [Handle, _i, _i]),
@@ -83,6 +85,9 @@ SIGNATURES = {
     "gp_batch_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_batch_set_graph_block": (_i, [Handle, _i]),
     "gp_batch_set_stop_rule": (_i, [Handle, _i]),
+    "gp_batch_set_dt_scale": (_i, [Handle, _d]),
+    "gp_batch_run_imag_schedule": (_i, [Handle, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, _i,
+                                        ctypes.POINTER(_i)]),
     "gp_batch_last_error": (ctypes.c_char_p, [Handle]),
     "gp_nn_param_count": (_i, []),
     "gp_nn_create": (_i, [ctypes.POINTER(Handle), ctypes.c_ulonglong, _vp]),

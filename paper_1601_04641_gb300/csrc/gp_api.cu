@@ -691,6 +691,29 @@ gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max
     return st;
 }
 
+gp_status gp_run_imag_schedule(gp_handle h, int levels, const double *dt_scale, const double *mu_tol,
+                               int check_every, int max_steps, int *steps_taken) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (levels < 1 || !dt_scale || !mu_tol) return fail(h, GP_ERR_ARG, "need levels >= 1 and both arrays");
+    for (int l = 0; l < levels; ++l)
+        if (!finite_pos(dt_scale[l])) return fail(h, GP_ERR_ARG, "dt scales must be finite and > 0");
+    const double base = h->dt;
+    int total = 0;
+    for (int l = 0; l < levels && st == GP_OK; ++l) {
+        int part = 0;
+        if (dt_scale[l] * base != h->dt) st = gp_set_dt(h, base * dt_scale[l]);
+        if (st == GP_OK) st = gp_run_imag_until(h, mu_tol[l], check_every, max_steps, &part);
+        total += part;
+    }
+    if (h->dt != base) {
+        const gp_status back = gp_set_dt(h, base);
+        if (st == GP_OK) st = back;
+    }
+    if (steps_taken) *steps_taken = total;
+    return st;
+}
+
 gp_status gp_set_stop_rule(gp_handle h, int rule) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
     if (rule != 0 && rule != 1) return fail(h, GP_ERR_ARG, "rule must be 0 or 1");

@@ -24,6 +24,7 @@ namespace {
 
 struct Inst {
     Geometry G;
+    double dt0 = 0.0;       // the step given at creation (G.dt = dt0 * the batch's dt scale)
     Tables tab;
     size_t psi_off = 0;     // byte offset in each packed psi buffer
     size_t sites = 0, bytes = 0;
@@ -74,6 +75,8 @@ struct gp_batch_s {
     bool dirty = true;
     int graph_block = 16;
     int stop_rule = 0;             // as gp_set_stop_rule
+    double dt_scale = 1.0;         // every instance steps with dt0 * dt_scale
+    size_t tab_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (parity, steps)
     std::vector<void *> scratch;   // device allocations of the launch sets
@@ -121,6 +124,50 @@ unsigned sweep_gridx(gp_batch b, const Inst &I, int ax) {
     const long long lines = axis_lines(I.G, ax);
     (void)b;
     return (unsigned)((lines + kSweepThreads - 1) / kSweepThreads);
+}
+
+// Tables, windows and segments of every instance for dt = dt0 * scale.  One
+// window per axis for the whole batch: the largest of the instances' smallest
+// admissible windows (0 if any instance admits none, or FP64).
+void configure(gp_batch b, double scale, std::vector<char> &host) {
+    const bool f32 = b->prec == GP_F32;
+    host.clear();
+    for (Inst &I : b->inst) {
+        I.G.dt = I.dt0 * scale;
+        I.tab = Tables();
+        append_tables(I.G, f32, 1, host, I.tab);
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        int w = 0;
+        bool all = f32;
+        for (size_t i = 0; i < b->inst.size() && all; ++i) {
+            const int m = b->inst[i].tab.ax[0][ax].min_window;
+            if (m == 0) all = false;
+            w = std::max(w, m);
+        }
+        b->window[ax] = all ? w : 0;
+    }
+    b->contiguous_z = b->window[2] > 0;
+    for (Inst &I : b->inst)
+        for (int ax = 0; ax < 3; ++ax)
+            choose_segments(I.G, ax, b->window[ax], 1, (int)b->elem, ax == 2 && b->contiguous_z, 0,
+                            &I.seg_len[ax], &I.n_seg[ax]);
+    b->dt_scale = scale;
+}
+
+// Norm / observables partials an instance may need under any window choice
+// (the windowed forms cut the strided axes into the most segments).
+size_t partial_cap(gp_batch b, const Inst &I) {
+    size_t cap = kInitNormBlocks;
+    for (int ax = 0; ax < 3; ++ax) {
+        int len, nseg;
+        choose_segments(I.G, ax, 4, 1, (int)b->elem, ax == 2, 0, &len, &nseg);
+        cap = std::max(cap, (size_t)sweep_gridx(b, I, ax) * nseg);
+        choose_segments(I.G, ax, 0, 1, (int)b->elem, false, 0, &len, &nseg);
+        cap = std::max(cap, (size_t)sweep_gridx(b, I, ax) * nseg);
+    }
+    FieldArgs fa = field_args(I.G, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return std::max(cap, (size_t)observables_blocks(fa) * 9);
 }
 
 FieldArgs inst_field_args(gp_batch b, int i) {
@@ -348,7 +395,6 @@ gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const doub
     b->elem = (prec == GP_F64 ? 8 : 4) * (field == GP_COMPLEX ? 2 : 1);
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     b->inst.resize(n);
-    const bool f32 = prec == GP_F32;
     std::vector<char> host;
     size_t psi = 0, parts = 0;
     for (int i = 0; i < n; ++i) {
@@ -359,44 +405,24 @@ gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const doub
         I.G.d[0] = grids[i].dx;
         I.G.d[1] = grids[i].dy;
         I.G.d[2] = grids[i].dz;
-        I.G.dt = dt[i];
+        I.dt0 = dt[i];
         I.G.w[0] = gamma[i];
         I.G.w[1] = nu[i];
         I.G.w[2] = lambda[i];
         I.G.g = g[i];
-        append_tables(I.G, f32, 1, host, I.tab);
         I.sites = (size_t)grids[i].nx * grids[i].ny * grids[i].nz;
         I.bytes = I.sites * b->elem;
         I.psi_off = psi;
         psi = align_up(psi + I.bytes, 256);
     }
-    // one window per axis for the whole batch: the largest of the instances'
-    // smallest admissible windows (0 if any instance admits none, or FP64)
-    for (int ax = 0; ax < 3; ++ax) {
-        int w = 0;
-        bool all = f32;
-        for (int i = 0; i < n && all; ++i) {
-            const int m = b->inst[i].tab.ax[0][ax].min_window;
-            if (m == 0) all = false;
-            w = std::max(w, m);
-        }
-        b->window[ax] = all ? w : 0;
-    }
-    b->contiguous_z = b->window[2] > 0;
+    configure(b, 1.0, host);
     for (int i = 0; i < n; ++i) {
         Inst &I = b->inst[i];
-        size_t cap = kInitNormBlocks;
-        for (int ax = 0; ax < 3; ++ax) {
-            choose_segments(I.G, ax, b->window[ax], 1, (int)b->elem, ax == 2 && b->contiguous_z, 0,
-                            &I.seg_len[ax], &I.n_seg[ax]);
-            cap = std::max(cap, (size_t)sweep_gridx(b, I, ax) * I.n_seg[ax]);
-        }
-        FieldArgs fa = field_args(I.G, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
-        cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
         I.part_off = parts;
-        parts += align_up(cap, 32);
+        parts += align_up(partial_cap(b, I), 32);
     }
     b->psi_bytes = psi;
+    b->tab_bytes = host.size();
     if (cudaMalloc(&b->d_psi[0], psi) != cudaSuccess || cudaMalloc(&b->d_psi[1], psi) != cudaSuccess ||
         cudaMalloc(&b->d_tab, host.size()) != cudaSuccess ||
         cudaMalloc(&b->d_scal, 2 * n * sizeof(double)) != cudaSuccess ||
@@ -587,6 +613,41 @@ gp_status gp_nn_predict_batch(gp_nn net, gp_batch b) {
         I.t = 0.0;
     }
     return GP_OK;
+}
+
+gp_status gp_batch_set_dt_scale(gp_batch b, double scale) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (!(scale > 0.0) || !std::isfinite(scale)) return bfail(b, GP_ERR_ARG, "scale must be finite and > 0");
+    if (scale == b->dt_scale) return GP_OK;
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    std::vector<char> host;
+    configure(b, scale, host);
+    if (host.size() != b->tab_bytes) return bfail(b, GP_ERR_STATE, "table layout changed with dt");
+    GPB_CK(b, cudaMemcpyAsync(b->d_tab, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream));
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    free_set(b);
+    b->dirty = true;
+    return GP_OK;
+}
+
+gp_status gp_batch_run_imag_schedule(gp_batch b, int levels, const double *dt_scale, const double *mu_tol,
+                                     int check_every, int max_steps, int *steps_taken) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (levels < 1 || !dt_scale || !mu_tol) return bfail(b, GP_ERR_ARG, "need levels >= 1 and both arrays");
+    std::vector<int> total(b->n, 0), part(b->n, 0);
+    const double base = b->dt_scale;
+    for (int l = 0; l < levels && st == GP_OK; ++l) {
+        st = gp_batch_set_dt_scale(b, base * dt_scale[l]);
+        if (st == GP_OK) st = gp_batch_run_imag_until(b, mu_tol[l], check_every, max_steps, part.data());
+        for (int i = 0; i < b->n; ++i) total[i] += part[i];
+    }
+    const gp_status back = gp_batch_set_dt_scale(b, base);
+    if (st == GP_OK) st = back;
+    if (steps_taken)
+        for (int i = 0; i < b->n; ++i) steps_taken[i] = total[i];
+    return st;
 }
 
 gp_status gp_batch_set_stop_rule(gp_batch b, int rule) {

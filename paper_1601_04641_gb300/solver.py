@@ -182,6 +182,16 @@ class GP:
         """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
         self._ck(self.lib.gp_set_stop_rule(self.h, int(rule)))
 
+    def run_imag_schedule(self, levels, check_every=10, max_steps=100000):
+        """levels: sequence of (dt scale, mu tol); see gp_run_imag_schedule."""
+        n = len(levels)
+        sc = (ctypes.c_double * n)(*[float(a) for a, _ in levels])
+        tl = (ctypes.c_double * n)(*[float(b) for _, b in levels])
+        taken = ctypes.c_int(0)
+        self._ck(self.lib.gp_run_imag_schedule(self.h, n, sc, tl, int(check_every), int(max_steps),
+                                               ctypes.byref(taken)))
+        return taken.value
+
     def tma_in_use(self):
         v = ctypes.c_int(0)
         self._ck(self.lib.gp_get_tma(self.h, ctypes.byref(v)))
@@ -280,6 +290,18 @@ class Batch:
     def set_stop_rule(self, rule):
         """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
         self._ck(self.lib.gp_batch_set_stop_rule(self.h, int(rule)))
+
+    def set_dt_scale(self, scale):
+        self._ck(self.lib.gp_batch_set_dt_scale(self.h, float(scale)))
+
+    def run_imag_schedule(self, levels, check_every=10, max_steps=100000):
+        """levels: sequence of (dt scale, mu tol); steps per instance."""
+        n = len(levels)
+        sc = (ctypes.c_double * n)(*[float(a) for a, _ in levels])
+        tl = (ctypes.c_double * n)(*[float(b) for _, b in levels])
+        taken = (ctypes.c_int * self.n)()
+        self._ck(self.lib.gp_batch_run_imag_schedule(self.h, n, sc, tl, int(check_every), int(max_steps), taken))
+        return list(taken)
 
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_batch_set_graph_block(self.h, int(steps)))

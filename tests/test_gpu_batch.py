@@ -117,3 +117,42 @@ def test_stop_rule_with_energy_never_stops_earlier():
         assert abs(out[1][1][i] - mu_ref) <= abs(out[0][1][i] - mu_ref) + 1e-12
         assert abs(out[1][1][i] - mu_ref) <= 1e-5 * mu_ref
         assert abs(mu1 - mu_ref) <= 1e-5 * mu_ref
+
+
+@pytest.mark.parametrize("prec,field", [("f64", "real"), ("f32", "complex")])
+def test_dt_schedule_reaches_the_target_fixed_point(prec, field):
+    """Converging at 10 dt first, then at dt (gp_batch_run_imag_schedule,
+    gp_run_imag_schedule) ends at the fixed point of dt -- within the stop
+    rule's residual of a tightly converged plain run -- in fewer steps than
+    the plain run, and leaves dt as it was."""
+    from paper_1601_04641_gb300.solver import GP, Batch
+    probs = uneven(5, seed=13)
+    levels = [(10.0, 1e-5), (1.0, 1e-7)]
+    b = Batch(probs, prec, field)
+    b.set_stop_rule(1)
+    b.init_gaussian()
+    steps_s = b.run_imag_schedule(levels, 10, 50000)
+    mu_s = [o["mu"] for o in b.observables()]
+    b.init_gaussian()
+    steps_p = b.run_imag_until(1e-7, 10, 50000)
+    mu_p = [o["mu"] for o in b.observables()]
+    b.close()
+    assert sum(steps_s) < sum(steps_p), (steps_s, steps_p)
+    tol = 2e-5 if prec == "f32" else 1e-5
+    for i, p in enumerate(probs):
+        gp = GP(p.shape, p.d, p.dt, p.omega, p.g, "f64", "real")
+        gp.init_gaussian()
+        gp.run_imag_until(1e-12, 10, 400000)
+        mu_ref = gp.observables()["mu"]
+        # the single-handle schedule, then a plain continuation at the restored dt
+        gp.set_stop_rule(1)
+        gp.init_gaussian()
+        gp.run_imag_schedule(levels, 10, 50000)
+        mu_h = gp.observables()["mu"]
+        gp.run_imag_until(1e-12, 10, 400000)
+        mu_after = gp.observables()["mu"]
+        gp.close()
+        assert abs(mu_s[i] - mu_ref) <= tol * mu_ref, (i, mu_s[i], mu_ref)
+        assert abs(mu_p[i] - mu_ref) <= tol * mu_ref
+        assert abs(mu_h - mu_ref) <= 1e-5 * mu_ref
+        assert abs(mu_after - mu_ref) <= 1e-7 * mu_ref  # dt restored (a wrong dt moves mu by ~1e-4)
