@@ -192,7 +192,7 @@ gp_status gp_step_stage(gp_handle h, int stage, int realtime);
  * default stream). */
 gp_status gp_set_stream(gp_handle h, void *cuda_stream);
 
-/* Block until the handle's queued work is done.  Returns GP_ERR_CUDA if a
+/* Block until the handle's queued work is done.  Returns GP_ERR_TIMEOUT if a
  * sweep kernel gave up waiting for its TMA copies (each wait is bounded to
  * about a second); gp_observables reports the same. */
 gp_status gp_sync(gp_handle h);
@@ -391,6 +391,18 @@ const char *gp_nn_last_error(gp_nn net);
  * failed create, or failed gp_observables_noalloc, when h is NULL).  Never
  * NULL. */
 const char *gp_last_error(gp_handle h);
+
+/* ---- failure-detection self-tests (no counterpart in the paper) ----
+ * gp_selftest_bounded_wait launches one warp on the given stream that waits,
+ * with the bounded mbarrier wait the TMA sweep uses, on an mbarrier whose
+ * phase completes (*completed = 1 expected) and on one that nothing arrives
+ * at, giving up after `cycles` clock cycles (*expired = 1 expected).  Nothing
+ * is copied and the kernel ends within about 2 * cycles; synchronises.
+ * gp_debug_fail_alloc(n) makes the n-th next device allocation of the library
+ * fail as if the device were out of memory (n <= 0: no failure); every
+ * creating call then returns GP_ERR_NOMEM and frees what it had allocated. */
+gp_status gp_selftest_bounded_wait(long long cycles, void *cuda_stream, int *completed, int *expired);
+void gp_debug_fail_alloc(int n);
 
 /* Library version string. */
 const char *gp_version(void);

@@ -208,7 +208,7 @@ gp_status build_coefficients(gp_handle h) {
         h->d_coef = nullptr;
     }
     if (!h->d_coef) {
-        if (cudaMalloc(&h->d_coef, off) != cudaSuccess) {
+        if (gpcn::dev_malloc(&h->d_coef, off) != cudaSuccess) {
             cudaGetLastError();
             return fail(h, GP_ERR_NOMEM, "cudaMalloc of the coefficient tables failed");
         }
@@ -236,10 +236,10 @@ gp_status alloc_scratch(gp_handle h) {
     cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32) * (size_t)(h->n[2] - 2));
     FieldArgs fa = handle_field_args(h);
     cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
-    if (cudaMalloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->d_scal, S_COUNT * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->d_obs, O_COUNT * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->d_counter, 2 * sizeof(unsigned int)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
+        gpcn::dev_malloc(&h->d_scal, S_COUNT * sizeof(double)) != cudaSuccess ||
+        gpcn::dev_malloc(&h->d_obs, O_COUNT * sizeof(double)) != cudaSuccess ||
+        gpcn::dev_malloc(&h->d_counter, 2 * sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         return fail(h, GP_ERR_NOMEM, "cudaMalloc of reduction scratch failed");
     }
@@ -310,7 +310,7 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
         h->buf[0] = dev_psi;
         h->own_buf0 = false;
     } else {
-        if (cudaMalloc(&h->buf[0], h->bytes) != cudaSuccess) {
+        if (gpcn::dev_malloc(&h->buf[0], h->bytes) != cudaSuccess) {
             cudaGetLastError();
             delete h;
             return fail(nullptr, GP_ERR_NOMEM, "cudaMalloc of psi failed");
@@ -322,7 +322,7 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
             return fail(nullptr, GP_ERR_CUDA, "cudaMemsetAsync of psi failed");
         }
     }
-    if (cudaMalloc(&h->buf[1], h->bytes) != cudaSuccess) {
+    if (gpcn::dev_malloc(&h->buf[1], h->bytes) != cudaSuccess) {
         cudaGetLastError();
         release(h);
         return fail(nullptr, GP_ERR_NOMEM, "cudaMalloc of the second psi buffer failed");
@@ -360,7 +360,7 @@ gp_status check_status(gp_handle h) {
     GP_CK(h, cudaMemcpy(&flag, h->d_status, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) {
         cudaMemset(h->d_status, 0, sizeof(flag));
-        return fail(h, GP_ERR_CUDA, "a sweep kernel's wait for its TMA copies expired; psi is not trustworthy");
+        return fail(h, GP_ERR_TIMEOUT, "a sweep kernel's wait for its TMA copies expired; psi is not trustworthy");
     }
     return GP_OK;
 }
@@ -435,7 +435,7 @@ gp_status run_graph_block(gp_handle h, int g, bool realtime, bool with_obs) {
             cudaGetLastError();
             return GP_ERR_STATE;
         }
-        if (with_obs && !h->d_obs_graph && cudaMalloc(&h->d_obs_graph, O_COUNT * sizeof(double)) != cudaSuccess) {
+        if (with_obs && !h->d_obs_graph && gpcn::dev_malloc(&h->d_obs_graph, O_COUNT * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return GP_ERR_STATE;
         }
@@ -740,7 +740,7 @@ gp_status gp_set_tracking(gp_handle h, int every, int capacity) {
         h->track_cap = 0;
     }
     if (every > 0 && !h->d_track) {
-        if (cudaMalloc(&h->d_track, (size_t)capacity * O_COUNT * sizeof(double)) != cudaSuccess) {
+        if (gpcn::dev_malloc(&h->d_track, (size_t)capacity * O_COUNT * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return fail(h, GP_ERR_NOMEM, "cudaMalloc of the tracking history failed");
         }

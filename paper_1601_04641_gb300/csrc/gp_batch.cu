@@ -110,7 +110,7 @@ template <typename T> gp_status upload(gp_batch b, const std::vector<T> &v, T **
     *out = nullptr;
     if (v.empty()) return GP_OK;
     void *p = nullptr;
-    if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, GP_ERR_NOMEM, "cudaMalloc of batch launch tables failed");
     }
@@ -423,12 +423,12 @@ gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const doub
     }
     b->psi_bytes = psi;
     b->tab_bytes = host.size();
-    if (cudaMalloc(&b->d_psi[0], psi) != cudaSuccess || cudaMalloc(&b->d_psi[1], psi) != cudaSuccess ||
-        cudaMalloc(&b->d_tab, host.size()) != cudaSuccess ||
-        cudaMalloc(&b->d_scal, 2 * n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->d_obs, (size_t)n * O_COUNT * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->d_partials, parts * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->d_counters, n * sizeof(unsigned int)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&b->d_psi[0], psi) != cudaSuccess || gpcn::dev_malloc(&b->d_psi[1], psi) != cudaSuccess ||
+        gpcn::dev_malloc(&b->d_tab, host.size()) != cudaSuccess ||
+        gpcn::dev_malloc(&b->d_scal, 2 * n * sizeof(double)) != cudaSuccess ||
+        gpcn::dev_malloc(&b->d_obs, (size_t)n * O_COUNT * sizeof(double)) != cudaSuccess ||
+        gpcn::dev_malloc(&b->d_partials, parts * sizeof(double)) != cudaSuccess ||
+        gpcn::dev_malloc(&b->d_counters, n * sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         release_batch(b);
         return bfail(nullptr, GP_ERR_NOMEM, "device allocation of the batch failed");

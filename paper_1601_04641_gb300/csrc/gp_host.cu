@@ -2,6 +2,7 @@
 #include "gp_host.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -229,6 +230,27 @@ FieldArgs field_args(const Geometry &G, const void *psi, const double *scale, do
     a.sites = (long long)G.n[0] * G.n[1] * G.n[2];
     return a;
 }
+
+// ------------------------------------------------------------------ allocation hook
+namespace {
+std::atomic<int> g_fail_alloc{0};  // > 0: the g_fail_alloc-th next allocation fails
+}
+
+cudaError_t dev_malloc_bytes(void **p, size_t bytes) {
+    int n = g_fail_alloc.load();
+    while (n > 0) {
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void set_fail_alloc(int n) { g_fail_alloc.store(n > 0 ? n : 0); }
 
 // ------------------------------------------------------------------ TMA maps
 namespace {

@@ -128,6 +128,13 @@ cudaError_t launch_sweep_batch(const SweepLaunch &L, const BatchLaunch &b, cudaS
 // Threads per block of the batched kernels.
 constexpr int kBatchLineThreads = 64;
 void set_thread_error(const char *msg);
+// Every device allocation of the library goes through dev_malloc, so that
+// tests can make the n-th next one fail (gp_debug_fail_alloc).
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+template <typename T> inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
+void set_fail_alloc(int n);
 // Encode the tensor map of an array of n_lines rows of N elements of
 // elem_bytes (4 or 8) for the TMA z sweep; false if the layout does not allow
 // one (row pitch or base not 16-byte aligned) or the driver has no encoder.

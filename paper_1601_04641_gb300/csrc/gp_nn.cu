@@ -55,8 +55,8 @@ gp_status ensure_partials(gp_nn net, int blocks) {
     cudaFree(net->d_lpart);
     net->d_partials = nullptr;
     net->d_lpart = nullptr;
-    if (cudaMalloc(&net->d_partials, (size_t)blocks * kNNParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&net->d_lpart, (size_t)blocks * sizeof(float)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&net->d_partials, (size_t)blocks * kNNParams * sizeof(float)) != cudaSuccess ||
+        gpcn::dev_malloc(&net->d_lpart, (size_t)blocks * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         net->part_blocks = 0;
         return nfail(net, GP_ERR_NOMEM, "cudaMalloc of gradient partials failed");
@@ -116,12 +116,12 @@ gp_status gp_nn_create(gp_nn *out, unsigned long long seed, void *cuda_stream) {
         return nfail(nullptr, GP_ERR_CUDA, "no CUDA device");
     }
     net->stream = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaMalloc(&net->P.master, kNNParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&net->P.m, kNNParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&net->P.v, kNNParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&net->P.deploy, kDeployCount * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc(&net->d_grad, kNNParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&net->d_loss, sizeof(float)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&net->P.master, kNNParams * sizeof(float)) != cudaSuccess ||
+        gpcn::dev_malloc(&net->P.m, kNNParams * sizeof(float)) != cudaSuccess ||
+        gpcn::dev_malloc(&net->P.v, kNNParams * sizeof(float)) != cudaSuccess ||
+        gpcn::dev_malloc(&net->P.deploy, kDeployCount * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        gpcn::dev_malloc(&net->d_grad, kNNParams * sizeof(float)) != cudaSuccess ||
+        gpcn::dev_malloc(&net->d_loss, sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         gp_nn_destroy(net);
         return nfail(nullptr, GP_ERR_NOMEM, "cudaMalloc of the network failed");
@@ -209,7 +209,7 @@ gp_status gp_nn_set_data(gp_nn net, int n, const gp_grid *grids, const double *g
     }
     cudaFree(net->d_inst);
     net->d_inst = nullptr;
-    if (cudaMalloc(&net->d_inst, n * sizeof(NNInstance)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&net->d_inst, n * sizeof(NNInstance)) != cudaSuccess) {
         cudaGetLastError();
         return nfail(net, GP_ERR_NOMEM, "cudaMalloc of the instance table failed");
     }
@@ -264,7 +264,7 @@ gp_status gp_nn_loss_grad(gp_nn net, int count, const int *instance, const long 
     if ((st = ensure_partials(net, blocks)) != GP_OK) return st;
     int *d_i = nullptr;
     long long *d_s = nullptr;
-    if (cudaMalloc(&d_i, count * sizeof(int)) != cudaSuccess || cudaMalloc(&d_s, count * sizeof(long long)) != cudaSuccess) {
+    if (gpcn::dev_malloc(&d_i, count * sizeof(int)) != cudaSuccess || gpcn::dev_malloc(&d_s, count * sizeof(long long)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(d_i);
         return nfail(net, GP_ERR_NOMEM, "cudaMalloc of the samples failed");

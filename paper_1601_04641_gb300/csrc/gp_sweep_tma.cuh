@@ -102,15 +102,15 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
         : "memory");
     return done != 0;
 }
-// Wait for the phase of `bar` with the given parity, for at most
-// kTmaSpinCycles clock cycles (none at all once `ok` is false).  Returns
-// false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, bool ok) {
+// Wait for the phase of `bar` with the given parity, for at most `cycles`
+// clock cycles (none at all once `ok` is false).  Returns false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, bool ok,
+                                                  long long cycles = kTmaSpinCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     if (!ok) return false;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kTmaSpinCycles) return false;
+        if (clock64() - t0 > cycles) return false;
     return true;
 }
 __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar, int x, int y) {

@@ -1,0 +1,96 @@
+"""Failure detection without a GPU fault: the bounded device wait gives up and
+reports (a wait that nothing can satisfy, a short bound, nothing copied);
+allocation failures made on the host return GP_ERR_NOMEM and leave no device
+memory behind; odd line lengths (3, 5, 33, 127) against the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_04641_gb300 import _native as N
+from paper_1601_04641_gb300 import build, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def test_bounded_wait_gives_up_and_reports():
+    import torch
+    lib = N.load()
+    done, expired = ctypes.c_int(-1), ctypes.c_int(-1)
+    stream = torch.cuda.current_stream().cuda_stream
+    st = lib.gp_selftest_bounded_wait(1 << 20, ctypes.c_void_p(stream), ctypes.byref(done), ctypes.byref(expired))
+    assert st == N.GP_OK, lib.gp_last_error(None)
+    assert done.value == 1 and expired.value == 1
+    # the context is still usable
+    from paper_1601_04641_gb300.solver import GP
+    gp = GP((12, 10, 16), (0.3, 0.3, 0.3), 0.01, (1, 1, 1), 1.0, "f32", "complex")
+    gp.init_gaussian()
+    gp.step_imag(5)
+    assert abs(gp.observables()["norm"] - 1.0) < 1e-5
+    gp.close()
+    assert lib.gp_selftest_bounded_wait(0, None, ctypes.byref(done), ctypes.byref(expired)) == N.GP_ERR_ARG
+
+
+def _creates():
+    from paper_1601_04641_gb300.solver import GP, Batch
+    from paper_1601_04641_gb300.warmstart import Net
+    ps = inputs.batch_problems(3, seed=3)
+    ps = [inputs.sized_box((20, 16, 12), p.omega, p.g) for p in ps]
+    return {
+        "handle": lambda: GP((20, 18, 16), (0.3, 0.3, 0.3), 0.01, (1, 1, 1), 1.0, "f32", "complex"),
+        "batch": lambda: Batch(ps, "f32", "real"),
+        "net": lambda: Net(seed=1),
+    }
+
+
+@pytest.mark.parametrize("kind", ["handle", "batch", "net"])
+def test_allocation_failures_return_nomem_and_free_everything(kind):
+    import torch
+    lib = N.load()
+    make = _creates()[kind]
+    obj = make()  # warm up: lazily loaded modules, first-use allocations
+    obj.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    for k in range(1, 40):
+        lib.gp_debug_fail_alloc(k)
+        try:
+            obj = make()
+        except N.GPError as e:
+            assert e.status == N.GP_ERR_NOMEM, str(e)
+            failures += 1
+            continue
+        finally:
+            lib.gp_debug_fail_alloc(0)
+        obj.close()  # k exceeded the allocations of one create: it succeeded
+        break
+    else:
+        pytest.fail("a create still failed after 39 allocations")
+    assert failures >= 4
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 8 << 20
+
+
+@pytest.mark.parametrize("shape", [(33, 5, 127), (127, 3, 33), (5, 127, 3)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_odd_line_lengths(shape, prec):
+    from paper_1601_04641_gb300.solver import GP
+    d, omega, g, dt = (0.21, 0.27, 0.19), (1.2, 0.9, 1.6), 6.0, 0.003
+    psi0 = inputs.random_field(shape, seed=17)
+    for realtime in (False, True):
+        gp = GP(shape, d, dt, omega, g, prec, "complex")
+        gp.set_psi(psi0.astype(gp.np_dtype))
+        (gp.step_real if realtime else gp.step_imag)(4)
+        got = gp.get_psi().astype(np.complex128)
+        gp.close()
+        ref = psi0.astype(np.complex64).astype(np.complex128) if prec == "f32" else psi0.copy()
+        oracle.step(ref, d, dt, omega, g, realtime, 4)
+        tol = 1e-12 if prec == "f64" else 4e-6
+        assert float(np.max(np.abs(got - ref))) <= tol * float(np.max(np.abs(ref))), (shape, prec, realtime)
