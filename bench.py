@@ -48,9 +48,9 @@ WORKLOADS = {
 NCU_TRAFFIC = {
     # ncu --set full of the 480x400x160 half-depth case (profiles/), scaled x2
     # by sites to a full 480x400x320 launch: (read + write) bytes per launch
-    ("real_large", "zsweep_norm"): (2 * (245.872896e6 + 197.295360e6), "e151ec1d69fd8886"),
-    ("real_large", "kick_xsweep"): (2 * (257.070592e6 + 192.659200e6), "e151ec1d69fd8886"),
-    ("real_large", "ysweep"): (2 * (250.793728e6 + 193.942272e6), "e151ec1d69fd8886"),
+    ("real_large", "zsweep_norm"): (2 * (245.977088e6 + 198.082560e6), "07c838761d646f18"),
+    ("real_large", "kick_xsweep"): (2 * (257.067008e6 + 192.767744e6), "07c838761d646f18"),
+    ("real_large", "ysweep"): (2 * (250.945536e6 + 193.392384e6), "07c838761d646f18"),
 }
 
 
