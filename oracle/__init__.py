@@ -62,9 +62,11 @@ def _load():
             lib.oracle_step.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int]
             lib.oracle_observables.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_double, _dp]
+            lib.oracle_step_strang.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, ctypes.c_double,
+                                               ctypes.c_int]
             for f in (lib.oracle_thomas, lib.oracle_gaussian, lib.oracle_kick,
                       lib.oracle_sweep, lib.oracle_renormalize, lib.oracle_step,
-                      lib.oracle_observables):
+                      lib.oracle_observables, lib.oracle_step_strang):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -85,7 +87,7 @@ class use_library:
             self.saved = _lib
             lib = ctypes.CDLL(self.path)
             for name in ("oracle_thomas", "oracle_gaussian", "oracle_kick", "oracle_sweep",
-                         "oracle_renormalize", "oracle_step", "oracle_observables"):
+                         "oracle_renormalize", "oracle_step", "oracle_observables", "oracle_step_strang"):
                 getattr(lib, name).argtypes = getattr(self.saved, name).argtypes
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -191,6 +193,18 @@ def step(psi, d, dt, omega, g, realtime, nsteps=1) -> np.ndarray:
     po, _c = _dbls(omega)
     _check(_load().oracle_step(pn, pd, psi.ctypes.data_as(_dp), float(dt), po, float(g),
                                int(bool(realtime)), int(nsteps)), "step")
+    return psi
+
+
+def step_strang(psi, d, dt, omega, g, nsteps=1) -> np.ndarray:
+    """In-place ``nsteps`` real-time steps with symmetric splitting: half
+    kick, x, y, z line solves, half kick (reading R17)."""
+    psi = _field(psi)
+    pn, _a = _ints(psi.shape)
+    pd, _b = _dbls(d)
+    po, _c = _dbls(omega)
+    _check(_load().oracle_step_strang(pn, pd, psi.ctypes.data_as(_dp), float(dt), po, float(g), int(nsteps)),
+           "step_strang")
     return psi
 
 

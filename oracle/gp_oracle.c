@@ -328,6 +328,29 @@ int oracle_step(const int n[3], const double d[3], double *psi_ri, double dt,
 }
 
 /*
+ * Symmetric (Strang) splitting in real time, reading R17: every step is a
+ * half kick exp(-i (dt/2) (V + g|psi|^2)), the x, y and z line solves with the
+ * full dt, and a second half kick, each step computed on its own (no merging
+ * of the half kicks of consecutive steps).  Real time only.
+ */
+int oracle_step_strang(const int n[3], const double d[3], double *psi_ri, double dt,
+                       const double omega[3], double g, int nsteps)
+{
+    if (nsteps < 0)
+        return ORACLE_EARG;
+    for (int s = 0; s < nsteps; s++) {
+        int rc = oracle_kick(n, d, psi_ri, 0.5 * dt, omega, g, 1);
+        for (int axis = 0; axis < 3 && rc == ORACLE_OK; axis++)
+            rc = oracle_sweep(n, d, psi_ri, axis, dt, 1);
+        if (rc == ORACLE_OK)
+            rc = oracle_kick(n, d, psi_ri, 0.5 * dt, omega, g, 1);
+        if (rc != ORACLE_OK)
+            return rc;
+    }
+    return ORACLE_OK;
+}
+
+/*
  * Observables (calcrms, calcmuen, norm), reading R4:
  *   norm = dV sum |psi|^2
  *   K    = (1/2) dV sum_axes sum_links |psi[m+1] - psi[m]|^2 / d^2

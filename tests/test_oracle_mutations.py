@@ -39,6 +39,11 @@ MUTATIONS = {
     "rms axes swapped": ("out[3] = sqrt(dv * s_x2 / norm);", "out[3] = sqrt(dv * s_y2 / norm);"),
     "last z link dropped": ("if (k + 1 < n[2]) {", "if (k + 2 < n[2]) {"),
     "gaussian width": ("exp(-0.5 * omega[0] * x * x)", "exp(-omega[0] * x * x)"),
+    "symmetric step with full kicks": ("int rc = oracle_kick(n, d, psi_ri, 0.5 * dt, omega, g, 1);",
+                                       "int rc = oracle_kick(n, d, psi_ri, 1.0 * dt, omega, g, 1);"),
+    "symmetric step without the trailing half kick": (
+        "            rc = oracle_kick(n, d, psi_ri, 0.5 * dt, omega, g, 1);\n",
+        "            rc = ORACLE_OK;\n"),
     "no renormalisation": ("if (rc == ORACLE_OK && !realtime)\n            rc = oracle_renormalize",
                            "if (rc == ORACLE_OK && realtime > 1)\n            rc = oracle_renormalize"),
 }
@@ -54,6 +59,8 @@ CHECKS = [
     pins.test_imag_time_positivity_symmetry_and_energy_descent,
     pins.test_g0_mu_converges_quadratically_in_dt,
     pins.test_thomas_fermi_limit_and_virial,
+    pins.test_strang_is_time_reversible,
+    pins.test_strang_is_second_order,
 ]
 
 

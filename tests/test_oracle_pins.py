@@ -258,3 +258,51 @@ def test_real_time_energy_drift_is_first_order():
         drifts.append(abs(oracle.observables(psi, d, omega, 40.0)["energy"] - e0) / e0)
     assert drifts[0] < 2e-2
     assert 1.6 <= drifts[0] / drifts[1] <= 2.4
+
+
+# ---------------------------------------------------------------- symmetric splitting
+def _strang_case():
+    shape, d, omega, g = (16, 14, 12), (0.35, 0.4, 0.45), (1.0, 1.3, 0.8), 20.0
+    psi0 = inputs.random_field(shape, seed=3)
+    oracle.renormalize(psi0, d)
+    return shape, d, omega, g, psi0
+
+
+def test_strang_is_time_reversible():
+    """Half kick, CN sweeps, half kick is symmetric: each CN sweep with -dt is
+    the inverse of the sweep with dt, the sweeps of different axes commute,
+    and a real-time kick keeps |psi|, so n steps with dt then n with -dt give
+    psi back to rounding.  The Lie order (kick then sweeps) does not (catches
+    a missing or misplaced half kick)."""
+    shape, d, omega, g, psi0 = _strang_case()
+    psi = psi0.copy()
+    oracle.step_strang(psi, d, 0.01, omega, g, 20)
+    oracle.step_strang(psi, d, -0.01, omega, g, 20)
+    assert np.max(np.abs(psi - psi0)) <= 1e-12 * np.max(np.abs(psi0))
+    lie = psi0.copy()
+    oracle.step(lie, d, 0.01, omega, g, True, 20)
+    oracle.step(lie, d, -0.01, omega, g, True, 20)
+    assert np.max(np.abs(lie - psi0)) >= 1e-4 * np.max(np.abs(psi0))
+
+
+def test_strang_is_second_order():
+    """Over a fixed time the symmetric splitting's error falls fourfold when
+    dt halves, the Lie splitting's twofold; both against the Lie method at a
+    32x finer step (pinned above), so a symmetric step with wrong kick
+    weights, converging to another limit, fails too."""
+    shape, d, omega, g, psi0 = _strang_case()
+    T = 0.08
+    ref = psi0.copy()
+    oracle.step(ref, d, T / 4096, omega, g, True, 4096)
+    err = {}
+    for name, fn in (("strang", lambda p, dt, n: oracle.step_strang(p, d, dt, omega, g, n)),
+                     ("lie", lambda p, dt, n: oracle.step(p, d, dt, omega, g, True, n))):
+        e = []
+        for n in (8, 16):
+            p = psi0.copy()
+            fn(p, T / n, n)
+            e.append(np.linalg.norm(p - ref) / np.linalg.norm(ref))
+        err[name] = e
+    assert 3.3 <= err["strang"][0] / err["strang"][1] <= 4.7, err
+    assert 1.7 <= err["lie"][0] / err["lie"][1] <= 2.6, err
+    assert err["strang"][1] < 0.5 * err["lie"][1]
