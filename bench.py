@@ -335,6 +335,46 @@ def e2e_region(torch, res, steps, dist):
     return el, nbytes / steps, (nbytes + obs_bytes) / steps
 
 
+def symmetric_splitting(torch, dev, steps, warmup):
+    """Both splittings of the real-time step: first order (kick, sweeps; the
+    main line) and symmetric (half kick, sweeps, half kick; records every
+    TRACK_EVERY steps settle the pending half kick).
+    - speed: the benchmark workload from the same prepared state, time per
+      step with tracking;
+    - accuracy: the FP64 240x200x160 workload over 200 steps of its dt, the
+      relative L2 distance of psi from a symmetric-splitting run at dt/8
+      (whose own error is about 1/64 of the symmetric one at dt)."""
+    out = {"speed": {"workload": None, "steps": steps}}
+    for order in (1, 2):
+        res = time_workload(torch, "real_large", steps, 0, dev)
+        gp = res["gp"]
+        gp.set_splitting(order)
+        gp.set_tracking(TRACK_EVERY, steps // TRACK_EVERY + 4)
+        gp.step_real(warmup)
+        el = timed_region(torch, res, steps, None)
+        gp.close()
+        out["speed"]["workload"] = res["problem"].name
+        out["speed"]["order_%d" % order] = {"ms_per_step": 1e3 * el / steps,
+                                            "value": res["problem"].sites * steps / el, "unit": UNIT}
+    from paper_1601_04641_gb300.solver import GP
+    p = inputs.real_medium()
+    runs = {}
+    for name, order, sub in (("order_1", 1, 1), ("order_2", 2, 1), ("reference", 2, 8)):
+        gp = GP(p.shape, p.d, p.dt / sub, p.omega, p.g, "f64", "complex", device=dev)
+        prepare(torch, gp, p, True)
+        gp.set_dt(p.dt / sub)
+        gp.set_splitting(order)
+        gp.step_real(200 * sub)
+        runs[name] = gp.get_psi(as_numpy=False)
+        gp.close()
+    ref = runs.pop("reference")
+    out["accuracy"] = {"workload": "%s, 200 steps of dt %g, FP64" % (p.name, p.dt),
+                       "rel_l2_vs_dt_over_8": {k: float(torch.linalg.vector_norm(v - ref) /
+                                                        torch.linalg.vector_norm(ref))
+                                               for k, v in runs.items()}}
+    return out
+
+
 def time_to_ground_state(torch, dev, count, tol, max_steps=20000):
     """The 64-condensate workload (uneven grids, traps, g) run to
     |mu(n) - mu(n-10)| < tol: the FP32 batched form against the plain method
@@ -532,6 +572,8 @@ def run_ours(args):
                               "kernel_ms": {k: 1e3 * v for k, v in kb2.items()}}
                 r2["gp"].close()
         line["also"] = also
+    if args.strang and world == 1:
+        line["symmetric_splitting"] = symmetric_splitting(torch, local, min(args.steps, 500), args.warmup)
     if args.gs and world == 1:
         line["time_to_ground_state"] = time_to_ground_state(torch, local, args.gs, 1e-6)
     if args.ws_train and world == 1:
@@ -563,6 +605,7 @@ def main():
     ap.add_argument("--ws-held", type=int, default=50, help="held-out condensates (200 = full set)")
     ap.add_argument("--ws-steps", type=int, default=8000, help="Adam steps")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--strang", type=int, default=1, help="1: also time the symmetric splitting")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -141,6 +141,17 @@ gp_status gp_step_imag(gp_handle h, int nsteps);
 /* Queue nsteps real-time steps (GP_COMPLEX only): kick, x, y, z line solves. */
 gp_status gp_step_real(gp_handle h, int nsteps);
 
+/* Splitting of the real-time step: 1 (default) the program summary's order,
+ * kick then the x, y and z line solves (first order in dt); 2 the symmetric
+ * form, half kick, line solves, half kick (second order, time-reversible).
+ * With order 2 consecutive steps share their half kicks (a real-time kick
+ * keeps |psi|, so two half kicks are one full kick), and the trailing half
+ * kick of the last step is applied when psi is next read or changed
+ * (gp_get_psi, gp_psi_device_ptr, gp_observables, tracking records,
+ * gp_set_g, gp_set_dt, imaginary-time steps).  Imaginary time always uses
+ * order 1.  gp_step_stage runs the order-1 stages. */
+gp_status gp_set_splitting(gp_handle h, int order);
+
 /* Imaginary-time propagation until |mu(n) - mu(n - check_every)| < mu_tol,
  * checking every check_every steps, or max_steps.  *steps_taken (may be
  * NULL) receives the number of steps.  Synchronises at every check. */

@@ -117,6 +117,8 @@ struct gp_handle_s {
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     bool tma_z = true;         // ... through TMA tiles where the grid allows it
     int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol
+    int splitting = 1;         // real time: 1 Lie (kick, sweeps), 2 symmetric (half kick, sweeps, half kick)
+    bool kick_pending = false; // symmetric splitting: buf[cur] still lacks its trailing half kick
     bool zmap_ok = false;      // zmap[b]: tensor map of buf[b] as n_lines rows of nz elements
     CUtensorMap zmap[2];
     unsigned int *d_status = nullptr;  // nonzero after a kernel's bounded wait expired
@@ -130,7 +132,12 @@ struct gp_handle_s {
     // CUDA graphs of blocks of steps, replayed on the handle's stream
     int graph_block = 16;              // steps per graph (0: launch kernel by kernel)
     cudaStream_t cap_stream = nullptr; // private stream used only for capture
-    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+    struct Graph {
+        cudaGraphExec_t exec;
+        int cur;                // the state the block leaves behind
+        bool scale_pending, kick_pending;
+    };
+    std::map<std::tuple<int, int, int, int, int, int>, Graph> graphs;
     double *d_obs_graph = nullptr;     // tracking record written inside a graph
     std::string err;
 };
@@ -265,7 +272,7 @@ void release(gp_handle h) {
     cudaFree(h->d_counter);
     cudaFree(h->d_track);
     cudaFree(h->d_obs_graph);
-    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaGetLastError();
     delete h;
@@ -395,10 +402,14 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     L.contiguous = (ax == 2 && h->contiguous_z && L.window > 0) ? 1 : 0;
     int seg_len = 0, n_seg = 0;
     segments(h, ax, L.window, &seg_len, &n_seg);
+    // symmetric splitting: the first step after a settled state starts with a
+    // half kick; later steps merge the previous trailing half kick with their
+    // leading one (a real-time kick keeps |psi|, so two half kicks are one)
+    const bool half = realtime && stage == 0 && h->splitting == 2 && !h->kick_pending;
     SweepArgs a = sweep_args(geom(h), ax, realtime, h->buf[h->cur], h->buf[h->cur ^ 1], h->d_coef,
                              h->tab, seg_len, n_seg,
                              h->d_scal + (h->scale_pending ? S_SCALE : S_ONE), h->d_partials,
-                             h->d_counter, h->d_scal + S_NORM_SWEEP, h->d_scal + S_SCALE);
+                             h->d_counter, h->d_scal + S_NORM_SWEEP, h->d_scal + S_SCALE, half);
     a.status = h->d_status;
     TmaMaps maps;
     if (L.contiguous && h->tma_z && h->zmap_ok) {
@@ -413,11 +424,24 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     h->cur ^= 1;
     if (stage == 0) h->scale_pending = false;
     if (stage == 2 && !realtime) h->scale_pending = true;
+    if (stage == 2 && realtime && h->splitting == 2) h->kick_pending = true;
+    return GP_OK;
+}
+
+// Symmetric splitting: apply the trailing half kick that buf[cur] lacks, so
+// that psi is the state after the last full step.
+gp_status settle(gp_handle h) {
+    if (!h->kick_pending) return GP_OK;
+    FieldArgs a = handle_field_args(h);
+    GP_CK(h, launch_kick(h->prec == GP_F32 ? P_F32 : P_F64, a, 0.5 * h->dt, h->buf[h->cur ^ 1], h->stream));
+    h->cur ^= 1;
+    h->scale_pending = false;
+    h->kick_pending = false;
     return GP_OK;
 }
 
 void drop_graphs(gp_handle h) {
-    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
     h->graphs.clear();
 }
 
@@ -428,7 +452,8 @@ void drop_graphs(gp_handle h) {
 // stream.  Returns GP_STATE if capture is not possible, so the caller can
 // launch the block kernel by kernel instead.
 gp_status run_graph_block(gp_handle h, int g, bool realtime, bool with_obs) {
-    const auto key = std::make_tuple(realtime ? 1 : 0, g, h->cur, h->scale_pending ? 1 : 0, with_obs ? 1 : 0);
+    const auto key = std::make_tuple(realtime ? h->splitting : 0, g, h->cur, h->scale_pending ? 1 : 0,
+                                     h->kick_pending ? 1 : 0, with_obs ? 1 : 0);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -440,7 +465,7 @@ gp_status run_graph_block(gp_handle h, int g, bool realtime, bool with_obs) {
             return GP_ERR_STATE;
         }
         const int cur0 = h->cur;
-        const bool pend0 = h->scale_pending;
+        const bool pend0 = h->scale_pending, kick0 = h->kick_pending;
         cudaStream_t user = h->stream;
         if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
@@ -450,10 +475,13 @@ gp_status run_graph_block(gp_handle h, int g, bool realtime, bool with_obs) {
         gp_status st = GP_OK;
         for (int s = 0; s < g && st == GP_OK; ++s)
             for (int stage = 0; stage < 3 && st == GP_OK; ++stage) st = run_stage(h, stage, realtime);
+        if (st == GP_OK && with_obs) st = settle(h);
         if (st == GP_OK && with_obs) st = queue_observables(h, h->d_obs_graph);
+        const gp_handle_s::Graph end{nullptr, h->cur, h->scale_pending, h->kick_pending};
         h->stream = user;
         h->cur = cur0;
         h->scale_pending = pend0;
+        h->kick_pending = kick0;
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
         cudaGraphExec_t exec = nullptr;
@@ -464,12 +492,12 @@ gp_status run_graph_block(gp_handle h, int g, bool realtime, bool with_obs) {
             cudaGetLastError();
             return GP_ERR_STATE;
         }
-        it = h->graphs.emplace(key, exec).first;
+        it = h->graphs.emplace(key, gp_handle_s::Graph{exec, end.cur, end.scale_pending, end.kick_pending}).first;
     }
-    GP_CK(h, cudaGraphLaunch(it->second, h->stream));
-    // the state the g steps leave behind
-    if ((3 * g) % 2) h->cur ^= 1;
-    h->scale_pending = !realtime;
+    GP_CK(h, cudaGraphLaunch(it->second.exec, h->stream));
+    h->cur = it->second.cur;
+    h->scale_pending = it->second.scale_pending;
+    h->kick_pending = it->second.kick_pending;
     return GP_OK;
 }
 
@@ -483,7 +511,8 @@ gp_status run_eager(gp_handle h, int nsteps, bool realtime) {
         h->step += 1;
         h->t += h->dt;
         if (h->track_every > 0 && h->step % h->track_every == 0 && h->track_count < h->track_cap) {
-            gp_status st = queue_observables(h, h->d_track + (size_t)h->track_count * O_COUNT);
+            gp_status st = settle(h);
+            if (st == GP_OK) st = queue_observables(h, h->d_track + (size_t)h->track_count * O_COUNT);
             if (st != GP_OK) return st;
             h->track_step.push_back(h->step);
             h->track_t.push_back(h->t);
@@ -497,6 +526,10 @@ gp_status run_steps(gp_handle h, int nsteps, bool realtime) {
     if (nsteps < 0) return fail(h, GP_ERR_ARG, "nsteps < 0");
     if (realtime && h->field != GP_COMPLEX)
         return fail(h, GP_ERR_STATE, "real-time steps need a GP_COMPLEX field");
+    if (!realtime) {
+        gp_status st = settle(h);
+        if (st != GP_OK) return st;
+    }
     // Whole blocks as graphs.  With tracking on, a block is track_every steps
     // ending on a tracking step (its record is copied out of the graph's
     // slot); steps up to the next tracking step go kernel by kernel.
@@ -554,7 +587,9 @@ void fill_obs(const double *o, long long step, double t, gp_obs *out) {
 }
 
 gp_status observables(gp_handle h, gp_obs *out) {
-    gp_status st = queue_observables(h, h->d_obs);
+    gp_status st = settle(h);
+    if (st != GP_OK) return st;
+    st = queue_observables(h, h->d_obs);
     if (st != GP_OK) return st;
     double o[O_COUNT];
     GP_CK(h, cudaMemcpyAsync(o, h->d_obs, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
@@ -595,6 +630,7 @@ gp_status gp_init_gaussian(gp_handle h) {
     GP_CK(h, launch_gaussian(p, cplx, a, h->stream));
     GP_CK(h, launch_norm(p, cplx, a, kNormBlocks, h->stream));
     h->scale_pending = true;
+    h->kick_pending = false;
     h->step = 0;
     h->t = 0.0;
     return GP_OK;
@@ -609,6 +645,7 @@ gp_status gp_set_psi(gp_handle h, const void *psi, int on_device) {
                              h->stream));
     if (!on_device) GP_CK(h, cudaStreamSynchronize(h->stream));
     h->scale_pending = false;
+    h->kick_pending = false;
     h->step = 0;
     h->t = 0.0;
     return GP_OK;
@@ -618,6 +655,7 @@ gp_status gp_get_psi(gp_handle h, void *psi, int on_device) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
+    if ((st = settle(h)) != GP_OK) return st;
     FieldArgs a = handle_field_args(h);
     const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
     const bool cplx = h->field == GP_COMPLEX;
@@ -638,6 +676,7 @@ gp_status gp_set_g(gp_handle h, double g) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!std::isfinite(g)) return fail(h, GP_ERR_ARG, "g must be finite");
+    if ((st = settle(h)) != GP_OK) return st;  // the pending half kick belongs to the old g
     if (g != h->g) drop_graphs(h);
     h->g = g;
     return GP_OK;
@@ -647,6 +686,7 @@ gp_status gp_set_dt(gp_handle h, double dt) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     if (!finite_pos(dt)) return fail(h, GP_ERR_ARG, "dt must be finite and > 0");
+    if ((st = settle(h)) != GP_OK) return st;  // the pending half kick belongs to the old dt
     drop_graphs(h);
     h->dt = dt;
     return build_coefficients(h);
@@ -779,7 +819,12 @@ gp_status gp_step_stage(gp_handle h, int stage, int realtime) {
     if (stage < 0 || stage > 2) return fail(h, GP_ERR_ARG, "stage must be 0, 1 or 2");
     if (realtime && h->field != GP_COMPLEX)
         return fail(h, GP_ERR_STATE, "real-time stages need a GP_COMPLEX field");
-    return run_stage(h, stage, realtime != 0);
+    if ((st = settle(h)) != GP_OK) return st;
+    const int split = h->splitting;  // single stages are the Lie form's
+    h->splitting = 1;
+    st = run_stage(h, stage, realtime != 0);
+    h->splitting = split;
+    return st;
 }
 
 gp_status gp_set_stream(gp_handle h, void *cuda_stream) {
@@ -849,6 +894,16 @@ gp_status gp_set_pair_lines(gp_handle h, int on) {
     return GP_OK;
 }
 
+gp_status gp_set_splitting(gp_handle h, int order) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (order != 1 && order != 2) return fail(h, GP_ERR_ARG, "order must be 1 or 2");
+    if ((st = settle(h)) != GP_OK) return st;
+    if (order != h->splitting) drop_graphs(h);
+    h->splitting = order;
+    return GP_OK;
+}
+
 gp_status gp_set_tma(gp_handle h, int on) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
     h->tma_z = on != 0;
@@ -888,6 +943,9 @@ gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]) {
 
 gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
     if (!h || !ptr) return fail(h, GP_ERR_ARG, "bad arguments");
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if ((st = settle(h)) != GP_OK) return st;
     *ptr = h->buf[h->cur];
     if (pending_scale) *pending_scale = h->scale_pending ? 1 : 0;
     return GP_OK;
@@ -931,11 +989,11 @@ void cache_store(const char *path, const std::string &key, const TuneChoice &c) 
 
 }  // namespace
 
-gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_path) {
-    gp_status st = enter(h);
-    if (st != GP_OK) return st;
-    if (realtime && h->field != GP_COMPLEX) return fail(h, GP_ERR_STATE, "real time needs a GP_COMPLEX field");
-    if (reps < 1) return fail(h, GP_ERR_ARG, "reps must be >= 1");
+}  // extern "C"
+
+namespace {
+gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) {
+    gp_status st = GP_OK;
     const char *path = cache_path ? cache_path : std::getenv("GP_AUTOTUNE_CACHE");
     const int mode = realtime ? 1 : 0;
     // A stage reads buf[cur] and writes only buf[cur ^ 1] (free between
@@ -1004,6 +1062,23 @@ gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_pat
     drop_graphs(h);
     return st;
 }
+}  // namespace
+
+extern "C" {
+
+gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_path) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (realtime && h->field != GP_COMPLEX) return fail(h, GP_ERR_STATE, "real time needs a GP_COMPLEX field");
+    if (reps < 1) return fail(h, GP_ERR_ARG, "reps must be >= 1");
+    if ((st = settle(h)) != GP_OK) return st;
+    const int split = h->splitting;  // trials time the Lie form's stages
+    h->splitting = 1;
+    st = autotune(h, realtime, reps, cache_path);
+    h->splitting = split;
+    return st;
+}
+
 
 gp_status gp_nn_predict(gp_nn net, gp_handle h) {
     gp_status st = enter(h);

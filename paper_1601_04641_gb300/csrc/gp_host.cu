@@ -59,6 +59,8 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
         off = align_up(off + rsz * G.n[ax], 256);
         T.phase_off[ax] = off;
         off = align_up(off + rsz * G.n[ax], 256);
+        T.phase_half_off[ax] = off;
+        off = align_up(off + rsz * G.n[ax], 256);
     }
     host.resize(off, 0);
     // exp(-dt w^2 a^2 / 2) per node of each axis: the trap part of the
@@ -70,6 +72,7 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
             const double dv = G.dt * 0.5 * G.w[ax] * G.w[ax] * a * a;
             put_real(host.data() + T.kick_off[ax] + i * rsz, std::exp(-dv), f32);
             put_real(host.data() + T.phase_off[ax] + i * rsz, dv, f32);
+            put_real(host.data() + T.phase_half_off[ax] + i * rsz, 0.5 * dv, f32);
         }
     for (int mode = 0; mode < modes; ++mode) {
         for (int ax = 0; ax < 3; ++ax) {
@@ -151,7 +154,8 @@ void choose_segments(const Geometry &G, int ax, int window, int lpt, int elem_by
 
 SweepArgs sweep_args(const Geometry &G, int ax, bool realtime, const void *in, void *out,
                      const char *tables, const Tables &T, int seg_len, int n_seg, const double *scale,
-                     double *partials, unsigned int *counter, double *norm_out, double *scale_out) {
+                     double *partials, unsigned int *counter, double *norm_out, double *scale_out,
+                     bool half_kick) {
     SweepArgs a;
     std::memset(&a, 0, sizeof(a));
     const long long ny = G.n[1], nz = G.n[2];
@@ -185,11 +189,12 @@ SweepArgs sweep_args(const Geometry &G, int ax, bool realtime, const void *in, v
         a.kick_ey = tables + T.kick_off[1];
         a.kick_ez = tables + T.kick_off[2];
     } else {
-        a.phase_ex = tables + T.phase_off[0];
-        a.phase_ey = tables + T.phase_off[1];
-        a.phase_ez = tables + T.phase_off[2];
+        const size_t *ph = half_kick ? T.phase_half_off : T.phase_off;
+        a.phase_ex = tables + ph[0];
+        a.phase_ey = tables + ph[1];
+        a.phase_ez = tables + ph[2];
     }
-    a.dt = G.dt;
+    a.dt = (realtime && half_kick) ? 0.5 * G.dt : G.dt;  // the kick's step (dt g |psi|^2)
     a.g = G.g;
     for (int q = 0; q < 3; ++q) {
         a.half_w2[q] = 0.5 * G.w[q] * G.w[q];

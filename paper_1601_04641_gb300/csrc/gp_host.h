@@ -31,6 +31,7 @@ struct Tables {
     AxisTables ax[2][3];   // [mode: 0 imaginary, 1 real][axis]
     size_t kick_off[3] = {0, 0, 0};   // exp(-dt w^2 a^2 / 2) per node (imaginary time)
     size_t phase_off[3] = {0, 0, 0};  // dt w^2 a^2 / 2 per node (real time)
+    size_t phase_half_off[3] = {0, 0, 0};  // the same for dt / 2 (symmetric splitting's half kick)
 };
 
 // Append the tables of G (modes = 1: imaginary time only, 2: both) to `host`
@@ -50,7 +51,8 @@ void choose_segments(const Geometry &G, int ax, int window, int lpt, int elem_by
 // Argument block of one sweep launch over G (ax = 0, 1, 2).
 SweepArgs sweep_args(const Geometry &G, int ax, bool realtime, const void *in, void *out,
                      const char *tables, const Tables &T, int seg_len, int n_seg, const double *scale,
-                     double *partials, unsigned int *counter, double *norm_out, double *scale_out);
+                     double *partials, unsigned int *counter, double *norm_out, double *scale_out,
+                     bool half_kick = false);
 
 // Argument block of the whole-field kernels over G.
 FieldArgs field_args(const Geometry &G, const void *psi, const double *scale, double *partials,

@@ -102,6 +102,8 @@ cudaError_t launch_gaussian(Prec p, bool cplx, const FieldArgs &a, cudaStream_t 
 cudaError_t launch_norm(Prec p, bool cplx, const FieldArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_observables(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s);
 cudaError_t launch_apply_scale(Prec p, bool cplx, const FieldArgs &a, void *dst, cudaStream_t s);
+// Real-time kick exp(-i kdt (V + g |psi|^2)) of a complex field into dst.
+cudaError_t launch_kick(Prec p, const FieldArgs &a, double kdt, void *dst, cudaStream_t s);
 
 // Observables output layout in FieldArgs::out.
 enum ObsSlot {

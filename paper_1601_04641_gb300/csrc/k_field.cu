@@ -324,6 +324,49 @@ __global__ void __launch_bounds__(kReduceThreads) observables_batch_kernel(const
     observables_body<R, CPLX>(a, blockIdx.x - f, __ldg(first + lo + 1) - f);
 }
 
+// Real-time kick of every site, psi <- exp(-i kdt (V + g |s psi|^2)) s psi
+// (the symmetric splitting's trailing half kick, kdt = dt / 2).  Every
+// constant arrives in the field's precision (FP64 work per thread would cost
+// more than the site's memory traffic on this part); a block walks
+// kKickRows rows of z, threads along z.
+template <typename R> struct KickConsts {
+    R x0, dx, y0, dy, z0, dz, hx, hy, hz, kg, kt;
+};
+constexpr int kKickRows = 16;
+
+template <typename R>
+__global__ void kick_kernel(const double *__restrict__ scale, KickConsts<R> k, const void *psi, void *dst, int nx,
+                            int ny, int nz) {
+    using V = cx<R>;
+    const R s = (R)__ldg(scale);  // once per thread: each thread walks ~kKickRows sites
+    const long long rows = (long long)nx * ny;
+    for (long long row = (long long)blockIdx.x * kKickRows, re = min(row + kKickRows, rows); row < re; ++row) {
+        const int x = (int)(row / ny), y = (int)(row % ny);
+        const R cx_ = fma((R)x, k.dx, k.x0), cy = fma((R)y, k.dy, k.y0);
+        const R vxy = fma(k.hx * cx_, cx_, k.hy * cy * cy);
+        const V *src = static_cast<const V *>(psi) + row * nz;
+        V *out = static_cast<V *>(dst) + row * nz;
+        for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+            const R cz = fma((R)z, k.dz, k.z0);
+            const V q{src[z].re * s, src[z].im * s};
+            const R th = fma(k.kg, fma(q.re, q.re, q.im * q.im), k.kt * fma(k.hz * cz, cz, vxy));
+            R sn, cs;
+            kick_sincos(th, &sn, &cs);
+            out[z] = V{fma(cs, q.re, sn * q.im), fma(cs, q.im, -sn * q.re)};
+        }
+    }
+}
+
+template <typename R> cudaError_t launch_kick_r(const FieldArgs &a, double kdt, void *dst, cudaStream_t s) {
+    KickConsts<R> k{(R)a.origin[0], (R)a.d[0], (R)a.origin[1], (R)a.d[1], (R)a.origin[2], (R)a.d[2],
+                    (R)a.half_w2[0], (R)a.half_w2[1], (R)a.half_w2[2], (R)(kdt * a.g), (R)kdt};
+    const long long rows = (long long)a.n[0] * a.n[1];
+    const unsigned blocks = (unsigned)((rows + kKickRows - 1) / kKickRows);
+    const unsigned threads = a.n[2] >= 256 ? 256 : 128;
+    kick_kernel<R><<<blocks, threads, 0, s>>>(a.scale, k, a.psi, dst, a.n[0], a.n[1], a.n[2]);
+    return cudaGetLastError();
+}
+
 template <typename R, bool CPLX>
 __global__ void apply_scale_kernel(FieldArgs a, void *dst) {
     using E = Elem<R, CPLX>;
@@ -361,6 +404,10 @@ cudaError_t dispatch_all(Prec p, bool cplx, int what, const FieldArgs &a, int bl
 }
 
 }  // namespace
+
+cudaError_t launch_kick(Prec p, const FieldArgs &a, double kdt, void *dst, cudaStream_t s) {
+    return p == P_F64 ? launch_kick_r<double>(a, kdt, dst, s) : launch_kick_r<float>(a, kdt, dst, s);
+}
 
 cudaError_t launch_observables_batch(Prec p, bool cplx, const FieldArgs *args, const unsigned *first, int n,
                                      unsigned total_blocks, cudaStream_t s) {

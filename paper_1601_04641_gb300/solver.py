@@ -182,6 +182,10 @@ class GP:
         """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
         self._ck(self.lib.gp_set_stop_rule(self.h, int(rule)))
 
+    def set_splitting(self, order):
+        """Real-time splitting: 1 kick then sweeps (default), 2 symmetric."""
+        self._ck(self.lib.gp_set_splitting(self.h, int(order)))
+
     def run_imag_schedule(self, levels, check_every=10, max_steps=100000):
         """levels: sequence of (dt scale, mu tol); see gp_run_imag_schedule."""
         n = len(levels)
