@@ -243,7 +243,7 @@ def prepare(torch, gp, p, realtime):
     torch.cuda.synchronize()
 
 
-def time_workload(torch, name, steps, warmup, dev, with_breakdown=True):
+def time_workload(torch, name, steps, warmup, dev):
     from paper_1601_04641_gb300.solver import GP
     factory, prec, field, realtime = WORKLOADS[name]
     p = factory()
