@@ -235,9 +235,10 @@ gp_status gp_set_pair_lines(gp_handle h, int on);
  * multiple of 16 bytes, a window > 0 with (chunk + window) pair values in
  * at most 256 bytes (chunk = 64 bytes of nodes: every window for FP32 real
  * fields, windows 4 and 8 for 8-byte elements), whole lines, and nz - 2 at
- * least one chunk plus the window plus 2; elsewhere the other form runs.  The arithmetic per line is the same in both.  gp_get_tma reports
- * whether the handle's buffers have tensor maps and the form is selected
- * (the per-launch conditions above still apply). */
+ * least one chunk plus the window plus 2; elsewhere the other form runs.
+ * The arithmetic per line is the same in both.  gp_get_tma reports whether
+ * the handle's buffers have tensor maps and the form is selected (the
+ * per-launch conditions above still apply). */
 gp_status gp_set_tma(gp_handle h, int on);
 gp_status gp_get_tma(gp_handle h, int *in_use);
 
@@ -268,13 +269,15 @@ gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_pat
 /* Steps per CUDA graph: gp_step_imag / gp_step_real capture blocks of this
  * many steps into a graph once and replay it (default 16; 0 or 1 launches
  * kernel by kernel).  With tracking on, blocks are track_every steps long.
- * Changing g, dt, the window, threads or segments re-captures. */
+ * Changing g, dt, the window, threads, segments or the splitting
+ * re-captures. */
 gp_status gp_set_graph_block(gp_handle h, int steps);
 
 /* Device pointer of the buffer that holds the current psi, and whether a
  * renormalisation factor is still pending on it (the value is then psi
- * times that factor; gp_get_psi applies it).  Valid until the next call
- * that queues work on the handle. */
+ * times that factor; gp_get_psi applies it).  A pending half kick of the
+ * symmetric splitting is applied first (queued on the stream).  Valid until
+ * the next call that queues work on the handle. */
 gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale);
 
 /* Observables of a caller-owned device psi, computed without allocating any
@@ -307,8 +310,8 @@ gp_status gp_observables_noalloc(const void *dev_psi, gp_grid grid, gp_precision
 
 /* ------------------------------------------------------------------ batch
  * Many independent condensates -- each with its own grid, spacings, dt,
- * trap and g (SURVEY's batched form; the paper runs one condensate per
- * program) -- advanced in imaginary time together: each step is three
+ * trap and g (the paper's programs run one condensate each) -- advanced in
+ * imaginary time together: each step is three
  * launches that cover all active instances (per-instance arguments, norm
  * partials and counters), blocks of steps are replayed from CUDA graphs, and
  * gp_batch_run_imag_until drops converged instances from the launches.  All
