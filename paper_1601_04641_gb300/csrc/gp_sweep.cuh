@@ -111,12 +111,8 @@ template <typename R> __device__ __noinline__ cx<R> sincos_full(R x) {
     return r;
 }
 template <typename R> __device__ __noinline__ R expm_full(R y) { return g_exp(-y); }
-// |x| in x's own precision (a float must not go through the FP64 pipe, which
-// runs at a small fraction of the FP32 rate on this part).
-__device__ __forceinline__ float abs_r(float x) { return fabsf(x); }
-__device__ __forceinline__ double abs_r(double x) { return fabs(x); }
 template <typename R> __device__ __forceinline__ void kick_sincos(R x, R *sn, R *cs) {
-    if (abs_r(x) <= Series<R>::kTrig) {
+    if (fabs(x) <= Series<R>::kTrig) {
         Series<R>::sincos(x, sn, cs);
     } else {
         const cx<R> r = sincos_full(x);
@@ -125,7 +121,7 @@ template <typename R> __device__ __forceinline__ void kick_sincos(R x, R *sn, R 
     }
 }
 template <typename R> __device__ __forceinline__ R kick_expm(R y) {
-    return abs_r(y) <= Series<R>::kExp ? Series<R>::expm(y) : expm_full(y);
+    return fabs(y) <= Series<R>::kExp ? Series<R>::expm(y) : expm_full(y);
 }
 
 // Per-site kick state of one x line.  Imaginary time: exp(-dt V) is the
