@@ -41,6 +41,8 @@
 // threads) whose last block writes the next renormalisation factor.
 #pragma once
 
+#include <type_traits>
+
 #include "gp_internal.h"
 
 namespace gpcn {
@@ -164,10 +166,15 @@ template <> struct Acc<float> {
 // component-wise float2 registers.
 template <typename V_> struct LineForm {
     static constexpr bool kPair = false;
+    static constexpr bool kChunkKick = false;  // kick_chunk: a chunk of nodes kicked at once
     using MemV = V_;
     __device__ __forceinline__ static V_ load(MemV m) { return m; }
     __device__ __forceinline__ static MemV store(V_ v) { return v; }
 };
+
+// Chunk kicks work in groups of at most kKickGroup nodes (bounds the
+// registers the group's phases and scaled values hold).
+constexpr int kKickGroup = 8;
 
 // Imaginary time, real field: c = kappa, coefficients real.
 template <typename R> struct FImagReal : LineForm<R> {
@@ -187,6 +194,32 @@ template <typename R> struct FImagReal : LineForm<R> {
     __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
         const V q = p * k.s;
         return q * (__ldg(k.ex + node) * k.eyz * kick_expm(k.dtg * (q * q)));
+    }
+    // kick of NB consecutive nodes from node0: table loads issued together,
+    // one series-range test per group, values equal kick's
+    static constexpr bool kChunkKick = true;
+    template <int NB> __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<R> &k, int node0) {
+#pragma unroll
+        for (int g0 = 0; g0 < NB; g0 += kKickGroup) {
+            constexpr int G = NB < kKickGroup ? NB : kKickGroup;
+            R ex[G], q[G], y[G];
+            bool small = true;
+#pragma unroll
+            for (int i = 0; i < G; ++i) ex[i] = __ldg(k.ex + node0 + g0 + i);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                q[i] = v[g0 + i] * k.s;
+                y[i] = k.dtg * (q[i] * q[i]);
+                small = small && fabs(y[i]) <= Series<R>::kExp;
+            }
+            if (small) {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = q[i] * (ex[i] * k.eyz * Series<R>::expm(y[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick(v[g0 + i], k, node0 + g0 + i);
+            }
+        }
     }
 };
 
@@ -212,6 +245,34 @@ template <typename R> struct FImagCplx : LineForm<cx<R>> {
         const V q{p.re * k.s, p.im * k.s};
         const R f = __ldg(k.ex + node) * k.eyz * kick_expm(k.dtg * abs2(q));
         return V{q.re * f, q.im * f};
+    }
+    static constexpr bool kChunkKick = true;
+    template <int NB> __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<R> &k, int node0) {
+#pragma unroll
+        for (int g0 = 0; g0 < NB; g0 += kKickGroup) {
+            constexpr int G = NB < kKickGroup ? NB : kKickGroup;
+            R ex[G], y[G];
+            V q[G];
+            bool small = true;
+#pragma unroll
+            for (int i = 0; i < G; ++i) ex[i] = __ldg(k.ex + node0 + g0 + i);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                q[i] = V{v[g0 + i].re * k.s, v[g0 + i].im * k.s};
+                y[i] = k.dtg * abs2(q[i]);
+                small = small && fabs(y[i]) <= Series<R>::kExp;
+            }
+            if (small) {
+#pragma unroll
+                for (int i = 0; i < G; ++i) {
+                    const R f = ex[i] * k.eyz * Series<R>::expm(y[i]);
+                    v[g0 + i] = V{q[i].re * f, q[i].im * f};
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick(v[g0 + i], k, node0 + g0 + i);
+            }
+        }
     }
 };
 
@@ -248,6 +309,35 @@ template <typename R> struct FRealTime : LineForm<cx<R>> {
         // exp(-i theta) q
         return V{fma(cs, q.re, sn * q.im), fma(cs, q.im, -sn * q.re)};
     }
+    static constexpr bool kChunkKick = true;
+    template <int NB> __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<R> &k, int node0) {
+#pragma unroll
+        for (int g0 = 0; g0 < NB; g0 += kKickGroup) {
+            constexpr int G = NB < kKickGroup ? NB : kKickGroup;
+            R px[G], th[G];
+            V q[G];
+            bool small = true;
+#pragma unroll
+            for (int i = 0; i < G; ++i) px[i] = __ldg(k.px + node0 + g0 + i);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                q[i] = V{v[g0 + i].re * k.s, v[g0 + i].im * k.s};
+                th[i] = fma(k.dtg, abs2(q[i]), px[i] + k.pyz);
+                small = small && fabs(th[i]) <= Series<R>::kTrig;
+            }
+            if (small) {
+#pragma unroll
+                for (int i = 0; i < G; ++i) {
+                    R sn, cs;
+                    Series<R>::sincos(th[i], &sn, &cs);
+                    v[g0 + i] = V{fma(cs, q[i].re, sn * q[i].im), fma(cs, q[i].im, -sn * q[i].re)};
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick(v[g0 + i], k, node0 + g0 + i);
+            }
+        }
+    }
 };
 
 // Two adjacent lines advanced together by one thread: every operation is
@@ -275,6 +365,21 @@ template <class F> struct FPair {
     __device__ __forceinline__ static Real abs2(V v) { return F::abs2(v.a) + F::abs2(v.b); }
     __device__ __forceinline__ static V kick2(V v, const KickState<Real> &ka, const KickState<Real> &kb, int node) {
         return V{F::kick(v.a, ka, node), F::kick(v.b, kb, node)};
+    }
+    static constexpr bool kChunkKick = F::kChunkKick;
+    template <int NB>
+    __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<Real> &ka,
+                                                      const KickState<Real> &kb, int node0) {
+        E a[NB], b[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            a[q] = v[q].a;
+            b[q] = v[q].b;
+        }
+        F::template kick_chunk<NB>(a, ka, node0);
+        F::template kick_chunk<NB>(b, kb, node0);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q] = V{a[q], b[q]};
     }
 };
 
@@ -326,23 +431,61 @@ struct PRealTimeF {
         return s.x + s.y;
     }
     // Kick of both lines: shared scale, dt g and x table; per-line dt (V_y + V_z).
+    // The scaled values q and the phase theta = dt V_x + dt (V_y + V_z) + dt g |q|^2.
+    __device__ __forceinline__ static float2 kick_phase(V p, const KickState<float> &ka, const KickState<float> &kb,
+                                                        float px, float2 &qre, float2 &qim) {
+        const float2 s = dup2(ka.s);
+        qre = mul2(p.re, s);
+        qim = mul2(p.im, s);
+        const float2 a2 = fma2(qre, qre, mul2(qim, qim));
+        const float2 base = add2(dup2(px), make_float2(ka.pyz, kb.pyz));
+        return fma2(dup2(ka.dtg), a2, base);
+    }
+    __device__ __forceinline__ static bool kick_small(float2 th) {
+        return fabsf(th.x) <= Series<float>::kTrig && fabsf(th.y) <= Series<float>::kTrig;
+    }
+    // exp(-i theta) q, theta within the series range.
+    __device__ __forceinline__ static V kick_series(float2 th, float2 qre, float2 qim) {
+        const float2 x2 = mul2(th, th);
+        const float2 sn = mul2(th, fma2(x2, fma2(x2, dup2(1.f / 120.f), dup2(-1.f / 6.f)), dup2(1.f)));
+        const float2 cs = fma2(x2, fma2(x2, fma2(x2, dup2(-1.f / 720.f), dup2(1.f / 24.f)), dup2(-0.5f)), dup2(1.f));
+        return V{fma2(cs, qre, mul2(sn, qim)), fma2(cs, qim, mul2(make_float2(-sn.x, -sn.y), qre))};
+    }
     __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
                                               int node) {
-        const float2 s = dup2(ka.s);
-        const float2 qre = mul2(p.re, s), qim = mul2(p.im, s);
-        const float2 a2 = fma2(qre, qre, mul2(qim, qim));
-        const float2 base = add2(dup2(__ldg(ka.px + node)), make_float2(ka.pyz, kb.pyz));
-        const float2 th = fma2(dup2(ka.dtg), a2, base);
+        float2 qre, qim;
+        const float2 th = kick_phase(p, ka, kb, __ldg(ka.px + node), qre, qim);
+        if (kick_small(th)) return kick_series(th, qre, qim);
         float2 sn, cs;
-        if (fabsf(th.x) <= Series<float>::kTrig && fabsf(th.y) <= Series<float>::kTrig) {
-            const float2 x2 = mul2(th, th);
-            sn = mul2(th, fma2(x2, fma2(x2, dup2(1.f / 120.f), dup2(-1.f / 6.f)), dup2(1.f)));
-            cs = fma2(x2, fma2(x2, fma2(x2, dup2(-1.f / 720.f), dup2(1.f / 24.f)), dup2(-0.5f)), dup2(1.f));
-        } else {
-            kick_sincos(th.x, &sn.x, &cs.x);
-            kick_sincos(th.y, &sn.y, &cs.y);
-        }
+        kick_sincos(th.x, &sn.x, &cs.x);
+        kick_sincos(th.y, &sn.y, &cs.y);
         return V{fma2(cs, qre, mul2(sn, qim)), fma2(cs, qim, mul2(make_float2(-sn.x, -sn.y), qre))};
+    }
+    // Kick of NB consecutive nodes (node0 ...): the x-table loads are issued
+    // together and one test per chunk selects the series for all of them;
+    // a chunk with any phase outside the series range takes kick2 node by
+    // node.  Either way every value equals kick2's.
+    static constexpr bool kChunkKick = true;
+    template <int NB>
+    __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<float> &ka,
+                                                      const KickState<float> &kb, int node0) {
+        float px[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) px[q] = __ldg(ka.px + node0 + q);
+        float2 th[NB], qre[NB], qim[NB];
+        bool small = true;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            th[q] = kick_phase(v[q], ka, kb, px[q], qre[q], qim[q]);
+            small = small && kick_small(th[q]);
+        }
+        if (small) {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) v[q] = kick_series(th[q], qre[q], qim[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) v[q] = kick2(v[q], ka, kb, node0 + q);
+        }
     }
 };
 
@@ -454,13 +597,15 @@ __device__ __forceinline__ void window_chunk(int t0, typename F::V (&D)[B + W], 
                                              typename F::C ips, IO &io) {
     using V = typename F::V;
     io.need(t0 + W + 2 + B);
+    V in[B];  // the chunk's inputs, positions t0+W+2 .. t0+W+B+1 (kicked as one chunk on the x sweep)
+    io.vals(t0 + W + 2, in);
 #pragma unroll
     for (int q = 0; q < B; ++q) {
         dprev = F::fwd(F::rhs(pm, p0, p1, kap), dprev, kap, SETTLED ? ips : ldc(ipm1 + t0 + W + q));
         D[W + q] = dprev;
         pm = p0;
         p0 = p1;
-        p1 = io.val(t0 + W + 2 + q);
+        p1 = in[q];
     }
     V phi = D[B + W - 1];
 #pragma unroll
@@ -602,6 +747,19 @@ template <class F, class M, typename R, int KIND> struct Hooks {
         }
         return v;
     }
+    // on_load of NB consecutive positions p .. p+NB-1.
+    template <int NB> __device__ __forceinline__ void on_load_chunk(int p, V (&v)[NB]) const {
+        if constexpr (KIND == K_X) {
+            if constexpr (M::kChunkKick && M::kPair) {
+                M::template kick_chunk<NB>(v, ka, kb, p + 1);
+            } else if constexpr (M::kChunkKick) {
+                M::template kick_chunk<NB>(v, ka, p + 1);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NB; ++q) v[q] = on_load(p + q, v[q]);
+            }
+        }
+    }
     __device__ __forceinline__ void on_store(V v) const {
         if (KIND == K_Z) acc->add(M::abs2(v));
     }
@@ -670,6 +828,11 @@ template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
     }
     __device__ __forceinline__ V val(int p) const {
         return hk.on_load(p, M::load(ring[((p - s0) & (RL - 1)) * T]));
+    }
+    template <int NB> __device__ __forceinline__ void vals(int p, V (&v)[NB]) const {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q] = M::load(ring[((p + q - s0) & (RL - 1)) * T]);
+        hk.on_load_chunk(p, v);
     }
     __device__ __forceinline__ void put(int t0, int q, V v) const {
         out[(long long)(t0 + q + 1) * st] = M::store(v);
@@ -810,6 +973,10 @@ template <class F, typename R, int B, int W> struct TileIO {
         while (issued <= c + kRingChunks - 2 && s0 + issued * B < limit) issue();
     }
     __device__ __forceinline__ V val(int p) const { return ring[lane * RS + ((p - s0) & (RL - 1))]; }
+    template <int NB> __device__ __forceinline__ void vals(int p, V (&v)[NB]) const {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q] = val(p + q);
+    }
     __device__ __forceinline__ void put(int, int q, V v) {
         otile[lane * OS + q] = v;
         csum += F::abs2(v);
