@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 D = (0.29, 0.26, 0.23)
 OMEGA = (1.0, 1.3, 1.8)
 # (nx, ny, nz): nz a multiple of 4 so that both 4- and 8-byte elements qualify;
-# nx * ny not a multiple of 128 rows (a ragged last warp); nz - 2 spanning
+# nx * ny not a multiple of 256 rows (a ragged last block, idle and ragged warps); nz - 2 spanning
 # several chunks with a ragged tail, or exactly the shortest admissible line.
 SHAPES = [(23, 17, 48), (19, 13, 100), (11, 9, 16), (7, 5, 28), (5, 3, 44)]
 

@@ -174,16 +174,30 @@ def model(psi, c, W, B, ahead=2):
     return np.array([out[i] for i in range(N)])
 
 
+def kernel_ahead():
+    """kTmaAhead as the kernel header defines it."""
+    import os
+    import re
+    hdr = os.path.join(os.path.dirname(__file__), "..", "paper_1601_04641_gb300", "csrc", "gp_sweep_tma.cuh")
+    with open(hdr) as f:
+        return int(re.search(r"constexpr int kTmaAhead = (\d+);", f.read()).group(1))
+
+
+def test_kernel_ring_depth_is_modelled():
+    assert kernel_ahead() in (1, 2, 3, 4)
+
+
+@pytest.mark.parametrize("ahead", [1, 2, 3, 4])
 @pytest.mark.parametrize("B", [8, 16])
 @pytest.mark.parametrize("W", [4, 8, 16])
-def test_tma_schedule_model(B, W):
+def test_tma_schedule_model(B, W, ahead):
     rng = np.random.default_rng(B * 100 + W)
     step = 2 if B == 8 else 4                # rows must start on 16-byte boundaries
     for N in range(B + W + 4 + (-(B + W + 4)) % step, B + W + 4 + 4 * B + 2, step):
         psi = rng.standard_normal(N) + 1j * rng.standard_normal(N)
         psi[0], psi[-1] = 7.0, -5.0          # must not enter the solution
         for c in (0.05j, 0.3, 0.02 + 0j):
-            got = model(psi, c, W, B)
+            got = model(psi, c, W, B, ahead)
             ref = dense(psi, c)
             cpmax = np.abs(thomas(c, N)[0]).max()
             assert np.max(np.abs(got - ref)) <= (4 * cpmax ** (W + 1) + 1e-12) * np.max(np.abs(ref)), (B, W, N, c)
