@@ -39,6 +39,8 @@ WORKLOADS = {
     "real_large_half": (inputs.real_large_half, "f32", "complex", True),
     "real_medium": (inputs.real_medium, "f64", "complex", True),
     "imag_small": (inputs.imag_small, "f64", "real", False),
+    "imag_large_real": (inputs.imag_large, "f32", "real", False),
+    "imag_large_cplx": (inputs.imag_large, "f32", "complex", False),
 }
 
 # DRAM bytes (read + write) per launch from `ncu` of each kernel, with the
@@ -590,9 +592,20 @@ def run_ours(args):
                 r2 = time_workload(torch, name, args.also_steps, 3, local)
                 el2 = timed_region(torch, r2, args.also_steps, None)
                 kb2 = kernel_breakdown(torch, r2, min(args.also_steps, 50))
-                also[name] = {"value": r2["problem"].sites * args.also_steps / el2,
+                p2 = r2["problem"]
+                elem2 = (8 if r2["prec"] == "f32" else 16) // (2 if r2["field"] == "real" else 1)
+                bytes2 = 2 * elem2 * p2.sites  # algorithmic bytes per sweep launch
+                also[name] = {"workload": p2.name, "grid": list(p2.shape),
+                              "psi": {(4, "real"): "float32", (8, "real"): "float64",
+                                      (8, "complex"): "complex64",
+                                      (16, "complex"): "complex128"}[(elem2, r2["field"])],
+                              "time": "real" if r2["realtime"] else "imaginary",
+                              "value": p2.sites * args.also_steps / el2,
                               "ms_per_step": 1e3 * el2 / args.also_steps, "dtype": r2["prec"],
-                              "kernel_ms": {k: 1e3 * v for k, v in kb2.items()}}
+                              "kernel_ms": {k: 1e3 * v for k, v in kb2.items()},
+                              "kernel_hbm_frac": {k: bytes2 / v / 1e9 / peak for k, v in kb2.items()}}
+                o2 = r2["gp"].observables()
+                also[name]["mu"] = o2["mu"]
                 r2["gp"].close()
         line["also"] = also
     if args.strang and world == 1:
@@ -619,7 +632,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="real_large")
-    ap.add_argument("--also", default="real_medium",
+    ap.add_argument("--also", default="real_medium,imag_large_real,imag_large_cplx",
                     help="comma-separated secondary workloads timed after the main one")
     ap.add_argument("--also-steps", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

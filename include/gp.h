@@ -67,8 +67,9 @@ typedef enum {
     GP_ERR_NOMEM = 3,     /* a device or host allocation failed */
     GP_ERR_NONFINITE = 4, /* psi holds NaN or Inf at an observables check */
     GP_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
-    GP_ERR_STATE = 6      /* call not valid in the handle's state (e.g. real
+    GP_ERR_STATE = 6,     /* call not valid in the handle's state (e.g. real
                              time on a GP_REAL field) */
+    GP_ERR_IO = 7         /* a file could not be opened or written */
 } gp_status;
 
 typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_precision; /* element precision of psi;
@@ -279,6 +280,37 @@ gp_status gp_set_graph_block(gp_handle h, int steps);
  * symmetric splitting is applied first (queued on the stream).  Valid until
  * the next call that queues work on the handle. */
 gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale);
+
+/* Density output.  The paper's programs write the condensate wavefunction
+ * to files ("Special features": each MPI process writes its part, and the
+ * parts concatenated give the whole wavefunction); on one GPU the whole
+ * wavefunction is one array, and these two calls give it and its integrated
+ * densities.
+ *
+ * Integrated 1D densities of the current psi:
+ *   rho_x[i] = dy dz sum_{j,k} |psi_ijk|^2   (nx values)
+ *   rho_y[j] = dx dz sum_{i,k} |psi_ijk|^2   (ny values)
+ *   rho_z[k] = dx dy sum_{i,j} |psi_ijk|^2   (nz values)
+ * so that sum_i rho_x[i] dx is the norm (gp_obs.norm).  A pending
+ * renormalisation factor s enters as s^2; a pending half kick of the
+ * symmetric splitting is a phase and does not change |psi|^2.  Host arrays,
+ * caller-owned; any of them may be NULL (not computed).  Computed on the
+ * GPU in FP64 with every sum in a fixed order (deterministic), using
+ * (nx ny + nx nz + nx + ny + nz) doubles of device scratch allocated for the
+ * call (GP_ERR_NOMEM if that fails); synchronises the handle's stream. */
+gp_status gp_density_profiles(gp_handle h, double *rho_x, double *rho_y, double *rho_z);
+
+typedef enum { GP_OUT_PSI = 0, GP_OUT_DENSITY = 1 } gp_output;
+
+/* Write the current psi (GP_OUT_PSI: the element type of the handle) or its
+ * density |psi|^2 (GP_OUT_DENSITY: float or double, computed in FP64 from
+ * the stored values and rounded once to the handle's precision) to `path` as
+ * a NumPy .npy file (format version 1.0, little-endian, C order, shape
+ * (nx, ny, nz): the layout above).  Pending factors are applied as by
+ * gp_get_psi.  Needs one host buffer of the array's size (GP_ERR_NOMEM if it
+ * cannot be allocated); GP_ERR_IO if the file cannot be opened or fully
+ * written (a partly written file is removed); synchronises the stream. */
+gp_status gp_write_wavefunction(gp_handle h, const char *path, int what);
 
 /* Observables of a caller-owned device psi, computed without allocating any
  * device memory.  No counterpart in the paper: it serves callers that cannot

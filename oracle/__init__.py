@@ -236,3 +236,15 @@ def run_imag_until(psi, d, dt, omega, g, mu_tol, check_every=10, max_steps=10000
             return steps, mu
         mu_prev = mu
     return steps, mu_prev
+
+
+def density_profiles(psi, d):
+    """Integrated 1D densities of a field (the programs' density output):
+    rho_x[i] = dy dz sum_{j,k} |psi_ijk|^2, rho_y[j] = dx dz sum_{i,k}
+    |psi_ijk|^2, rho_z[k] = dx dy sum_{i,j} |psi_ijk|^2 -- |psi|^2 summed over
+    the other two axes times their spacings, so that sum_i rho_x[i] dx is the
+    norm.  Plain numpy sums in FP64 (the definition itself)."""
+    psi = np.asarray(psi)
+    rho = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+    return (rho.sum(axis=(1, 2)) * d[1] * d[2], rho.sum(axis=(0, 2)) * d[0] * d[2],
+            rho.sum(axis=(0, 1)) * d[0] * d[1])

@@ -12,9 +12,10 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgpcn.so")
 
-GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_NOMEM, GP_ERR_NONFINITE, GP_ERR_TIMEOUT, GP_ERR_STATE = range(7)
+GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_NOMEM, GP_ERR_NONFINITE, GP_ERR_TIMEOUT, GP_ERR_STATE, GP_ERR_IO = range(8)
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_CUDA", 3: "GP_ERR_NOMEM",
-                4: "GP_ERR_NONFINITE", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_STATE"}
+                4: "GP_ERR_NONFINITE", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_STATE", 7: "GP_ERR_IO"}
+GP_OUT_PSI, GP_OUT_DENSITY = 0, 1
 GP_F64, GP_F32 = 0, 1
 GP_COMPLEX, GP_REAL = 0, 1
 
@@ -73,6 +74,8 @@ SIGNATURES = {
     "gp_autotune": (_i, [Handle, _i, _i, ctypes.c_char_p]),
     "gp_set_graph_block": (_i, [Handle, _i]),
     "gp_psi_device_ptr": (_i, [Handle, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
+    "gp_density_profiles": (_i, [Handle, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    "gp_write_wavefunction": (_i, [Handle, ctypes.c_char_p, _i]),
     "gp_observables_noalloc": (_i, [_vp, Grid, _i, _i, _d, _d, _d, _d, _d, _vp, _vp]),
     "gp_batch_create": (_i, [ctypes.POINTER(Handle), _i, ctypes.POINTER(Grid), ctypes.POINTER(_d),
                              ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),

@@ -64,6 +64,16 @@ def real_large_half() -> Problem:
                    name="real 480x400x160 complex64 (half-depth profiling case)", meta=dict(p.meta))
 
 
+def imag_large() -> Problem:
+    """The 480x400x320 grid of the real-time workload (d = 0.05, trap
+    (0.5, 1, 1.5)) in imaginary time at g = 20, dt = 0.1 d^2: the precision
+    variants of the imaginary-time path (FP32 real field against FP32
+    complex) on an HBM-sized grid."""
+    p = real_large()
+    return Problem(p.shape, p.d, 0.1 * p.d[0] ** 2, p.omega, 20.0,
+                   name="imag 480x400x320, g 20, dt 0.1 d^2", meta={})
+
+
 def sized_box(shape, omega, g, dt_factor=0.1) -> Problem:
     """Grid spacing that holds both the g = 0 Gaussian (6 oscillator lengths)
     and 1.3x the Thomas-Fermi radius in the half-box, per axis."""

@@ -6,6 +6,7 @@ the method runs in the library's CUDA kernels through the C ABI.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -126,6 +127,21 @@ class GP:
         self._ck(self.lib.gp_observables(self.h, ctypes.byref(o)))
         return {"norm": o.norm, "mu": o.mu, "energy": o.energy, "rms_x": o.rms_x,
                 "rms_y": o.rms_y, "rms_z": o.rms_z, "step": o.step, "t": o.t}
+
+    def density_profiles(self):
+        """Integrated 1D densities (rho_x, rho_y, rho_z) of the current psi,
+        each summed over the other two axes times their spacings."""
+        nx, ny, nz = self.shape
+        rx, ry, rz = np.empty(nx), np.empty(ny), np.empty(nz)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._ck(self.lib.gp_density_profiles(self.h, rx.ctypes.data_as(dp), ry.ctypes.data_as(dp),
+                                              rz.ctypes.data_as(dp)))
+        return rx, ry, rz
+
+    def write_wavefunction(self, path, density=False):
+        """Write psi (or |psi|^2) to `path` as a .npy file of shape (nx, ny, nz)."""
+        self._ck(self.lib.gp_write_wavefunction(self.h, os.fsencode(path),
+                                                N.GP_OUT_DENSITY if density else N.GP_OUT_PSI))
 
     def set_tracking(self, every, capacity=1024):
         """Queue the observables every `every` steps on the device (no host sync)."""
