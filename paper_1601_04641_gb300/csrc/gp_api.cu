@@ -5,6 +5,7 @@
 #include "gp_host.h"
 #include "gp_internal.h"
 #include "gp_nn_internal.h"
+#include "gp_output.h"
 
 #include <algorithm>
 #include <cstdio>

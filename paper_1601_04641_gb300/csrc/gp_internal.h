@@ -105,13 +105,6 @@ cudaError_t launch_apply_scale(Prec p, bool cplx, const FieldArgs &a, void *dst,
 // Real-time kick exp(-i kdt (V + g |psi|^2)) of a complex field into dst.
 cudaError_t launch_kick(Prec p, const FieldArgs &a, double kdt, void *dst, cudaStream_t s);
 
-// Integrated density profiles rho_x, rho_y, rho_z of a.psi (times the square
-// of *a.scale) into out[0 .. nx+ny+nz): x nodes, then y, then z.  scratch
-// holds profile_scratch_doubles(a) doubles of device memory.
-size_t profile_scratch_doubles(const FieldArgs &a);
-cudaError_t launch_density_profiles(Prec p, bool cplx, const FieldArgs &a, double *scratch, double *out,
-                                    cudaStream_t s);
-
 // Observables output layout in FieldArgs::out.
 enum ObsSlot {
     O_RHO = 0, O_V, O_RHO2, O_X2, O_Y2, O_Z2, O_LX, O_LY, O_LZ,   // raw sums

@@ -5,7 +5,7 @@
 //
 // s the pending renormalisation factor, so that sum_i rho_x(i) dx is the norm.
 // Deterministic: every sum runs in a fixed order, in FP64.
-#include "gp_internal.h"
+#include "gp_output.h"
 
 namespace gpcn {
 
