@@ -49,9 +49,9 @@ WORKLOADS = {
 NCU_TRAFFIC = {
     # ncu --set full of the 480x400x160 half-depth case (profiles/), scaled x2
     # by sites to a full 480x400x320 launch: (read + write) bytes per launch
-    ("real_large", "zsweep_norm"): (2 * (246.239488e6 + 200.524544e6), "75f71ac2387ec6ff"),
-    ("real_large", "kick_xsweep"): (2 * (257.194240e6 + 193.633280e6), "75f71ac2387ec6ff"),
-    ("real_large", "ysweep"): (2 * (251.146240e6 + 193.761792e6), "75f71ac2387ec6ff"),
+    ("real_large", "zsweep_norm"): (2 * (246.239488e6 + 200.524544e6), "3f7ebbb422de0aa4"),
+    ("real_large", "kick_xsweep"): (2 * (257.194240e6 + 193.633280e6), "3f7ebbb422de0aa4"),
+    ("real_large", "ysweep"): (2 * (251.146240e6 + 193.761792e6), "3f7ebbb422de0aa4"),
 }
 
 

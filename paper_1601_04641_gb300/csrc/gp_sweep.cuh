@@ -489,9 +489,165 @@ struct PRealTimeF {
     }
 };
 
+// exp(-y) by the FP32 series of Series<float>::expm, on two lines at once.
+__device__ __forceinline__ float2 expm_series2(float2 y) {
+    return fma2(y, fma2(y, fma2(y, fma2(y, dup2(1.f / 24.f), dup2(-1.f / 6.f)), dup2(0.5f)), dup2(-1.f)), dup2(1.f));
+}
+
+// Packed FP32 pairs of the imaginary-time forms, in the same operation order
+// as FImagReal<float> / FImagCplx<float> (results equal the scalar forms').
+struct PImagRealF {
+    using Real = float;
+    using F = FImagReal<float>;
+    using C = float;
+    using V = float2;                     // (line a, line b)
+    using MemV = typename FPair<F>::V;
+    static constexpr bool kPair = true;
+    __device__ __forceinline__ static V load(MemV m) { return make_float2(m.a, m.b); }
+    __device__ __forceinline__ static MemV store(V v) { return MemV{v.x, v.y}; }
+    __device__ __forceinline__ static V zero() { return dup2(0.f); }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, float k) {
+        return fma2(dup2(k), fma2(dup2(-2.f), p0, add2(pm, p1)), p0);
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, float k, C ipm1) {
+        const float2 u = fma2(dup2(k), dprev, r);
+        return fma2(u, dup2(ipm1), u);
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) { return fma2(dup2(-cp), phi, dp); }
+    __device__ __forceinline__ static float abs2(V v) {
+        const float2 s = mul2(v, v);
+        return s.x + s.y;
+    }
+    // q, y = dt g q^2 of both lines
+    __device__ __forceinline__ static float2 kick_arg(V p, const KickState<float> &ka, float2 &q) {
+        q = mul2(p, dup2(ka.s));
+        return mul2(dup2(ka.dtg), mul2(q, q));
+    }
+    __device__ __forceinline__ static bool kick_small(float2 y) {
+        return fabs(y.x) <= Series<float>::kExp && fabs(y.y) <= Series<float>::kExp;
+    }
+    __device__ __forceinline__ static V kick_apply(float2 q, float ex, const KickState<float> &ka,
+                                                   const KickState<float> &kb, float2 e) {
+        return mul2(q, mul2(mul2(dup2(ex), make_float2(ka.eyz, kb.eyz)), e));
+    }
+    __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
+                                              int node) {
+        float2 q;
+        const float2 y = kick_arg(p, ka, q);
+        const float ex = __ldg(ka.ex + node);
+        if (kick_small(y)) return kick_apply(q, ex, ka, kb, expm_series2(y));
+        return kick_apply(q, ex, ka, kb, make_float2(kick_expm(y.x), kick_expm(y.y)));
+    }
+    static constexpr bool kChunkKick = true;
+    template <int NB>
+    __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<float> &ka,
+                                                      const KickState<float> &kb, int node0) {
+#pragma unroll
+        for (int g0 = 0; g0 < NB; g0 += kKickGroup) {
+            constexpr int G = NB < kKickGroup ? NB : kKickGroup;
+            float ex[G];
+            float2 q[G], y[G];
+            bool small = true;
+#pragma unroll
+            for (int i = 0; i < G; ++i) ex[i] = __ldg(ka.ex + node0 + g0 + i);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                y[i] = kick_arg(v[g0 + i], ka, q[i]);
+                small = small && kick_small(y[i]);
+            }
+            if (small) {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick_apply(q[i], ex[i], ka, kb, expm_series2(y[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick2(v[g0 + i], ka, kb, node0 + g0 + i);
+            }
+        }
+    }
+};
+
+struct PImagCplxF {
+    using Real = float;
+    using F = FImagCplx<float>;
+    using C = float;
+    struct __align__(16) V { float2 re, im; };  // (line a, line b) per component
+    using MemV = typename FPair<F>::V;
+    static constexpr bool kPair = true;
+    __device__ __forceinline__ static V load(MemV m) {
+        return V{make_float2(m.a.re, m.b.re), make_float2(m.a.im, m.b.im)};
+    }
+    __device__ __forceinline__ static MemV store(V v) {
+        MemV m;
+        m.a = cx<float>{v.re.x, v.im.x};
+        m.b = cx<float>{v.re.y, v.im.y};
+        return m;
+    }
+    __device__ __forceinline__ static V zero() { return V{dup2(0.f), dup2(0.f)}; }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, float k) {
+        return V{PImagRealF::rhs(pm.re, p0.re, p1.re, k), PImagRealF::rhs(pm.im, p0.im, p1.im, k)};
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, float k, C ipm1) {
+        return V{PImagRealF::fwd(r.re, dprev.re, k, ipm1), PImagRealF::fwd(r.im, dprev.im, k, ipm1)};
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) {
+        return V{PImagRealF::back(dp.re, cp, phi.re), PImagRealF::back(dp.im, cp, phi.im)};
+    }
+    __device__ __forceinline__ static float abs2(V v) {
+        const float2 s = fma2(v.re, v.re, mul2(v.im, v.im));
+        return s.x + s.y;
+    }
+    __device__ __forceinline__ static float2 kick_arg(V p, const KickState<float> &ka, V &q) {
+        const float2 s = dup2(ka.s);
+        q = V{mul2(p.re, s), mul2(p.im, s)};
+        return mul2(dup2(ka.dtg), fma2(q.re, q.re, mul2(q.im, q.im)));
+    }
+    __device__ __forceinline__ static V kick_apply(V q, float ex, const KickState<float> &ka,
+                                                   const KickState<float> &kb, float2 e) {
+        const float2 f = mul2(mul2(dup2(ex), make_float2(ka.eyz, kb.eyz)), e);
+        return V{mul2(q.re, f), mul2(q.im, f)};
+    }
+    __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
+                                              int node) {
+        V q;
+        const float2 y = kick_arg(p, ka, q);
+        const float ex = __ldg(ka.ex + node);
+        if (PImagRealF::kick_small(y)) return kick_apply(q, ex, ka, kb, expm_series2(y));
+        return kick_apply(q, ex, ka, kb, make_float2(kick_expm(y.x), kick_expm(y.y)));
+    }
+    static constexpr bool kChunkKick = true;
+    template <int NB>
+    __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<float> &ka,
+                                                      const KickState<float> &kb, int node0) {
+#pragma unroll
+        for (int g0 = 0; g0 < NB; g0 += kKickGroup) {
+            constexpr int G = NB < kKickGroup ? NB : kKickGroup;
+            float ex[G];
+            V q[G];
+            float2 y[G];
+            bool small = true;
+#pragma unroll
+            for (int i = 0; i < G; ++i) ex[i] = __ldg(ka.ex + node0 + g0 + i);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                y[i] = kick_arg(v[g0 + i], ka, q[i]);
+                small = small && PImagRealF::kick_small(y[i]);
+            }
+            if (small) {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick_apply(q[i], ex[i], ka, kb, expm_series2(y[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick2(v[g0 + i], ka, kb, node0 + g0 + i);
+            }
+        }
+    }
+};
+
 // The paired form of a single-line form.
 template <class F> struct PairForm { using type = FPair<F>; };
 template <> struct PairForm<FRealTime<float>> { using type = PRealTimeF; };
+template <> struct PairForm<FImagReal<float>> { using type = PImagRealF; };
+template <> struct PairForm<FImagCplx<float>> { using type = PImagCplxF; };
 
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
