@@ -337,6 +337,38 @@ def e2e_region(torch, res, steps, dist):
     return el, nbytes / steps, (nbytes + obs_bytes) / steps
 
 
+def precision_vs_fp64(torch, dev, steps):
+    """Accuracy of the complex64 form on the benchmark workload: the same
+    500-step quench run in FP64 from the same (FP32-representable) start
+    state; errors of mu, E, rms and psi (relative L2) of the FP32 run.  At
+    61 M sites the C oracle would need most of an hour, so the reference is
+    the FP64 GPU path, which the tests hold to the oracle within 1e-12."""
+    from paper_1601_04641_gb300.solver import GP
+    p = inputs.real_large()
+    g64 = GP(p.shape, p.d, p.dt, p.omega, p.g, "f64", "complex", device=dev)
+    prepare(torch, g64, p, True)
+    start = g64.get_psi(as_numpy=False).to(torch.complex64)
+    g64.set_psi(start.to(torch.complex128))
+    g32 = GP(p.shape, p.d, p.dt, p.omega, p.g, "f32", "complex", device=dev)
+    g32.set_psi(start)
+    del start
+    g64.step_real(steps)
+    g32.step_real(steps)
+    o64, o32 = g64.observables(), g32.observables()
+    a = g64.get_psi(as_numpy=False)
+    b = g32.get_psi(as_numpy=False).to(torch.complex128)
+    rel_l2 = float(torch.linalg.vector_norm(b - a) / torch.linalg.vector_norm(a))
+    del a, b
+    g64.close()
+    g32.close()
+    torch.cuda.synchronize()
+    rel = lambda k: abs(o32[k] - o64[k]) / abs(o64[k])
+    return {"workload": p.name, "steps": steps, "reference": "FP64 GPU path from the same start state",
+            "mu_rel_err": rel("mu"), "energy_rel_err": rel("energy"),
+            "rms_rel_err": [rel("rms_x"), rel("rms_y"), rel("rms_z")], "norm_rel_err": rel("norm"),
+            "psi_rel_l2": rel_l2, "bounds": {"mu_rel": 1e-5, "psi_rel_l2": 1e-4}}
+
+
 def symmetric_splitting(torch, dev, steps, warmup):
     """Both splittings of the real-time step: first order (kick, sweeps; the
     main line) and symmetric (half kick, sweeps, half kick; records every
@@ -608,6 +640,8 @@ def run_ours(args):
                 also[name]["mu"] = o2["mu"]
                 r2["gp"].close()
         line["also"] = also
+    if args.precision and world == 1:
+        line["precision_vs_fp64"] = precision_vs_fp64(torch, local, 500)
     if args.strang and world == 1:
         line["symmetric_splitting"] = symmetric_splitting(torch, local, min(args.steps, 500), args.warmup)
     if args.gs and world == 1:
@@ -644,6 +678,8 @@ def main():
     ap.add_argument("--ws-steps", type=int, default=8000, help="Adam steps")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--strang", type=int, default=1, help="1: also time the symmetric splitting")
+    ap.add_argument("--precision", type=int, default=1,
+                    help="1: also measure the complex64 run's error against FP64 (500 steps)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

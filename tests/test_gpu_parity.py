@@ -404,3 +404,39 @@ def test_full_size_one_step_sampled(which):
     scale = np.max(np.abs(ref))
     err = np.max(np.abs(got[idx] - ref[idx])) / scale
     assert err <= (1e-12 if prec == "f64" else 1e-5), err
+
+
+def test_full_size_complex64_quench_accuracy():
+    """The benchmark workload's precision form (480x400x320, complex64 psi,
+    FP64 coefficients and reductions), 500 real-time steps of the quench,
+    against the FP64 path (held to the oracle within 1e-12 by the tests
+    above) from the same start state: |dmu|/mu <= 1e-5, relative L2 of psi
+    <= 1e-4."""
+    import torch
+    p = inputs.real_large()
+    g64 = make(p.shape, p.d, p.dt, p.omega, p.g, "f64", "complex")
+    g64.init_gaussian()
+    g64.set_g(p.meta["g_prepare"])
+    g64.set_dt(0.1 * p.d[0] ** 2)
+    g64.step_imag(100)
+    g64.set_g(p.g)
+    g64.set_dt(p.dt)
+    start = g64.get_psi(as_numpy=False).to(torch.complex64)
+    g64.set_psi(start.to(torch.complex128))
+    g32 = make(p.shape, p.d, p.dt, p.omega, p.g, "f32", "complex")
+    g32.set_psi(start)
+    del start
+    g64.step_real(500)
+    g32.step_real(500)
+    o64, o32 = g64.observables(), g32.observables()
+    a = g64.get_psi(as_numpy=False)
+    b = g32.get_psi(as_numpy=False).to(torch.complex128)
+    rel_l2 = float(torch.linalg.vector_norm(b - a) / torch.linalg.vector_norm(a))
+    del a, b
+    g64.close()
+    g32.close()
+    assert abs(o32["mu"] - o64["mu"]) <= 1e-5 * o64["mu"]
+    assert abs(o32["energy"] - o64["energy"]) <= 1e-5 * o64["energy"]
+    for k in ("rms_x", "rms_y", "rms_z"):
+        assert abs(o32[k] - o64[k]) <= 1e-5 * o64[k]
+    assert rel_l2 <= 1e-4
