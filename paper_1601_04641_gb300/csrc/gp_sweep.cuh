@@ -138,6 +138,7 @@ template <typename R> struct KickState {
     const R *ex;      // exp(-dt V_x(i)) per node (imaginary time)
     R pyz;            // dt (V_y + V_z) of the line (real time)
     const R *px;      // dt V_x(i) per node (real time)
+    R xo, xd, xc;     // x(i) = xo + i xd and dt V_x(i) = xc x(i)^2 (real time, computed in place)
 };
 
 // Per-thread sum: plain FP64, or FP32 with an error-free two-sum
@@ -451,27 +452,33 @@ struct PRealTimeF {
         const float2 cs = fma2(x2, fma2(x2, fma2(x2, dup2(-1.f / 720.f), dup2(1.f / 24.f)), dup2(-0.5f)), dup2(1.f));
         return V{fma2(cs, qre, mul2(sn, qim)), fma2(cs, qim, mul2(make_float2(-sn.x, -sn.y), qre))};
     }
+    // dt V_x at x node `node`, computed in registers: the same formula as the
+    // x phase table, in FP32 (about 1e-11 from the table's FP64-rounded value
+    // at the benchmark's dt), instead of a dependent table load per node.
+    __device__ __forceinline__ static float px_of(const KickState<float> &k, int node) {
+        const float x = fmaf((float)node, k.xd, k.xo);
+        return k.xc * (x * x);
+    }
     __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
                                               int node) {
         float2 qre, qim;
-        const float2 th = kick_phase(p, ka, kb, __ldg(ka.px + node), qre, qim);
+        const float2 th = kick_phase(p, ka, kb, px_of(ka, node), qre, qim);
         if (kick_small(th)) return kick_series(th, qre, qim);
         float2 sn, cs;
         kick_sincos(th.x, &sn.x, &cs.x);
         kick_sincos(th.y, &sn.y, &cs.y);
         return V{fma2(cs, qre, mul2(sn, qim)), fma2(cs, qim, mul2(make_float2(-sn.x, -sn.y), qre))};
     }
-    // Kick of NB consecutive nodes (node0 ...): the x-table loads are issued
-    // together and one test per chunk selects the series for all of them;
-    // a chunk with any phase outside the series range takes kick2 node by
-    // node.  Either way every value equals kick2's.
+    // Kick of NB consecutive nodes (node0 ...): one test per chunk selects
+    // the series for all of them; a chunk with any phase outside the series
+    // range takes kick2 node by node.  Either way every value equals kick2's.
     static constexpr bool kChunkKick = true;
     template <int NB>
     __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<float> &ka,
                                                       const KickState<float> &kb, int node0) {
         float px[NB];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) px[q] = __ldg(ka.px + node0 + q);
+        for (int q = 0; q < NB; ++q) px[q] = px_of(ka, node0 + q);
         float2 th[NB], qre[NB], qim[NB];
         bool small = true;
 #pragma unroll
@@ -883,6 +890,9 @@ template <typename R, int KIND> __device__ __forceinline__ void kick_init(KickSt
     k.px = static_cast<const R *>(a.phase_ex);
     k.pyz = a.phase_ex ? __ldg(static_cast<const R *>(a.phase_ey) + j) + __ldg(static_cast<const R *>(a.phase_ez) + kk)
                        : R(0);
+    k.xo = (R)a.origin[0];
+    k.xd = (R)a.d[0];
+    k.xc = (R)(a.dt * a.half_w2[0]);
 }
 
 // F is the single-line form; M is F (one line per thread) or its pair form.
