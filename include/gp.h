@@ -391,7 +391,8 @@ const char *gp_batch_last_error(gp_batch b);
  * A learned initial state for imaginary time (no counterpart in the paper,
  * which starts from a Gaussian): a conditioned coordinate MLP maps a grid
  * node x of a condensate with trap (gamma, nu, lambda) and nonlinearity g to
- * an amplitude.  Features: x_a sqrt(w_a)/4; min(sum (x_a/R_a)^2, 4)/2 - 1
+ * an amplitude.  Features: min(w_a x_a^2, 16)/8 - 1 per axis (even in x_a,
+ * so every prediction is even, as the ground state is); min(sum (x_a/R_a)^2, 4)/2 - 1
  * with the Thomas-Fermi radii R_a = sqrt(2 mu_TF)/w_a, mu_TF =
  * (15 g w_x w_y w_z / 4 pi)^(2/5)/2; min(sum w_a x_a^2, 16)/8 - 1;
  * (ln g - 3.1)/3.1; (w_a - 1.75)/1.25 (9 used, padded to 16).  Layers: three

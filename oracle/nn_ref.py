@@ -48,7 +48,7 @@ def features(shape, d, omega, g, sites):
     sq = np.zeros(sites.size)
     for a in range(3):
         u = x[a] * math.sqrt(w[a])
-        f[:, a] = 0.25 * u
+        f[:, a] = 0.125 * np.minimum(u * u, 16.0) - 1.0
         su += u * u
         sq += (x[a] / r[a]) ** 2
     f[:, 3] = 0.5 * np.minimum(sq, 4.0) - 1.0

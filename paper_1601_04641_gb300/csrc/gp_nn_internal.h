@@ -38,7 +38,9 @@ struct NNParams {
 };
 
 // One condensate as the network sees it.  Features of the node at x:
-//   f0..f2 = x_a sqrt(w_a) / 4                  (oscillator units)
+//   f0..f2 = min(w_a x_a^2, 16) / 8 - 1         (per axis, even in x_a: the
+//            ground state of the symmetric trap on the symmetric grid is
+//            even in x, y and z, and so is every prediction)
 //   f3     = min(sum (x_a / R_a)^2, 4) / 2 - 1  (Thomas-Fermi radii
 //            R_a = sqrt(2 mu_TF) / w_a, mu_TF = (15 g w_x w_y w_z / 4 pi)^(2/5) / 2)
 //   f4     = min(sum w_a x_a^2, 16) / 8 - 1

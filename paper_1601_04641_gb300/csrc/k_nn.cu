@@ -71,7 +71,7 @@ __device__ __forceinline__ void features(const NNInstance &I, long long site, fl
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float u = x[a] * I.sqrt_w[a];
-        f[a] = 0.25f * u;
+        f[a] = 0.125f * fminf(u * u, 16.f) - 1.f;  // even in x_a: so is every prediction
         su += u * u;
         const float q = x[a] * I.inv_rtf[a];
         sq += q * q;

@@ -42,7 +42,7 @@ def test_features_special_values():
     """Centre node of an odd grid: coordinates 0, so f0..f4 take their
     offsets; f5 and f6..f8 follow g and the trap."""
     f = nn_ref.features((5, 7, 9), (0.3, 0.2, 0.1), (1.0, 1.75, 3.0), math.exp(3.1), [2 * 63 + 3 * 9 + 4])
-    assert np.allclose(f[0, :5], [0, 0, 0, -1, -1])
+    assert np.allclose(f[0, :5], [-1, -1, -1, -1, -1])
     assert abs(f[0, 5]) < 1e-15
     assert np.allclose(f[0, 6:9], [-0.6, 0.0, 1.0])
     assert np.all(f[0, 9:] == 0)
@@ -53,4 +53,17 @@ def test_features_special_values():
     d = r / 50.0
     f = nn_ref.features((n, 3, 3), (d, 1, 1), w, g, [(100 + 50) * 9 + 1 * 3 + 1])
     assert abs(f[0, 3] + 0.5) < 1e-12
-    assert abs(f[0, 0] - 0.25 * r) < 1e-12
+    assert abs(f[0, 0] - (0.125 * min(r * r, 16.0) - 1.0)) < 1e-12
+
+
+def test_features_are_even_in_each_coordinate():
+    """Mirror nodes (i, j, k) and (n-1-i, n-1-j, n-1-k), and each single
+    reflection, have identical features: the network's output is even in x,
+    y and z, like the ground state of the symmetric trap on the symmetric grid."""
+    shape, d = (6, 7, 8), (0.3, 0.25, 0.2)
+    nx, ny, nz = shape
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    site = lambda a, b, c: (a * ny + b) * nz + c
+    f = nn_ref.features(shape, d, (1.2, 0.7, 2.1), 40.0, site(i, j, k).ravel())
+    for mi, mj, mk in ((nx - 1 - i, j, k), (i, ny - 1 - j, k), (i, j, nz - 1 - k), (nx - 1 - i, ny - 1 - j, nz - 1 - k)):
+        assert np.array_equal(f, nn_ref.features(shape, d, (1.2, 0.7, 2.1), 40.0, site(mi, mj, mk).ravel()))
