@@ -432,7 +432,7 @@ def time_to_ground_state(torch, dev, count, tol, max_steps=20000):
     b = Batch(probs, "f32", "complex", device=dev)
     b.set_stop_rule(1)  # after a dt switch mu need not approach monotonically
     b.init_gaussian()
-    steps_s = b.run_imag_schedule([(10.0, 100 * tol), (1.0, tol)], 10, max_steps)
+    steps_s = b.run_imag_schedule([(10.0, 100 * tol), (3.0, 10 * tol), (1.0, tol)], 10, max_steps)
     obs_s = b.observables()
     torch.cuda.synchronize()
     t_sched = time.perf_counter() - t0
@@ -470,7 +470,7 @@ def time_to_ground_state(torch, dev, count, tol, max_steps=20000):
             "mu_rel_diff_max": max(rel), "converged": sum(s < max_steps for s in steps_b),
             "mu_rel_err_vs_converged": {"plain_fp64": err(mu_p[:8]), "batched_fp32": err([o["mu"] for o in obs_b[:8]]),
                                         "schedule_fp32": err([o["mu"] for o in obs_s[:8]]), "instances": 8},
-            "schedule": {"levels": "10 dt to |dmu|, |dE| < %g, then dt to |dmu|, |dE| < %g" % (100 * tol, tol),
+            "schedule": {"levels": "10 dt to |dmu|, |dE| < %g, 3 dt to %g, then dt to %g" % (100 * tol, 10 * tol, tol),
                          "batched_fp32_s": t_sched, "speedup_vs_plain": t_plain / t_sched,
                          "steps": stats(steps_s), "mu_rel_diff_max": max(rel_s)}}
 
@@ -529,13 +529,13 @@ def schedule_from_starts(torch, dev, net, count, tol, max_steps=20000):
     """The 64-condensate workload, batched FP32, to |dmu| < tol and |dE| < tol
     (stop rule 1), from the Gaussian and from the network's prediction
     (energy fallback to the Gaussian per instance), each either through the
-    dt schedule (10 dt to 100 tol, then dt) or at dt alone; each run timed
+    dt schedule (10 dt to 100 tol, 3 dt to 10 tol, then dt) or at dt alone; each run timed
     from batch creation to convergence, prediction and fallback test
     included.  The schedule's coarse level draws every start to its own
     fixed point first, so a good start pays at dt alone."""
     from paper_1601_04641_gb300.solver import Batch
     probs = inputs.batch_problems(count, seed=0)
-    levels = [(10.0, 100 * tol), (1.0, tol)]
+    levels = [(10.0, 100 * tol), (3.0, 10 * tol), (1.0, tol)]
     runs = {}
     for start in ("gauss", "nn"):
         for method in ("schedule", "dt"):
@@ -587,7 +587,7 @@ def time_to_ground_state_sharded(torch, dev, count, tol, rank, world, dist, max_
     probs = inputs.batch_problems(count, seed=0)
     mine = [probs[i] for i in replicas.shard_by_sites([p.sites for p in probs], rank, world)]
     out = {}
-    for name, levels in (("batched_fp32_s", None), ("schedule_fp32_s", [(10.0, 100 * tol), (1.0, tol)])):
+    for name, levels in (("batched_fp32_s", None), ("schedule_fp32_s", [(10.0, 100 * tol), (3.0, 10 * tol), (1.0, tol)])):
         torch.cuda.synchronize()
         dist.barrier()
         t0 = time.perf_counter()
