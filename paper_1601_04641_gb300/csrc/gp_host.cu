@@ -85,9 +85,12 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
             AxisTables &at = T.ax[mode][ax];
             at.cp_max = 0.0;
             for (int t = 0; t < n - 1; ++t) at.cp_max = std::max(at.cp_max, std::abs(cp[t]));
+            // the smallest window whose truncation, at most cp_max^(W+1) of the
+            // line's largest value, stays within half the unit roundoff (below
+            // the rounding of a single operation)
             at.min_window = 0;
             for (int w : {4, 8, 16}) {
-                if (std::pow(at.cp_max, w + 1) <= eps / 8.0) {
+                if (std::pow(at.cp_max, w + 1) <= eps / 2.0) {
                     at.min_window = w;
                     break;
                 }
