@@ -218,7 +218,7 @@ gp_status gp_get_window(gp_handle h, int mode, int window[3]);
 /* Override the window of every axis and mode: -1 restores the automatic
  * choice, 0 forces the exact two-pass solve, 4 / 8 / 16 force that window
  * (GP_ERR_ARG if it is below the smallest window that keeps the truncation
- * under an eighth of the unit roundoff for this dt). */
+ * within half the unit roundoff for this dt). */
 gp_status gp_set_window(gp_handle h, int window);
 
 /* Window of one axis in both modes (-1 automatic, 0 exact, 4 / 8 / 16 if

@@ -29,8 +29,8 @@
 //    phi[t0 .. t0+B-1] is recovered by starting the backward recurrence at
 //    t0+B+W-1 with phi ~ dp (dropping cp * phi[t0+B+W]); the dropped term
 //    reaches phi[t0+B-1] through W+1 factors, i.e. |cp|_max^(W+1) max|phi|.
-// The host picks W so that |cp|_max^(W+1) is below an eighth of the unit
-// roundoff, or uses the exact two-pass form (window 0, one segment), which
+// The host picks W so that |cp|_max^(W+1) is within half the unit roundoff
+// (below the rounding of one operation), or uses the exact two-pass form (window 0, one segment), which
 // stages dp in the output and reads it back.  The last chunk of a line is
 // solved exactly from phi[n-1] = dp[n-1].
 //
@@ -431,8 +431,9 @@ struct PRealTimeF {
         const float2 s = fma2(v.re, v.re, mul2(v.im, v.im));
         return s.x + s.y;
     }
-    // Kick of both lines: shared scale, dt g and x table; per-line dt (V_y + V_z).
-    // The scaled values q and the phase theta = dt V_x + dt (V_y + V_z) + dt g |q|^2.
+    // Kick of both lines: shared scale, dt g and dt V_x (given as px);
+    // per-line dt (V_y + V_z).  The scaled values q and the phase
+    // theta = dt V_x + dt (V_y + V_z) + dt g |q|^2.
     __device__ __forceinline__ static float2 kick_phase(V p, const KickState<float> &ka, const KickState<float> &kb,
                                                         float px, float2 &qre, float2 &qim) {
         const float2 s = dup2(ka.s);
