@@ -99,21 +99,31 @@ static cudaError_t launch_kind(const SweepLaunch &L, const SweepArgs &a, cudaStr
 }
 
 // ---------------------------------------------------------------- batched
-template <class F, typename R, int W, int KIND>
-static cudaError_t launch_batch_lines_w(const BatchLaunch &b, cudaStream_t s) {
-    using V = typename F::V;
+template <class F, typename R, int W, int KIND, int LPT>
+static cudaError_t launch_batch_lines_wl(const BatchLaunch &b, cudaStream_t s) {
+    using V = typename LinesPerThread<F, LPT>::M::MemV;
     const unsigned threads = kBatchLineThreads;
     const size_t smem = W > 0 ? column_ring_bytes<V>(threads) : 0;
     static bool attr = false;
     if (!attr && smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(batch_lines_kernel<F, R, W, KIND, 1>,
+        cudaError_t e = cudaFuncSetAttribute(batch_lines_kernel<F, R, W, KIND, LPT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     BatchDesc d{b.args, b.first, b.gridx, b.n};
-    batch_lines_kernel<F, R, W, KIND, 1><<<b.total_blocks, threads, smem, s>>>(d);
+    batch_lines_kernel<F, R, W, KIND, LPT><<<b.total_blocks, threads, smem, s>>>(d);
     return cudaGetLastError();
+}
+
+// One line per thread, or adjacent line pairs (lpt 2; elements of 8 bytes or
+// less, windowed forms) for instances whose lines pair up in memory.
+template <class F, typename R, int W, int KIND>
+static cudaError_t launch_batch_lines_w(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    if constexpr (sizeof(typename F::V) <= 8 && W > 0) {
+        if (L.lpt == 2) return launch_batch_lines_wl<F, R, W, KIND, 2>(b, s);
+    }
+    return launch_batch_lines_wl<F, R, W, KIND, 1>(b, s);
 }
 
 template <class F, typename R, int W>
@@ -143,10 +153,10 @@ static cudaError_t launch_batch_kind(const SweepLaunch &L, const BatchLaunch &b,
         }
     }
     switch (L.window) {
-    case 0: return launch_batch_lines_w<F, R, 0, KIND>(b, s);
-    case 4: return launch_batch_lines_w<F, R, 4, KIND>(b, s);
-    case 8: return launch_batch_lines_w<F, R, 8, KIND>(b, s);
-    case 16: return launch_batch_lines_w<F, R, 16, KIND>(b, s);
+    case 0: return launch_batch_lines_w<F, R, 0, KIND>(L, b, s);
+    case 4: return launch_batch_lines_w<F, R, 4, KIND>(L, b, s);
+    case 8: return launch_batch_lines_w<F, R, 8, KIND>(L, b, s);
+    case 16: return launch_batch_lines_w<F, R, 16, KIND>(L, b, s);
     default: return cudaErrorInvalidValue;
     }
 }
