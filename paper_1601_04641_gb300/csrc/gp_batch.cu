@@ -154,13 +154,17 @@ void configure(gp_batch b, double scale, std::vector<char> &host) {
     b->contiguous_z = b->window[2] > 0;
     for (Inst &I : b->inst)
         for (int ax = 0; ax < 3; ++ax) {
-            // adjacent line pairs on a strided axis (windowed, 8-byte elements)
-            // when every pair is adjacent in memory: an even number of lines
-            // and, for y lines (i, k), an even nz.  Measured on the
-            // 64-condensate workload: complex64 0.312 -> 0.296 ms per step;
+            // adjacent line pairs on a strided axis (window 4, 8-byte
+            // elements) when every pair is adjacent in memory: an even number
+            // of lines and, for y lines (i, k), an even nz.  Measured on the
+            // 64-condensate workload: complex64 0.312 -> 0.298 ms per step;
             // FP32 real fields (8 bytes per pair node) 0.196 -> 0.208, as
-            // pairing halves the threads of these small grids -- not paired
-            const bool pair = ax < 2 && b->window[ax] > 0 && b->elem == 8 && axis_lines(I.G, ax) % 2 == 0 &&
+            // pairing halves the threads of these small grids.  A pair cuts
+            // lines into 8-node chunks, each re-running W back steps: at
+            // windows 8 and 16 (the coarse levels of a dt schedule) that
+            // overhead outweighs the packed arithmetic (schedule 0.451 ->
+            // 0.479 s with pairs at every window)
+            const bool pair = ax < 2 && b->window[ax] == 4 && b->elem == 8 && axis_lines(I.G, ax) % 2 == 0 &&
                               (ax != 1 || I.G.n[2] % 2 == 0);
             I.lpt[ax] = pair ? 2 : 1;
             choose_segments(I.G, ax, b->window[ax], I.lpt[ax], (int)b->elem, ax == 2 && b->contiguous_z, 0,

@@ -39,10 +39,11 @@ def test_batch_instances_equal_single_runs(prec, field):
     w = b.window()
     for i, p in enumerate(probs):
         gp = GP(p.shape, p.d, p.dt, p.omega, p.g, prec, field)
-        # adjacent line pairs under the batch's rule (8-byte elements, even
-        # line counts, even nz for y lines): the pair forms cut lines into
-        # 8-node chunks, so both must pair alike to agree bit for bit
-        gp.set_pair_lines(prec == "f32" and field == "complex")
+        # adjacent line pairs under the batch's rule (window 4, 8-byte
+        # elements, even line counts, even nz for y lines): the pair forms cut
+        # lines into 8-node chunks, so both must pair alike to agree bit for bit
+        assert w[0] == w[1]
+        gp.set_pair_lines(prec == "f32" and field == "complex" and w[0] == 4)
         gp.set_tma(False)  # the batched z sweep uses per-thread copies (same norm order)
         seg, _ = b.segments(i)
         for ax in range(3):
