@@ -343,9 +343,11 @@ gp_status gp_observables_noalloc(const void *dev_psi, gp_grid grid, gp_precision
 /* ------------------------------------------------------------------ batch
  * Many independent condensates -- each with its own grid, spacings, dt,
  * trap and g (the paper's programs run one condensate each) -- advanced in
- * imaginary time together: each step is three
- * launches that cover all active instances (per-instance arguments, norm
- * partials and counters), blocks of steps are replayed from CUDA graphs, and
+ * imaginary time together: each step is one launch per sweep covering all
+ * active instances (two on a strided axis at window 4 with complex64 fields:
+ * instances whose lines pair up in memory advance line pairs), with
+ * per-instance arguments, norm partials and counters; blocks of steps are
+ * replayed from CUDA graphs, and
  * gp_batch_run_imag_until drops converged instances from the launches.  All
  * instances share one precision and field; each axis uses one window for the
  * whole batch (the largest of the instances' smallest admissible windows;

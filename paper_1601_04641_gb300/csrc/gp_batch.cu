@@ -1,9 +1,10 @@
 // gp_batch.cu -- many independent condensates (uneven grids, traps and g)
-// advanced together: every imaginary-time step is three launches (kick + x,
-// y, z + norm) that each cover all active instances, with per-instance
-// argument blocks, norm partials and completion counters; blocks of steps
-// are replayed from captured CUDA graphs; converged instances drop out of
-// the launches.
+// advanced together: every imaginary-time step is one launch per sweep
+// (kick + x, y, z + norm) over all active instances -- two on a strided axis
+// when some instances advance line pairs and others single lines -- with
+// per-instance argument blocks, norm partials and completion counters;
+// blocks of steps are replayed from captured CUDA graphs; converged
+// instances drop out of the launches.
 #include "gp.h"
 #include "gp_host.h"
 #include "gp_internal.h"
