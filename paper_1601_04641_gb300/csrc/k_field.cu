@@ -309,6 +309,13 @@ __global__ void __launch_bounds__(kReduceThreads) observables_kernel(FieldArgs a
     observables_body<R, CPLX>(a, blockIdx.x, gridDim.x);
 }
 
+// The complex64 field's observables with at most 80 registers: three
+// 256-thread blocks per SM (unbounded it took 98 and two blocks, and ncu
+// showed it issue- and occupancy-bound).
+__global__ void __launch_bounds__(kReduceThreads, 3) observables_c64_kernel(FieldArgs a) {
+    observables_body<float, true>(a, blockIdx.x, gridDim.x);
+}
+
 // Many condensates in one launch: instance i owns blocks [first[i], first[i+1]).
 template <typename R, bool CPLX>
 __global__ void __launch_bounds__(kReduceThreads) observables_batch_kernel(const FieldArgs *args,
@@ -388,7 +395,12 @@ cudaError_t dispatch(int what, const FieldArgs &a, int blocks, void *dst, cudaSt
     switch (what) {
     case 0: gaussian_kernel<R, CPLX><<<fill_blocks(a.sites), 256, 0, s>>>(a); break;
     case 1: norm_kernel<R, CPLX><<<blocks, kReduceThreads, 0, s>>>(a); break;
-    case 2: observables_kernel<R, CPLX><<<observables_blocks(a), kReduceThreads, 0, s>>>(a); break;
+    case 2:
+        if constexpr (sizeof(R) == 4 && CPLX)
+            observables_c64_kernel<<<observables_blocks(a), kReduceThreads, 0, s>>>(a);
+        else
+            observables_kernel<R, CPLX><<<observables_blocks(a), kReduceThreads, 0, s>>>(a);
+        break;
     case 3: apply_scale_kernel<R, CPLX><<<fill_blocks(a.sites), 256, 0, s>>>(a, dst); break;
     default: return cudaErrorInvalidValue;
     }
