@@ -12,7 +12,6 @@ every other test before this one.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from paper_1601_04641_gb300 import _native as N
