@@ -50,9 +50,9 @@ WORKLOADS = {
 NCU_TRAFFIC = {
     # ncu --set full of the 480x400x160 half-depth case (profiles/), scaled x2
     # by sites to a full 480x400x320 launch: (read + write) bytes per launch
-    ("real_large", "zsweep_norm"): (2 * (246.290944e6 + 199.825152e6), "74b17fb3792f2075"),
-    ("real_large", "kick_xsweep"): (2 * (257.212160e6 + 194.386176e6), "74b17fb3792f2075"),
-    ("real_large", "ysweep"): (2 * (250.992640e6 + 193.096192e6), "74b17fb3792f2075"),
+    ("real_large", "zsweep_norm"): (2 * (246.290944e6 + 199.825152e6), "ffc8bb149e21534f"),
+    ("real_large", "kick_xsweep"): (2 * (257.212160e6 + 194.386176e6), "ffc8bb149e21534f"),
+    ("real_large", "ysweep"): (2 * (250.992640e6 + 193.096192e6), "ffc8bb149e21534f"),
 }
 
 

@@ -139,7 +139,7 @@ template <typename T> inline cudaError_t dev_malloc(T **p, size_t bytes) {
 void set_fail_alloc(int n);
 // Encode the tensor map of an array of n_lines rows of N elements of
 // elem_bytes (4 or 8) for the TMA z sweep; false if the layout does not allow
-// one (row pitch or base not 16-byte aligned) or the driver has no encoder.
+// one (row pitch or base not 16-byte aligned) or the CUDA driver offers no encoder.
 bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, int elem_bytes);
 constexpr int kReduceThreads = 256;
 
