@@ -3,7 +3,9 @@
 
 CPU: the oracle's profiles are pinned by a brute-force triple loop, by the
 norm of the C oracle's observables, and by the closed form of a separable
-field.  GPU: the library's profiles against the oracle's on the same fields
+field; six planted mistakes (spacings of the wrong axes, a missing spacing,
+sums over the wrong axes, |psi| for |psi|^2, the real part only, the cell
+volume for the two spacings) each fail at least one pin.  GPU: the library's profiles against the oracle's on the same fields
 (FP64 and FP32, real and complex, with a pending renormalisation and with a
 pending half kick), and the written files against gp_get_psi."""
 import os
@@ -16,11 +18,13 @@ from paper_1601_04641_gb300 import inputs
 
 
 # ---------------------------------------------------------------- oracle pins (CPU)
-def test_profiles_equal_brute_force_loops():
+# Each pin takes the profile function, so that planted mistakes can be shown
+# to fail at least one of them.
+def pin_brute_force(profiles):
     rng = np.random.default_rng(3)
     psi = rng.standard_normal((4, 3, 5)) + 1j * rng.standard_normal((4, 3, 5))
     d = (0.3, 0.2, 0.7)
-    rx, ry, rz = oracle.density_profiles(psi, d)
+    rx, ry, rz = profiles(psi, d)
     bx, by, bz = np.zeros(4), np.zeros(3), np.zeros(5)
     for i in range(4):
         for j in range(3):
@@ -29,19 +33,18 @@ def test_profiles_equal_brute_force_loops():
                 bx[i] += a2 * d[1] * d[2]
                 by[j] += a2 * d[0] * d[2]
                 bz[k] += a2 * d[0] * d[1]
-    for got, want in ((rx, bx), (ry, by), (rz, bz)):
-        assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+    return all(g.shape == w.shape and np.max(np.abs(g - w)) <= 1e-14 * np.max(np.abs(w))
+               for g, w in ((rx, bx), (ry, by), (rz, bz)))
 
 
-def test_profiles_integrate_to_the_oracle_norm():
+def pin_norm(profiles):
     p = inputs.imag_small()
     psi = inputs.random_field(p.shape, seed=5)
     norm = oracle.observables(psi, p.d, p.omega, p.g)["norm"]
-    for r, h in zip(oracle.density_profiles(psi, p.d), p.d):
-        assert abs(r.sum() * h - norm) <= 1e-13 * norm
+    return all(abs(r.sum() * h - norm) <= 1e-13 * norm for r, h in zip(profiles(psi, p.d), p.d))
 
 
-def test_profiles_of_a_separable_field():
+def pin_separable(profiles):
     # psi = a_i b_j c_k: rho_x = |a|^2 (dy sum |b|^2)(dz sum |c|^2), and so on
     rng = np.random.default_rng(11)
     a, b, c = (rng.standard_normal(n) + 1j * rng.standard_normal(n) for n in (7, 6, 9))
@@ -50,8 +53,56 @@ def test_profiles_of_a_separable_field():
     A, B, C = (np.abs(v) ** 2 for v in (a, b, c))
     want = (A * d[1] * B.sum() * d[2] * C.sum(), B * d[0] * A.sum() * d[2] * C.sum(),
             C * d[0] * A.sum() * d[1] * B.sum())
-    for got, w in zip(oracle.density_profiles(psi, d), want):
-        assert np.max(np.abs(got - w)) <= 1e-13 * np.max(w)
+    return all(g.shape == w.shape and np.max(np.abs(g - w)) <= 1e-13 * np.max(w)
+               for g, w in zip(profiles(psi, d), want))
+
+
+PINS = (pin_brute_force, pin_norm, pin_separable)
+
+
+def test_profiles_equal_brute_force_loops():
+    assert pin_brute_force(oracle.density_profiles)
+
+
+def test_profiles_integrate_to_the_oracle_norm():
+    assert pin_norm(oracle.density_profiles)
+
+
+def test_profiles_of_a_separable_field():
+    assert pin_separable(oracle.density_profiles)
+
+
+def _rho(psi):
+    psi = np.asarray(psi)
+    return psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+
+
+MUTANTS = {
+    # spacings of the wrong axes
+    "swapped_spacing": lambda psi, d: (_rho(psi).sum(axis=(1, 2)) * d[0] * d[2], _rho(psi).sum(axis=(0, 2)) * d[1] * d[2],
+                                       _rho(psi).sum(axis=(0, 1)) * d[0] * d[1]),
+    # one spacing left out
+    "missing_spacing": lambda psi, d: (_rho(psi).sum(axis=(1, 2)) * d[1], _rho(psi).sum(axis=(0, 2)) * d[0] * d[2],
+                                       _rho(psi).sum(axis=(0, 1)) * d[0] * d[1]),
+    # summed over the profile's own axis instead of the other two
+    "wrong_axes": lambda psi, d: (_rho(psi).sum(axis=(0, 1)) * d[1] * d[2], _rho(psi).sum(axis=(0, 2)) * d[0] * d[2],
+                                  _rho(psi).sum(axis=(1, 2)) * d[0] * d[1]),
+    # |psi| instead of |psi|^2
+    "modulus_not_density": lambda psi, d: tuple(np.sqrt(_rho(psi)).sum(axis=ax) * w for ax, w in
+                                                (((1, 2), d[1] * d[2]), ((0, 2), d[0] * d[2]), ((0, 1), d[0] * d[1]))),
+    # real part only
+    "real_part_only": lambda psi, d: tuple((np.asarray(psi).real ** 2).sum(axis=ax) * w for ax, w in
+                                           (((1, 2), d[1] * d[2]), ((0, 2), d[0] * d[2]), ((0, 1), d[0] * d[1]))),
+    # times the full cell volume dV instead of the two spacings
+    "cell_volume": lambda psi, d: tuple(_rho(psi).sum(axis=ax) * d[0] * d[1] * d[2] for ax in ((1, 2), (0, 2), (0, 1))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name):
+    with np.errstate(all="ignore"):
+        caught = [pin.__name__ for pin in PINS if not pin(MUTANTS[name])]
+    assert caught, "no pin catches " + name
 
 
 # ---------------------------------------------------------------- library vs oracle (GPU)
