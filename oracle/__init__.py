@@ -27,6 +27,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gp_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "libgporacle.so")
+_OMP_PATH = os.path.join(_HERE, "libgporacle_omp.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -34,17 +35,29 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
+def _compile(out_path: str, extra, force: bool) -> str:
+    if force or not os.path.exists(out_path) or (
+            os.path.getmtime(out_path) < os.path.getmtime(_SRC)):
+        tmp = out_path + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] + list(extra) + [
+            _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out_path)
+    return out_path
+
+
 def build(force: bool = False) -> str:
     """Compile ``gp_oracle.c`` into ``libgporacle.so`` next to it (gcc, no
     fused multiply-add contraction so x86 and Arm give the same bits)."""
-    if force or not os.path.exists(_LIB_PATH) or (
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
-        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-               _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_LIB_PATH, [], force)
+
+
+def build_openmp(force: bool = False) -> str:
+    """The same source built with -fopenmp into ``libgporacle_omp.so``: the
+    kick's sites and the sweeps' lines are shared out over the host cores
+    (OMP_NUM_THREADS), each computed exactly as in the serial build; every
+    sum stays serial.  Use it through ``use_library``."""
+    return _compile(_OMP_PATH, ["-fopenmp"], force)
 
 
 def _load():
@@ -223,18 +236,23 @@ def observables(psi, d, omega, g) -> dict:
     return dict(zip(OBS_KEYS, (float(v) for v in out)))
 
 
-def run_imag_until(psi, d, dt, omega, g, mu_tol, check_every=10, max_steps=100000):
+def run_imag_until(psi, d, dt, omega, g, mu_tol, check_every=10, max_steps=100000, rule=0):
     """Imaginary-time propagation with the stop rule |mu(n) - mu(n-K)| < tol,
-    checked every K steps (reading R6).  Returns (steps taken, last mu)."""
-    mu_prev = observables(psi, d, omega, g)["mu"]
-    steps = 0
+    checked every K steps (reading R6); rule 1 also requires
+    |E(n) - E(n-K)| < tol, rule 2 rule 1's test at two consecutive checks.
+    Returns (steps taken, last mu)."""
+    o = observables(psi, d, omega, g)
+    mu_prev, e_prev = o["mu"], o["energy"]
+    steps, streak = 0, 0
     while steps < max_steps:
         step(psi, d, dt, omega, g, False, check_every)
         steps += check_every
-        mu = observables(psi, d, omega, g)["mu"]
-        if abs(mu - mu_prev) < mu_tol:
-            return steps, mu
-        mu_prev = mu
+        o = observables(psi, d, omega, g)
+        ok = abs(o["mu"] - mu_prev) < mu_tol and (rule == 0 or abs(o["energy"] - e_prev) < mu_tol)
+        streak = streak + 1 if ok else 0
+        if streak >= (2 if rule == 2 else 1):
+            return steps, o["mu"]
+        mu_prev, e_prev = o["mu"], o["energy"]
     return steps, mu_prev
 
 

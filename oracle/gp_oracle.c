@@ -46,6 +46,12 @@
  * Every entry point returns 0 on success, -1 on bad arguments, -2 when an
  * allocation fails, -3 on a zero pivot.  Arrays of complex values are passed
  * as interleaved (re, im) doubles.
+ *
+ * The kick's sites and the sweeps' lines are independent, so their loops
+ * carry OpenMP work-sharing pragmas: a build with -fopenmp spreads them over
+ * the host cores (each site and each line computed exactly as in the serial
+ * build, so the two builds agree bit for bit); a build without it ignores
+ * them.  Every sum (norm, observables) stays a serial loop in a fixed order.
  */
 #include <complex.h>
 #include <math.h>
@@ -200,6 +206,7 @@ int oracle_kick(const int n[3], const double d[3], double *psi_ri, double dt,
     if (!n || !d || !omega || !psi_ri || !valid_grid(n, d) || !isfinite(dt))
         return ORACLE_EARG;
     cplx *psi = (cplx *)psi_ri;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int i = 0; i < n[0]; i++)
         for (int j = 0; j < n[1]; j++)
             for (int k = 0; k < n[2]; k++) {
@@ -232,53 +239,60 @@ int oracle_sweep(const int n[3], const double d[3], double *psi_ri, int axis, do
     const int m_int = len - 2;
     const cplx c = (realtime ? I : 1.0) * dt / (4.0 * d[axis] * d[axis]);
 
-    cplx *sub = malloc((size_t)m_int * sizeof(cplx));
-    cplx *diag = malloc((size_t)m_int * sizeof(cplx));
-    cplx *sup = malloc((size_t)m_int * sizeof(cplx));
-    cplx *rhs = malloc((size_t)m_int * sizeof(cplx));
-    cplx *sol = malloc((size_t)m_int * sizeof(cplx));
-    cplx *line = malloc((size_t)len * sizeof(cplx));
-    int rc = ORACLE_OK;
-    if (!sub || !diag || !sup || !rhs || !sol || !line) {
-        rc = ORACLE_ENOMEM;
-        goto out;
-    }
-    for (int m = 0; m < m_int; m++) {
-        sub[m] = -c;
-        diag[m] = 1.0 + 2.0 * c;
-        sup[m] = -c;
-    }
-
     /* The two axes that label the lines, and the strides of all three. */
     const size_t stride[3] = {(size_t)n[1] * (size_t)n[2], (size_t)n[2], 1};
     const int a1 = (axis == 0) ? 1 : 0;
     const int a2 = (axis == 2) ? 1 : 2;
-    for (int p = 0; p < n[a1]; p++) {
-        for (int q = 0; q < n[a2]; q++) {
-            size_t base = (size_t)p * stride[a1] + (size_t)q * stride[a2];
-            for (int m = 0; m < len; m++)
-                line[m] = psi[base + (size_t)m * stride[axis]];
-            for (int m = 1; m <= len - 2; m++) {
-                cplx left = (m - 1 >= 1) ? line[m - 1] : 0.0;
-                cplx right = (m + 1 <= len - 2) ? line[m + 1] : 0.0;
-                rhs[m - 1] = c * left + (1.0 - 2.0 * c) * line[m] + c * right;
-            }
-            rc = thomas_solve(m_int, sub, diag, sup, rhs, sol);
-            if (rc != ORACLE_OK)
-                goto out;
-            psi[base] = 0.0;
-            psi[base + (size_t)(len - 1) * stride[axis]] = 0.0;
-            for (int m = 1; m <= len - 2; m++)
-                psi[base + (size_t)m * stride[axis]] = sol[m - 1];
+    int rc = ORACLE_OK;
+#pragma omp parallel
+    {
+        /* each thread's own line buffers and matrix */
+        cplx *sub = malloc((size_t)m_int * sizeof(cplx));
+        cplx *diag = malloc((size_t)m_int * sizeof(cplx));
+        cplx *sup = malloc((size_t)m_int * sizeof(cplx));
+        cplx *rhs = malloc((size_t)m_int * sizeof(cplx));
+        cplx *sol = malloc((size_t)m_int * sizeof(cplx));
+        cplx *line = malloc((size_t)len * sizeof(cplx));
+        int my_rc = (sub && diag && sup && rhs && sol && line) ? ORACLE_OK : ORACLE_ENOMEM;
+        for (int m = 0; m < m_int && my_rc == ORACLE_OK; m++) {
+            sub[m] = -c;
+            diag[m] = 1.0 + 2.0 * c;
+            sup[m] = -c;
         }
+#pragma omp for collapse(2) schedule(static)
+        for (int p = 0; p < n[a1]; p++) {
+            for (int q = 0; q < n[a2]; q++) {
+                if (my_rc != ORACLE_OK)
+                    continue;
+                size_t base = (size_t)p * stride[a1] + (size_t)q * stride[a2];
+                for (int m = 0; m < len; m++)
+                    line[m] = psi[base + (size_t)m * stride[axis]];
+                for (int m = 1; m <= len - 2; m++) {
+                    cplx left = (m - 1 >= 1) ? line[m - 1] : 0.0;
+                    cplx right = (m + 1 <= len - 2) ? line[m + 1] : 0.0;
+                    rhs[m - 1] = c * left + (1.0 - 2.0 * c) * line[m] + c * right;
+                }
+                my_rc = thomas_solve(m_int, sub, diag, sup, rhs, sol);
+                if (my_rc != ORACLE_OK)
+                    continue;
+                psi[base] = 0.0;
+                psi[base + (size_t)(len - 1) * stride[axis]] = 0.0;
+                for (int m = 1; m <= len - 2; m++)
+                    psi[base + (size_t)m * stride[axis]] = sol[m - 1];
+            }
+        }
+#pragma omp critical
+        {
+            if (my_rc != ORACLE_OK && rc == ORACLE_OK)
+                rc = my_rc;
+        }
+        free(sub);
+        free(diag);
+        free(sup);
+        free(rhs);
+        free(sol);
+        free(line);
     }
-out:
-    free(sub);
-    free(diag);
-    free(sup);
-    free(rhs);
-    free(sol);
-    free(line);
     return rc;
 }
 
