@@ -175,7 +175,11 @@ gp_status gp_run_imag_schedule(gp_handle h, int levels, const double *dt_scale, 
  * close to the ground state it can turn around on its way in, and at the
  * turning point its change between checks drops below the tolerance long
  * before convergence.  E decreases monotonically in imaginary time, so rule 1
- * stops only where both have settled.  No effect on the steps themselves. */
+ * stops only where both have settled.  2 requires rule 1's condition at two
+ * consecutive checks: after a change of dt (a schedule's next level) mu and
+ * E approach their new values along several modes at once, and a single
+ * check can fall between a sign change of their differences.  No effect on
+ * the steps themselves; GP_ERR_ARG for another rule. */
 gp_status gp_set_stop_rule(gp_handle h, int rule);
 
 /* Compute the observables of the current psi into *out (synchronises).
@@ -206,7 +210,11 @@ gp_status gp_set_stream(gp_handle h, void *cuda_stream);
 
 /* Block until the handle's queued work is done.  Returns GP_ERR_TIMEOUT if a
  * sweep kernel gave up waiting for its TMA copies (each wait is bounded to
- * about a second); gp_observables reports the same. */
+ * about a second); gp_observables reports the same.  psi is then undefined
+ * -- lines of other blocks of that launch included, since a copy may land
+ * after its block has exited -- and every call that reads or advances psi
+ * returns GP_ERR_STATE until gp_set_psi, gp_init_gaussian or gp_nn_predict
+ * sets it again. */
 gp_status gp_sync(gp_handle h);
 
 /* Window of the windowed back substitution per axis for imaginary (mode 0)
@@ -225,9 +233,22 @@ gp_status gp_set_window(gp_handle h, int window);
  * admissible for that axis). */
 gp_status gp_set_axis_window(gp_handle h, int axis, int window);
 
-/* Two adjacent lines per thread on the strided axes (1, the default, where
- * the layout allows it) or one (0).  The arithmetic per line is the same. */
+/* Several adjacent lines per thread on the strided axes (1, the default:
+ * the widest group the layout and form allow) or one line per thread (0).
+ * A group of g lines needs the axis's line count, and for the y sweep nz, to
+ * be a multiple of g.  Pairs serve elements of up to 8 bytes; groups of four
+ * serve FP32 real fields with a windowed solve, so that each row a warp
+ * moves is 512 contiguous bytes.  The arithmetic per line is the same. */
 gp_status gp_set_pair_lines(gp_handle h, int on);
+
+/* The most adjacent lines per thread on one strided axis (axis 0 = x,
+ * 1 = y; lines 1, 2 or 4; default 4), within the rules of gp_set_pair_lines.
+ * GP_ERR_ARG for another axis or count. */
+gp_status gp_set_lines_per_thread(gp_handle h, int axis, int lines);
+
+/* Lines per thread each axis's sweep uses in `mode` (0 imaginary, 1 real
+ * time) under the current settings (the z sweep always reports 1). */
+gp_status gp_get_lines_per_thread(gp_handle h, int mode, int lines[3]);
 
 /* The z sweep (stride-1 axis) through tensor-memory-accelerator tiles: one
  * bulk tensor copy per 64 lines x 64 bytes, two lines per thread (1, the
@@ -238,8 +259,9 @@ gp_status gp_set_pair_lines(gp_handle h, int on);
  * fields, windows 4 and 8 for 8-byte elements), whole lines, and nz - 2 at
  * least one chunk plus the window plus 2; elsewhere the other form runs.
  * The arithmetic per line is the same in both.  gp_get_tma reports whether
- * the handle's buffers have tensor maps and the form is selected (the
- * per-launch conditions above still apply). */
+ * the z sweep of imaginary time, or (complex fields) of real time, takes the
+ * TMA form under the current settings: selected, tensor maps encoded for the
+ * handle's buffers, and the conditions above met. */
 gp_status gp_set_tma(gp_handle h, int on);
 gp_status gp_get_tma(gp_handle h, int *in_use);
 
@@ -280,6 +302,13 @@ gp_status gp_set_graph_block(gp_handle h, int steps);
  * symmetric splitting is applied first (queued on the stream).  Valid until
  * the next call that queues work on the handle. */
 gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale);
+
+/* The renormalisation factor pending on the buffer gp_psi_device_ptr gives
+ * (1.0 when none is pending): psi is that buffer times *scale.  Synchronises
+ * the handle's stream.  A caller that reads the buffer directly -- e.g.
+ * gp_observables_noalloc after imaginary-time steps -- passes this factor as
+ * the read scale. */
+gp_status gp_pending_scale(gp_handle h, double *scale);
 
 /* Density output.  The paper's programs write the condensate wavefunction
  * to files ("Special features": each MPI process writes its part, and the
@@ -345,8 +374,9 @@ gp_status gp_observables_noalloc(const void *dev_psi, gp_grid grid, gp_precision
  * trap and g (the paper's programs run one condensate each) -- advanced in
  * imaginary time together: each step is one launch per sweep covering all
  * active instances (two on a strided axis at window 4 with complex64 fields:
- * instances whose lines pair up in memory advance line pairs), with
- * per-instance arguments, norm partials and counters; blocks of steps are
+ * instances whose lines pair up in memory advance line pairs; two on the z
+ * axis when some instances' rows fit the TMA form of gp_set_tma and others
+ * do not), with per-instance arguments, norm partials and counters; blocks of steps are
  * replayed from CUDA graphs, and
  * gp_batch_run_imag_until drops converged instances from the launches.  All
  * instances share one precision and field; each axis uses one window for the
@@ -386,6 +416,15 @@ gp_status gp_batch_get_window(gp_batch b, int window[3]);
 gp_status gp_batch_get_segments(gp_batch b, int i, int seg_len[3], int n_seg[3]);
 /* Steps per CUDA graph (default 16; 0 or 1: launch by launch). */
 gp_status gp_batch_set_graph_block(gp_batch b, int steps);
+/* z sweep of the instances whose rows fit the TMA form (the rules of
+ * gp_set_tma, at the batch's z window; at most 64 instances, the first ones
+ * in creation order) through TMA tiles (1, the default) or every instance
+ * through per-thread copies (0).  Each TMA instance gets its own tensor maps;
+ * the arithmetic per line, and so psi, is the same either way; norms may
+ * differ by rounding (the two forms group the norm's sums differently).
+ * gp_batch_get_tma gives the number of instances on the TMA form. */
+gp_status gp_batch_set_tma(gp_batch b, int on);
+gp_status gp_batch_get_tma(gp_batch b, int *count);
 /* Last error of the batch (NULL: as gp_last_error(NULL)). */
 const char *gp_batch_last_error(gp_batch b);
 
@@ -449,9 +488,14 @@ const char *gp_last_error(gp_handle h);
  * is copied and the kernel ends within about 2 * cycles; synchronises.
  * gp_debug_fail_alloc(n) makes the n-th next device allocation of the library
  * fail as if the device were out of memory (n <= 0: no failure); every
- * creating call then returns GP_ERR_NOMEM and frees what it had allocated. */
+ * creating call then returns GP_ERR_NOMEM and frees what it had allocated.
+ * gp_debug_raise_status(h) sets the handle's device status word from the
+ * host, as a sweep kernel does when a bounded wait expires (nothing waits or
+ * faults on the device): the next synchronising call reports
+ * GP_ERR_TIMEOUT and psi is lost until set again (see gp_sync). */
 gp_status gp_selftest_bounded_wait(long long cycles, void *cuda_stream, int *completed, int *expired);
 void gp_debug_fail_alloc(int n);
+gp_status gp_debug_raise_status(gp_handle h);
 
 /* Library version string. */
 const char *gp_version(void);

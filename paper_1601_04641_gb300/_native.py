@@ -60,11 +60,14 @@ SIGNATURES = {
     "gp_set_window": (_i, [Handle, _i]),
     "gp_set_axis_window": (_i, [Handle, _i, _i]),
     "gp_set_pair_lines": (_i, [Handle, _i]),
+    "gp_set_lines_per_thread": (_i, [Handle, _i, _i]),
+    "gp_get_lines_per_thread": (_i, [Handle, _i, ctypes.POINTER(_i)]),
     "gp_set_tma": (_i, [Handle, _i]),
     "gp_set_stop_rule": (_i, [Handle, _i]),
     "gp_set_splitting": (_i, [Handle, _i]),
     "gp_selftest_bounded_wait": (_i, [ctypes.c_longlong, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_debug_fail_alloc": (None, [_i]),
+    "gp_debug_raise_status": (_i, [Handle]),
     "gp_run_imag_schedule": (_i, [Handle, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, _i,
                                   ctypes.POINTER(_i)]),
     "gp_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),
@@ -74,6 +77,7 @@ SIGNATURES = {
     "gp_autotune": (_i, [Handle, _i, _i, ctypes.c_char_p]),
     "gp_set_graph_block": (_i, [Handle, _i]),
     "gp_psi_device_ptr": (_i, [Handle, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
+    "gp_pending_scale": (_i, [Handle, ctypes.POINTER(_d)]),
     "gp_density_profiles": (_i, [Handle, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "gp_write_wavefunction": (_i, [Handle, ctypes.c_char_p, _i]),
     "gp_observables_noalloc": (_i, [_vp, Grid, _i, _i, _d, _d, _d, _d, _d, _vp, _vp]),
@@ -90,6 +94,8 @@ SIGNATURES = {
     "gp_batch_get_window": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_batch_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_batch_set_graph_block": (_i, [Handle, _i]),
+    "gp_batch_set_tma": (_i, [Handle, _i]),
+    "gp_batch_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_batch_set_stop_rule": (_i, [Handle, _i]),
     "gp_batch_set_dt_scale": (_i, [Handle, _d]),
     "gp_batch_run_imag_schedule": (_i, [Handle, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, _i,

@@ -117,13 +117,14 @@ struct gp_handle_s {
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     bool tma_z = true;         // ... through TMA tiles where the grid allows it
-    int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol
+    int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol; 2 rule 1 twice in a row
     int splitting = 1;         // real time: 1 Lie (kick, sweeps), 2 symmetric (half kick, sweeps, half kick)
     bool kick_pending = false; // symmetric splitting: buf[cur] still lacks its trailing half kick
     bool zmap_ok = false;      // zmap[b]: tensor map of buf[b] as n_lines rows of nz elements
     CUtensorMap zmap[2];
     unsigned int *d_status = nullptr;  // nonzero after a kernel's bounded wait expired
-    bool pair_lines = true;    // two lines per thread on the strided axes when possible
+    bool psi_lost = false;             // an expired wait was reported: psi is undefined until set again
+    int max_lpt[2] = {4, 4};   // most adjacent lines per thread on the x and y sweeps (1, 2 or 4)
     int seg_override[3] = {0, 0, 0};  // interior nodes per segment, 0 = automatic
     // observables history queued during stepping
     int track_every = 0, track_cap = 0, track_count = 0;
@@ -239,6 +240,7 @@ FieldArgs handle_field_args(gp_handle h) {
 constexpr int kNormBlocks = 152 * 4;
 
 gp_status alloc_scratch(gp_handle h) {
+    prepare_field_launches();
     // z sweep: at most one block per 32 (line, segment) threads, segments of >= 1 node
     size_t cap = kNormBlocks;
     cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32) * (size_t)(h->n[2] - 2));
@@ -360,6 +362,18 @@ gp_status enter(gp_handle h) {
     return GP_OK;
 }
 
+// enter() for the calls that read or advance psi: after an expired TMA wait
+// psi is lost (the results of the launch are undefined, other blocks' lines
+// included), and those calls fail until psi is set again.
+gp_status enter_psi(gp_handle h) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    if (h->psi_lost)
+        return fail(h, GP_ERR_STATE, "psi was lost to an expired TMA wait; set it again (gp_set_psi, "
+                                     "gp_init_gaussian)");
+    return GP_OK;
+}
+
 gp_status queue_observables(gp_handle h, double *dst);
 
 // After a synchronisation: a kernel whose bounded wait expired left a flag.
@@ -368,24 +382,28 @@ gp_status check_status(gp_handle h) {
     GP_CK(h, cudaMemcpy(&flag, h->d_status, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) {
         cudaMemset(h->d_status, 0, sizeof(flag));
-        return fail(h, GP_ERR_TIMEOUT, "a sweep kernel's wait for its TMA copies expired; psi is not trustworthy");
+        h->psi_lost = true;
+        return fail(h, GP_ERR_TIMEOUT, "a sweep kernel's wait for its TMA copies expired; psi is lost until set again");
     }
     return GP_OK;
 }
 
-// Two adjacent lines per thread on the strided axes when every pair is
-// adjacent in memory and 2-element aligned: an even number of lines and,
-// for y lines (i, k), an even nz.  Elements of 8 bytes or less only.
-int lines_per_thread(gp_handle h, int ax) {
-    if (!h->pair_lines || ax == 2 || h->elem > 8) return 1;
-    if (sweep_lines(h, ax) % 2) return 1;
-    if (ax == 1 && h->n[2] % 2) return 1;
-    return 2;
+// Adjacent lines per thread on the strided axes, up to max_lpt[ax]: a group
+// of g lines must be adjacent in memory and g-element aligned, i.e. the line
+// count a multiple of g and, for y lines (i, k), nz a multiple of g.  Pairs
+// for elements of 8 bytes or less; groups of four for FP32 real fields with
+// a windowed solve (the form that has a four-line variant).
+int lines_per_thread(gp_handle h, int ax, int window) {
+    if (ax == 2 || h->elem > 8) return 1;
+    auto fits = [&](int g) { return sweep_lines(h, ax) % g == 0 && (ax != 1 || h->n[2] % g == 0); };
+    if (h->max_lpt[ax] >= 4 && h->elem == 4 && window > 0 && fits(4)) return 4;
+    if (h->max_lpt[ax] >= 2 && fits(2)) return 2;
+    return 1;
 }
 
 // Segments of one axis (see choose_segments).
 void segments(gp_handle h, int ax, int window, int *seg_len, int *n_seg) {
-    choose_segments(geom(h), ax, window, lines_per_thread(h, ax), (int)h->elem, h->contiguous_z,
+    choose_segments(geom(h), ax, window, lines_per_thread(h, ax, window), (int)h->elem, h->contiguous_z,
                     h->seg_override[ax], seg_len, n_seg);
 }
 
@@ -399,7 +417,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     const int ax = stage;
     L.window = h->window[mode][ax];
     L.threads = h->threads[ax];
-    L.lpt = lines_per_thread(h, ax);
+    L.lpt = lines_per_thread(h, ax, L.window);
     L.contiguous = (ax == 2 && h->contiguous_z && L.window > 0) ? 1 : 0;
     int seg_len = 0, n_seg = 0;
     segments(h, ax, L.window, &seg_len, &n_seg);
@@ -632,6 +650,7 @@ gp_status gp_init_gaussian(gp_handle h) {
     GP_CK(h, launch_norm(p, cplx, a, kNormBlocks, h->stream));
     h->scale_pending = true;
     h->kick_pending = false;
+    h->psi_lost = false;
     h->step = 0;
     h->t = 0.0;
     return GP_OK;
@@ -647,13 +666,14 @@ gp_status gp_set_psi(gp_handle h, const void *psi, int on_device) {
     if (!on_device) GP_CK(h, cudaStreamSynchronize(h->stream));
     h->scale_pending = false;
     h->kick_pending = false;
+    h->psi_lost = false;
     h->step = 0;
     h->t = 0.0;
     return GP_OK;
 }
 
 gp_status gp_get_psi(gp_handle h, void *psi, int on_device) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
     if ((st = settle(h)) != GP_OK) return st;
@@ -694,20 +714,20 @@ gp_status gp_set_dt(gp_handle h, double dt) {
 }
 
 gp_status gp_step_imag(gp_handle h, int nsteps) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     return run_steps(h, nsteps, false);
 }
 
 gp_status gp_step_real(gp_handle h, int nsteps) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     return run_steps(h, nsteps, true);
 }
 
 gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max_steps,
                             int *steps_taken) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (!(mu_tol > 0.0) || check_every < 1 || max_steps < 0)
         return fail(h, GP_ERR_ARG, "need mu_tol > 0, check_every >= 1, max_steps >= 0");
@@ -715,7 +735,8 @@ gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max
     st = observables(h, &o);
     if (st != GP_OK) return st;
     double mu_prev = o.mu, e_prev = o.energy;
-    int taken = 0;
+    int taken = 0, streak = 0;
+    const int need = h->stop_rule == 2 ? 2 : 1;  // consecutive checks that must pass
     while (taken < max_steps) {
         const int n = std::min(check_every, max_steps - taken);
         st = run_steps(h, n, false);
@@ -723,8 +744,10 @@ gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max
         taken += n;
         st = observables(h, &o);
         if (st != GP_OK) break;
-        if (std::fabs(o.mu - mu_prev) < mu_tol && (h->stop_rule == 0 || std::fabs(o.energy - e_prev) < mu_tol))
-            break;
+        const bool pass = std::fabs(o.mu - mu_prev) < mu_tol &&
+                          (h->stop_rule == 0 || std::fabs(o.energy - e_prev) < mu_tol);
+        streak = pass ? streak + 1 : 0;
+        if (streak >= need) break;
         mu_prev = o.mu;
         e_prev = o.energy;
     }
@@ -734,7 +757,7 @@ gp_status gp_run_imag_until(gp_handle h, double mu_tol, int check_every, int max
 
 gp_status gp_run_imag_schedule(gp_handle h, int levels, const double *dt_scale, const double *mu_tol,
                                int check_every, int max_steps, int *steps_taken) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (levels < 1 || !dt_scale || !mu_tol) return fail(h, GP_ERR_ARG, "need levels >= 1 and both arrays");
     for (int l = 0; l < levels; ++l)
@@ -757,20 +780,20 @@ gp_status gp_run_imag_schedule(gp_handle h, int levels, const double *dt_scale, 
 
 gp_status gp_set_stop_rule(gp_handle h, int rule) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
-    if (rule != 0 && rule != 1) return fail(h, GP_ERR_ARG, "rule must be 0 or 1");
+    if (rule < 0 || rule > 2) return fail(h, GP_ERR_ARG, "rule must be 0, 1 or 2");
     h->stop_rule = rule;
     return GP_OK;
 }
 
 gp_status gp_observables(gp_handle h, gp_obs *out) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (!out) return fail(h, GP_ERR_ARG, "out is NULL");
     return observables(h, out);
 }
 
 gp_status gp_density_profiles(gp_handle h, double *rho_x, double *rho_y, double *rho_z) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (!rho_x && !rho_y && !rho_z) return GP_OK;
     FieldArgs a = handle_field_args(h);  // the pending scale enters as s^2; a pending half kick is a phase
@@ -800,7 +823,7 @@ gp_status gp_density_profiles(gp_handle h, double *rho_x, double *rho_y, double 
 }
 
 gp_status gp_write_wavefunction(gp_handle h, const char *path, int what) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (!path) return fail(h, GP_ERR_ARG, "path is NULL");
     if (what != GP_OUT_PSI && what != GP_OUT_DENSITY) return fail(h, GP_ERR_ARG, "what must be GP_OUT_PSI or GP_OUT_DENSITY");
@@ -907,7 +930,7 @@ gp_status gp_get_tracking(gp_handle h, gp_obs *out, int max, int *count) {
 }
 
 gp_status gp_step_stage(gp_handle h, int stage, int realtime) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (stage < 0 || stage > 2) return fail(h, GP_ERR_ARG, "stage must be 0, 1 or 2");
     if (realtime && h->field != GP_COMPLEX)
@@ -982,8 +1005,23 @@ gp_status gp_set_axis_window(gp_handle h, int axis, int window) {
 
 gp_status gp_set_pair_lines(gp_handle h, int on) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
-    h->pair_lines = on != 0;
+    h->max_lpt[0] = h->max_lpt[1] = on ? 4 : 1;
     drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_set_lines_per_thread(gp_handle h, int axis, int lines) {
+    if (!h || axis < 0 || axis > 1) return fail(h, GP_ERR_ARG, "axis must be 0 (x) or 1 (y)");
+    if (lines != 1 && lines != 2 && lines != 4) return fail(h, GP_ERR_ARG, "lines must be 1, 2 or 4");
+    h->max_lpt[axis] = lines;
+    drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_get_lines_per_thread(gp_handle h, int mode, int lines[3]) {
+    if (!h || !lines || mode < 0 || mode > 1) return fail(h, GP_ERR_ARG, "bad arguments");
+    if (mode >= modes_of(h)) return fail(h, GP_ERR_STATE, "no real-time tables on a GP_REAL field");
+    for (int ax = 0; ax < 3; ++ax) lines[ax] = lines_per_thread(h, ax, h->window[mode][ax]);
     return GP_OK;
 }
 
@@ -1006,7 +1044,17 @@ gp_status gp_set_tma(gp_handle h, int on) {
 
 gp_status gp_get_tma(gp_handle h, int *in_use) {
     if (!h || !in_use) return fail(h, GP_ERR_ARG, "bad arguments");
-    *in_use = (h->tma_z && h->zmap_ok && h->contiguous_z) ? 1 : 0;
+    // the z sweep of either mode takes the TMA form: enabled, maps encoded,
+    // the contiguous windowed solve, and rows and window that fit it
+    int used = 0;
+    for (int mode = 0; mode < modes_of(h); ++mode) {
+        const int w = h->window[mode][2];
+        int seg_len = 0, n_seg = 0;
+        segments(h, 2, w, &seg_len, &n_seg);
+        used |= (h->tma_z && h->zmap_ok && h->contiguous_z && w > 0 &&
+                 tma_z_fits((int)h->elem, w, h->n[2], n_seg, sweep_lines(h, 2))) ? 1 : 0;
+    }
+    *in_use = used;
     return GP_OK;
 }
 
@@ -1036,7 +1084,7 @@ gp_status gp_get_segments(gp_handle h, int mode, int seg_len[3], int n_seg[3]) {
 
 gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
     if (!h || !ptr) return fail(h, GP_ERR_ARG, "bad arguments");
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if ((st = settle(h)) != GP_OK) return st;
     *ptr = h->buf[h->cur];
@@ -1044,29 +1092,52 @@ gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
     return GP_OK;
 }
 
+gp_status gp_debug_raise_status(gp_handle h) {
+    gp_status st = enter(h);
+    if (st != GP_OK) return st;
+    const unsigned int flag = 1u;
+    GP_CK(h, cudaMemcpyAsync(h->d_status, &flag, sizeof(flag), cudaMemcpyHostToDevice, h->stream));
+    GP_CK(h, cudaStreamSynchronize(h->stream));
+    return GP_OK;
+}
+
+gp_status gp_pending_scale(gp_handle h, double *scale) {
+    if (!h || !scale) return fail(h, GP_ERR_ARG, "bad arguments");
+    gp_status st = enter_psi(h);
+    if (st != GP_OK) return st;
+    if ((st = settle(h)) != GP_OK) return st;
+    double v = 1.0;
+    if (h->scale_pending) {
+        GP_CK(h, cudaMemcpyAsync(&v, h->d_scal + S_SCALE, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+        GP_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    *scale = v;
+    return GP_OK;
+}
+
 // ---------------------------------------------------------------- autotuner
 namespace {
 
 struct TuneChoice {
-    int threads, seg, pair;
+    int threads, seg, lpt;  // lpt: most lines per thread (strided axes)
 };
 
 std::string tune_key(gp_handle h, int realtime, int ax) {
     std::ostringstream k;
     k << h->n[0] << "x" << h->n[1] << "x" << h->n[2] << (h->prec == GP_F32 ? "/f32" : "/f64")
       << (h->field == GP_COMPLEX ? "/c" : "/r") << (realtime ? "/rt" : "/it") << "/w" << h->window[realtime][ax]
-      << "/ax" << ax;
+      << "/ax" << ax << "/v2";
     return k.str();
 }
 
-// Cache file: one "key threads seg pair" line per tuned (grid, form, axis).
+// Cache file: one "key threads seg lpt" line per tuned (grid, form, axis).
 bool cache_lookup(const char *path, const std::string &key, TuneChoice *c) {
     if (!path || !*path) return false;
     std::ifstream f(path);
     std::string k;
     TuneChoice t;
     bool found = false;
-    while (f >> k >> t.threads >> t.seg >> t.pair)
+    while (f >> k >> t.threads >> t.seg >> t.lpt)
         if (k == key) {
             *c = t;
             found = true;
@@ -1077,7 +1148,7 @@ bool cache_lookup(const char *path, const std::string &key, TuneChoice *c) {
 void cache_store(const char *path, const std::string &key, const TuneChoice &c) {
     if (!path || !*path) return;
     std::ofstream f(path, std::ios::app);
-    f << key << " " << c.threads << " " << c.seg << " " << c.pair << "\n";
+    f << key << " " << c.threads << " " << c.seg << " " << c.lpt << "\n";
 }
 
 }  // namespace
@@ -1102,11 +1173,11 @@ gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) 
     GP_CK(h, cudaEventCreate(&e1));
     for (int ax = 0; ax < 3 && st == GP_OK; ++ax) {
         const std::string key = tune_key(h, realtime, ax);
-        TuneChoice best{h->threads[ax], h->seg_override[ax], h->pair_lines ? 1 : 0};
+        TuneChoice best{h->threads[ax], h->seg_override[ax], ax < 2 ? h->max_lpt[ax] : 1};
         if (cache_lookup(path, key, &best)) {
             h->threads[ax] = best.threads;
             h->seg_override[ax] = best.seg;
-            if (ax < 2) h->pair_lines = best.pair != 0;
+            if (ax < 2) h->max_lpt[ax] = best.lpt;
             continue;
         }
         const int n = h->n[ax] - 2;
@@ -1114,16 +1185,26 @@ gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) 
         const int segs[] = {0, 64, 128, 256, n};
         for (int th : {64, 128})
             for (int sg : segs)
-                for (int pr : {1, 0}) {
-                    if (ax == 2 && pr == 0) continue;  // pairs apply to the strided axes only
+                for (int lp : {4, 2, 1}) {
+                    if (ax == 2 && lp != 1) continue;  // line groups apply to the strided axes only
                     if (h->window[mode][ax] == 0 && sg != 0) continue;  // the exact solve has no segments
-                    cands.push_back({th, sg, pr});
+                    // skip limits that select the same group size as a larger one
+                    if (ax < 2 && lp < 4) {
+                        const int keep = h->max_lpt[ax];
+                        h->max_lpt[ax] = lp * 2;
+                        const int wider = lines_per_thread(h, ax, h->window[mode][ax]);
+                        h->max_lpt[ax] = lp;
+                        const int mine = lines_per_thread(h, ax, h->window[mode][ax]);
+                        h->max_lpt[ax] = keep;
+                        if (wider == mine) continue;
+                    }
+                    cands.push_back({th, sg, lp});
                 }
         float best_ms = 1e30f;
         for (const TuneChoice &c : cands) {
             h->threads[ax] = c.threads;
             h->seg_override[ax] = c.seg;
-            if (ax < 2) h->pair_lines = c.pair != 0;
+            if (ax < 2) h->max_lpt[ax] = c.lpt;
             float ms = 0.f;
             for (int r = 0; r <= reps && st == GP_OK; ++r) {  // r = 0 warms up
                 h->cur = cur0;
@@ -1142,7 +1223,7 @@ gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) 
         }
         h->threads[ax] = best.threads;
         h->seg_override[ax] = best.seg;
-        if (ax < 2) h->pair_lines = best.pair != 0;
+        if (ax < 2) h->max_lpt[ax] = best.lpt;
         cache_store(path, key, best);
     }
     cudaEventDestroy(e0);
@@ -1160,7 +1241,7 @@ gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) 
 extern "C" {
 
 gp_status gp_autotune(gp_handle h, int realtime, int reps, const char *cache_path) {
-    gp_status st = enter(h);
+    gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
     if (realtime && h->field != GP_COMPLEX) return fail(h, GP_ERR_STATE, "real time needs a GP_COMPLEX field");
     if (reps < 1) return fail(h, GP_ERR_ARG, "reps must be >= 1");
@@ -1183,6 +1264,8 @@ gp_status gp_nn_predict(gp_nn net, gp_handle h) {
     FieldArgs a = handle_field_args(h);
     GP_CK(h, launch_norm(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
     h->scale_pending = true;
+    h->kick_pending = false;
+    h->psi_lost = false;
     h->step = 0;
     h->t = 0.0;
     return GP_OK;

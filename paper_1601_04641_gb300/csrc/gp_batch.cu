@@ -32,6 +32,7 @@ struct Inst {
     size_t part_off = 0;    // offset (doubles) of the partials region
     int seg_len[3] = {0, 0, 0}, n_seg[3] = {0, 0, 0};
     int lpt[3] = {1, 1, 1}; // lines per thread of the strided sweeps (2: adjacent line pairs)
+    bool ztma = false;      // z sweep through TMA tiles (its rows fit the TMA form)
     int cur = 0;            // which packed buffer holds psi
     long long step = 0;
     double t = 0.0;
@@ -39,14 +40,17 @@ struct Inst {
 };
 
 // Device tables of one launch configuration (a set of instances, a parity).
-// Each sweep has up to two launches: group 0 the instances that advance one
-// line per thread, group 1 those that advance adjacent line pairs.
+// Each sweep has up to two launches.  Strided sweeps: group 0 the instances
+// that advance one line per thread, group 1 those that advance adjacent line
+// pairs.  z sweep: group 0 the per-thread-copy form, group 1 the TMA form
+// (at most kTmaBatch instances whose rows fit it, with their tensor maps).
 struct LaunchSet {
     SweepArgs *args[3][2][2] = {};   // [sweep][group][parity]
     unsigned *first[3][2] = {};
     unsigned *gridx[3][2] = {};
     unsigned total[3][2] = {};
     int count[3][2] = {};
+    std::vector<BatchTmaMaps> zmaps;  // [parity]: maps of the z sweep's TMA group
     FieldArgs *fargs = nullptr;   // observables of the instances, for their current parity
     unsigned *ofirst = nullptr;
     unsigned ototal = 0;
@@ -76,10 +80,11 @@ struct gp_batch_s {
     unsigned int *d_counters = nullptr;
     int window[3] = {0, 0, 0};
     bool contiguous_z = false;
+    bool use_tma = true;           // z sweep through TMA for the instances whose rows fit
     LaunchSet act;                 // the active instances
     bool dirty = true;
     int graph_block = 16;
-    int stop_rule = 0;             // as gp_set_stop_rule
+    int stop_rule = 0;             // as gp_set_stop_rule (0, 1 or 2)
     double dt_scale = 1.0;         // every instance steps with dt0 * dt_scale
     size_t tab_bytes = 0;
     cudaStream_t cap_stream = nullptr;
@@ -131,6 +136,18 @@ unsigned sweep_gridx(gp_batch b, const Inst &I, int ax, int lpt = 1) {
     return (unsigned)((units + kSweepThreads - 1) / kSweepThreads);
 }
 
+// Which instances take the TMA z sweep: the first kTmaBatch whose rows fit
+// the TMA form at the batch's z window (the contiguous z sweep solves whole
+// lines, one segment).
+void assign_ztma(gp_batch b) {
+    int count = 0;
+    for (Inst &I : b->inst) {
+        I.ztma = b->use_tma && b->contiguous_z && count < kTmaBatch &&
+                 tma_z_fits((int)b->elem, b->window[2], I.G.n[2], 1, axis_lines(I.G, 2));
+        count += I.ztma ? 1 : 0;
+    }
+}
+
 // Tables, windows and segments of every instance for dt = dt0 * scale.  One
 // window per axis for the whole batch: the largest of the instances' smallest
 // admissible windows (0 if any instance admits none, or FP64).
@@ -153,6 +170,7 @@ void configure(gp_batch b, double scale, std::vector<char> &host) {
         b->window[ax] = all ? w : 0;
     }
     b->contiguous_z = b->window[2] > 0;
+    assign_ztma(b);
     for (Inst &I : b->inst)
         for (int ax = 0; ax < 3; ++ax) {
             // adjacent line pairs on a strided axis (window 4, 8-byte
@@ -202,22 +220,34 @@ gp_status build_set(gp_batch b) {
     LaunchSet &S = b->act;
     for (int i = 0; i < b->n; ++i)
         if (b->inst[i].active) S.members.push_back(i);
+    S.zmaps.assign(2, BatchTmaMaps());
     for (int k = 0; k < 3; ++k) {
         for (int g = 0; g < 2; ++g) {
             std::vector<SweepArgs> args[2];
             std::vector<unsigned> first{0}, gridx;
             for (int i : S.members) {
                 const Inst &I = b->inst[i];
-                if (I.lpt[k] != g + 1) continue;
+                const bool tma = k == 2 && I.ztma;
+                if (k == 2 ? (tma != (g == 1)) : I.lpt[k] != g + 1) continue;
                 for (int p = 0; p < 2; ++p) {
                     // sweep k of a step that starts with psi in buffer I.cur ^ p
                     const int in = I.cur ^ p ^ (k & 1);
-                    args[p].push_back(sweep_args(I.G, k, false, b->d_psi[in] + I.psi_off,
-                                                 b->d_psi[in ^ 1] + I.psi_off, b->d_tab, I.tab, I.seg_len[k],
+                    const char *src = b->d_psi[in] + I.psi_off;
+                    char *dst = b->d_psi[in ^ 1] + I.psi_off;
+                    args[p].push_back(sweep_args(I.G, k, false, src, dst, b->d_tab, I.tab, I.seg_len[k],
                                                  I.n_seg[k], b->d_scal + 2 * i, b->d_partials + I.part_off,
                                                  b->d_counters + i, b->d_scal + 2 * i + 1, b->d_scal + 2 * i));
+                    if (tma) {
+                        const size_t q = args[p].size() - 1;
+                        const long long rows = axis_lines(I.G, 2);
+                        if (!encode_z_map(&S.zmaps[p].in[q], src, I.G.n[2], rows, (int)b->elem) ||
+                            !encode_z_map(&S.zmaps[p].out[q], dst, I.G.n[2], rows, (int)b->elem))
+                            return bfail(b, GP_ERR_CUDA, "encoding a tensor map of the batched z sweep failed");
+                    }
                 }
-                const unsigned gx = sweep_gridx(b, I, k, I.lpt[k]);
+                // TMA: one block per kTmaWarps * 64 rows, as a single-condensate launch
+                const unsigned gx = tma ? (unsigned)((axis_lines(I.G, 2) + kTmaBlockRows - 1) / kTmaBlockRows)
+                                        : sweep_gridx(b, I, k, I.lpt[k]);
                 gridx.push_back(gx);
                 first.push_back(first.back() + gx * (unsigned)I.n_seg[k]);
             }
@@ -234,7 +264,7 @@ gp_status build_set(gp_batch b) {
     std::vector<unsigned> of{0};
     for (int i : S.members) {
         fa.push_back(inst_field_args(b, i));
-        of.push_back(of.back() + (unsigned)observables_blocks(fa.back()));
+        of.push_back(of.back() + (unsigned)observables_body_blocks(fa.back()));
     }
     S.ototal = of.back();
     gp_status st;
@@ -257,8 +287,9 @@ gp_status launch_step(gp_batch b, cudaStream_t s, int parity) {
         L.contiguous = (k == 2 && b->contiguous_z) ? 1 : 0;
         for (int g = 0; g < 2; ++g) {
             if (S.count[k][g] == 0) continue;
-            L.lpt = g + 1;
+            L.lpt = k < 2 ? g + 1 : 1;
             BatchLaunch bl{S.args[k][g][parity], S.first[k][g], S.gridx[k][g], S.count[k][g], S.total[k][g]};
+            if (k == 2 && g == 1) bl.tma = &S.zmaps[parity];
             GPB_CK(b, launch_sweep_batch(L, bl, s));
         }
     }
@@ -415,6 +446,7 @@ gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const doub
         delete b;
         return bfail(nullptr, GP_ERR_CUDA, "no CUDA device");
     }
+    prepare_field_launches();
     b->n = n;
     b->prec = prec;
     b->field = field;
@@ -567,7 +599,8 @@ gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, in
     std::vector<double> host;
     if ((st = observe_active(b, host)) != GP_OK) return st;
     std::vector<double> mu_prev(b->n), e_prev(b->n);
-    std::vector<int> taken(b->n, 0);
+    std::vector<int> taken(b->n, 0), streak(b->n, 0);
+    const int need = b->stop_rule == 2 ? 2 : 1;  // consecutive checks that must pass
     for (int i = 0; i < b->n; ++i) {
         mu_prev[i] = host[(size_t)i * O_COUNT + O_MU];
         e_prev[i] = host[(size_t)i * O_COUNT + O_E];
@@ -586,8 +619,10 @@ gp_status gp_batch_run_imag_until(gp_batch b, double mu_tol, int check_every, in
                 st = bfail(b, GP_ERR_NONFINITE, "instance " + std::to_string(i) + " became non-finite");
                 break;
             }
-            if (std::fabs(o[O_MU] - mu_prev[i]) < mu_tol &&
-                (b->stop_rule == 0 || std::fabs(o[O_E] - e_prev[i]) < mu_tol)) {
+            const bool pass = std::fabs(o[O_MU] - mu_prev[i]) < mu_tol &&
+                              (b->stop_rule == 0 || std::fabs(o[O_E] - e_prev[i]) < mu_tol);
+            streak[i] = pass ? streak[i] + 1 : 0;
+            if (streak[i] >= need) {
                 b->inst[i].active = false;
                 changed = true;
             }
@@ -678,8 +713,27 @@ gp_status gp_batch_run_imag_schedule(gp_batch b, int levels, const double *dt_sc
 
 gp_status gp_batch_set_stop_rule(gp_batch b, int rule) {
     if (!b) return bfail(b, GP_ERR_ARG, "NULL batch");
-    if (rule != 0 && rule != 1) return bfail(b, GP_ERR_ARG, "rule must be 0 or 1");
+    if (rule < 0 || rule > 2) return bfail(b, GP_ERR_ARG, "rule must be 0, 1 or 2");
     b->stop_rule = rule;
+    return GP_OK;
+}
+
+gp_status gp_batch_set_tma(gp_batch b, int on) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    b->use_tma = on != 0;
+    assign_ztma(b);
+    free_set(b);
+    b->dirty = true;
+    return GP_OK;
+}
+
+gp_status gp_batch_get_tma(gp_batch b, int *count) {
+    if (!b || !count) return bfail(b, GP_ERR_ARG, "bad arguments");
+    int c = 0;
+    for (const Inst &I : b->inst) c += I.ztma ? 1 : 0;
+    *count = c;
     return GP_OK;
 }
 

@@ -63,14 +63,16 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
         off = align_up(off + rsz * G.n[ax], 256);
     }
     host.resize(off, 0);
-    // exp(-dt w^2 a^2 / 2) per node of each axis: the trap part of the
-    // imaginary-time kick factorises over the axes; its phase dt w^2 a^2 / 2
-    // is the trap part of the real-time kick's angle, a sum over the axes.
+    // exp(-dt w^2 a^2 / 2) - 1 per node of each axis: the trap part of the
+    // imaginary-time kick factorises over the axes (stored as deviations
+    // from one, which keeps their rounding from acting as a potential error
+    // of u / dt); its phase dt w^2 a^2 / 2 is the trap part of the real-time
+    // kick's angle, a sum over the axes.
     for (int ax = 0; ax < 3; ++ax)
         for (int i = 0; i < G.n[ax]; ++i) {
             const double a = (i - 0.5 * (G.n[ax] - 1)) * G.d[ax];
             const double dv = G.dt * 0.5 * G.w[ax] * G.w[ax] * a * a;
-            put_real(host.data() + T.kick_off[ax] + i * rsz, std::exp(-dv), f32);
+            put_real(host.data() + T.kick_off[ax] + i * rsz, std::expm1(-dv), f32);
             put_real(host.data() + T.phase_off[ax] + i * rsz, dv, f32);
             put_real(host.data() + T.phase_half_off[ax] + i * rsz, 0.5 * dv, f32);
         }

@@ -29,7 +29,7 @@ struct AxisTables {
 
 struct Tables {
     AxisTables ax[2][3];   // [mode: 0 imaginary, 1 real][axis]
-    size_t kick_off[3] = {0, 0, 0};   // exp(-dt w^2 a^2 / 2) per node (imaginary time)
+    size_t kick_off[3] = {0, 0, 0};   // exp(-dt w^2 a^2 / 2) - 1 per node (imaginary time)
     size_t phase_off[3] = {0, 0, 0};  // dt w^2 a^2 / 2 per node (real time)
     size_t phase_half_off[3] = {0, 0, 0};  // the same for dt / 2 (symmetric splitting's half kick)
 };

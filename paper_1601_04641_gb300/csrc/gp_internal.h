@@ -37,9 +37,9 @@ struct SweepArgs {
     double kappa;          // |c| = dt / (4 d^2)
     // kick (K_X): site (i, j, k) with i along the line, (j, k) = (L / nz, L % nz)
     const double *scale;   // pending renormalisation factor applied on load
-    const void *kick_ex;   // imaginary time: exp(-dt V_x(i)) per x node (else null)
-    const void *kick_ey;   //                 exp(-dt V_y(j)) per y node
-    const void *kick_ez;   //                 exp(-dt V_z(k)) per z node
+    const void *kick_ex;   // imaginary time: exp(-dt V_x(i)) - 1 per x node (else null)
+    const void *kick_ey;   //                 exp(-dt V_y(j)) - 1 per y node
+    const void *kick_ez;   //                 exp(-dt V_z(k)) - 1 per z node
     const void *phase_ex;  // real time: dt V_x(i) per x node (else null)
     const void *phase_ey;  //            dt V_y(j) per y node
     const void *phase_ez;  //            dt V_z(k) per z node
@@ -64,13 +64,35 @@ struct TmaMaps {
     CUtensorMap in, out;
 };
 
+// Whether the TMA z sweep serves a line of N nodes of elem_bytes (4 or 8)
+// at window W cut into n_seg segments: whole lines (one segment), rows that
+// start on 16-byte boundaries, a register ring of (chunk + W) pair values
+// within 256 bytes (chunk = 64 bytes of nodes), and at least one chunk plus
+// the window plus two interior nodes.
+inline bool tma_z_fits(int elem_bytes, int W, int N, int n_seg, long long n_lines) {
+    if (elem_bytes != 4 && elem_bytes != 8) return false;
+    const int chunk = 64 / elem_bytes;
+    return W > 0 && (chunk + W) * 2 * elem_bytes <= 256 && n_seg == 1 && N - 2 >= chunk + W + 2 &&
+           ((long long)N * elem_bytes) % 16 == 0 && n_lines > 0 && n_lines <= 0x7fffffffLL;
+}
+
+// Tensor maps of a batched TMA z sweep: instance q of the launch (its
+// position in the launch's argument array) reads rows through in[q] and
+// writes them through out[q].  Passed by value as one kernel parameter
+// block (16 KB at 64 instances, within the 32 KB parameter limit).
+constexpr int kTmaBatch = 64;
+constexpr int kTmaBlockRows = 256;  // z lines per block of the TMA z sweep
+struct BatchTmaMaps {
+    CUtensorMap in[kTmaBatch], out[kTmaBatch];
+};
+
 struct SweepLaunch {
     Prec prec;
     Form form;
     Kind kind;
     int window;            // 4, 8, 16, or 0 for the exact two-pass solve
     int threads;           // threads per block
-    int lpt;               // lines per thread of the strided kernel (1, or 2 adjacent lines)
+    int lpt;               // lines per thread of the strided kernel (1, or 2 or 4 adjacent lines)
     int contiguous;        // 1: warp-tiled kernel for the stride-1 axis
     const TmaMaps *tma = nullptr;  // z sweep through TMA tiles where the grid allows it
 };
@@ -101,6 +123,9 @@ struct FieldArgs {
 cudaError_t launch_gaussian(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s);
 cudaError_t launch_norm(Prec p, bool cplx, const FieldArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_observables(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s);
+// Look up, once per device, the launch shapes the field kernels take from
+// the device (call from the current device, outside any stream capture).
+void prepare_field_launches();
 cudaError_t launch_apply_scale(Prec p, bool cplx, const FieldArgs &a, void *dst, cudaStream_t s);
 // Real-time kick exp(-i kdt (V + g |psi|^2)) of a complex field into dst.
 cudaError_t launch_kick(Prec p, const FieldArgs &a, double kdt, void *dst, cudaStream_t s);
@@ -112,7 +137,11 @@ enum ObsSlot {
     O_COUNT = 16
 };
 
+// The most blocks (partials) any observables launch over this field uses.
 int observables_blocks(const FieldArgs &a);
+// Blocks of the per-(j, k) observables kernels over one condensate (also one
+// condensate's share of the batched observables launch).
+int observables_body_blocks(const FieldArgs &a);
 cudaError_t launch_observables_batch(Prec p, bool cplx, const FieldArgs *args, const unsigned *first, int n,
                                      unsigned total_blocks, cudaStream_t s);
 
@@ -125,6 +154,7 @@ struct BatchLaunch {
     const unsigned *gridx;
     int n;
     unsigned total_blocks;
+    const BatchTmaMaps *tma = nullptr;  // z sweep through TMA (n <= kTmaBatch instances that fit)
 };
 cudaError_t launch_sweep_batch(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s);
 // Threads per block of the batched kernels.

@@ -63,20 +63,27 @@ __device__ __forceinline__ cx<double> ldc(const cx<double> *p) {
     return cx<double>{v.x, v.y};
 }
 
-__device__ __forceinline__ float g_exp(float x) { return expf(x); }
-__device__ __forceinline__ double g_exp(double x) { return exp(x); }
+__device__ __forceinline__ float g_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double g_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ void g_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void g_sincos(double x, double *s, double *c) { sincos(x, s, c); }
 
 // Short Taylor polynomials for the kick's small arguments (textbook series,
 // Horner form).  Each is used only where its truncation error is below a
-// quarter of the unit roundoff; larger arguments fall back to exp / sincos.
+// quarter of the unit roundoff of the factor it forms; larger arguments fall
+// back to expm1 / sincos.
 //   FP32: sin through x^5, cos through x^6 for |x| <= 0.2 (next terms
-//         x^7/7!, x^8/8! below 2^-26 relative); exp(-y) through y^4 for
-//         |y| <= 0.05 (next term below 2^-27).
+//         x^7/7!, x^8/8! below 2^-26 relative); exp(-y) - 1 through y^4 for
+//         |y| <= 0.05 (next term below 2^-27 of exp(-y)).
 //   FP64: sin through x^9, cos through x^10 for |x| <= 0.1 (next terms below
-//         2^-58 relative); exp(-y) through y^7 for |y| <= 0.02 (next term
-//         below 2^-60).
+//         2^-58 relative); exp(-y) - 1 through y^7 for |y| <= 0.02 (next
+//         term below 2^-60 of exp(-y)).
+// Imaginary-time factors are formed as deviations from one (exp(-y) - 1,
+// and the trap tables hold exp(-dt V_a) - 1): a factor rounded once near one
+// and applied at every step acts as a potential error of u / dt (u the unit
+// roundoff), the same at every step, which shifts the FP32 fixed point (by
+// about 7e-6 of mu on the 480x400x320 grid at dt = 0.1 d^2); a deviation
+// rounded once is off by u |dt V|, a potential error of u |V|.
 template <typename R> struct Series;
 template <> struct Series<float> {
     static constexpr float kTrig = 0.2f, kExp = 0.05f;
@@ -85,8 +92,8 @@ template <> struct Series<float> {
         *sn = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
         *cs = fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f), 1.f);
     }
-    __device__ __forceinline__ static float expm(float y) {  // exp(-y)
-        return fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.f / 24.f, -1.f / 6.f), 0.5f), -1.f), 1.f);
+    __device__ __forceinline__ static float expm1m(float y) {  // exp(-y) - 1
+        return y * fmaf(y, fmaf(y, fmaf(y, 1.f / 24.f, -1.f / 6.f), 0.5f), -1.f);
     }
 };
 template <> struct Series<double> {
@@ -98,10 +105,9 @@ template <> struct Series<double> {
         *cs = fma(x2, fma(x2, fma(x2, fma(x2, fma(x2, -1.0 / 3628800.0, 1.0 / 40320.0), -1.0 / 720.0),
                                   1.0 / 24.0), -0.5), 1.0);
     }
-    __device__ __forceinline__ static double expm(double y) {  // exp(-y)
-        return fma(y, fma(y, fma(y, fma(y, fma(y, fma(y, fma(y, -1.0 / 5040.0, 1.0 / 720.0),
-                                                         -1.0 / 120.0), 1.0 / 24.0), -1.0 / 6.0),
-                                  0.5), -1.0), 1.0);
+    __device__ __forceinline__ static double expm1m(double y) {  // exp(-y) - 1
+        return y * fma(y, fma(y, fma(y, fma(y, fma(y, fma(y, -1.0 / 5040.0, 1.0 / 720.0), -1.0 / 120.0),
+                                              1.0 / 24.0), -1.0 / 6.0), 0.5), -1.0);
     }
 };
 // The library functions are called out of line: every load site of the x
@@ -112,7 +118,7 @@ template <typename R> __device__ __noinline__ cx<R> sincos_full(R x) {
     g_sincos(x, &r.im, &r.re);
     return r;
 }
-template <typename R> __device__ __noinline__ R expm_full(R y) { return g_exp(-y); }
+template <typename R> __device__ __noinline__ R expm1m_full(R y) { return g_expm1(-y); }
 template <typename R> __device__ __forceinline__ void kick_sincos(R x, R *sn, R *cs) {
     if (fabs(x) <= Series<R>::kTrig) {
         Series<R>::sincos(x, sn, cs);
@@ -122,20 +128,30 @@ template <typename R> __device__ __forceinline__ void kick_sincos(R x, R *sn, R 
         *cs = r.re;
     }
 }
-template <typename R> __device__ __forceinline__ R kick_expm(R y) {
-    return fabs(y) <= Series<R>::kExp ? Series<R>::expm(y) : expm_full(y);
+// exp(-y) - 1
+template <typename R> __device__ __forceinline__ R kick_expm1m(R y) {
+    return fabs(y) <= Series<R>::kExp ? Series<R>::expm1m(y) : expm1m_full(y);
+}
+// Deviation from one of the imaginary-time kick factor
+// (1 + ex)(1 + eyz)(1 + m): the trap part of the node and line, then the
+// nonlinear part m = exp(-dt g |q|^2) - 1.
+template <typename R> __device__ __forceinline__ R kick_dev(R ex, R eyz, R m) {
+    const R t = fma(ex, eyz, ex + eyz);
+    return fma(t, m, t + m);
 }
 
 // Per-site kick state of one x line.  Imaginary time: exp(-dt V) is the
-// product of per-axis factors exp(-dt V_x(i)) (a table) and
-// exp(-dt (V_y(j) + V_z(k))) (fixed along the line), times exp(-dt g |psi|^2).
+// product of per-axis factors exp(-dt V_x(i)) (a table of deviations from
+// one) and exp(-dt (V_y(j) + V_z(k))) (fixed along the line, held as its
+// deviation from one), times exp(-dt g |psi|^2); the kicked value is
+// q + q D with D the product's deviation from one (kick_dev).
 // Real time: theta = dt V_x(i) (a table) + dt (V_y(j) + V_z(k)) (fixed along
 // the line) + dt g |psi|^2, and exp(-i theta).
 template <typename R> struct KickState {
     R s;              // pending renormalisation factor
     R dtg;            // dt * g
-    R eyz;            // exp(-dt (V_y + V_z)) of the line (imaginary time)
-    const R *ex;      // exp(-dt V_x(i)) per node (imaginary time)
+    R eyz;            // exp(-dt (V_y + V_z)) - 1 of the line (imaginary time)
+    const R *ex;      // exp(-dt V_x(i)) - 1 per node (imaginary time)
     R pyz;            // dt (V_y + V_z) of the line (real time)
     const R *px;      // dt V_x(i) per node (real time)
     R xo, xd, xc;     // x(i) = xo + i xd and dt V_x(i) = xc x(i)^2 (real time, computed in place)
@@ -166,7 +182,7 @@ template <> struct Acc<float> {
 // for one line; the packed pair forms keep the two lines' values in
 // component-wise float2 registers.
 template <typename V_> struct LineForm {
-    static constexpr bool kPair = false;
+    static constexpr int kLines = 1;
     static constexpr bool kChunkKick = false;  // kick_chunk: a chunk of nodes kicked at once
     using MemV = V_;
     __device__ __forceinline__ static V_ load(MemV m) { return m; }
@@ -194,7 +210,7 @@ template <typename R> struct FImagReal : LineForm<R> {
     __device__ __forceinline__ static R abs2(V v) { return v * v; }
     __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
         const V q = p * k.s;
-        return q * (__ldg(k.ex + node) * k.eyz * kick_expm(k.dtg * (q * q)));
+        return fma(q, kick_dev(__ldg(k.ex + node), k.eyz, kick_expm1m(k.dtg * (q * q))), q);
     }
     // kick of NB consecutive nodes from node0: table loads issued together,
     // one series-range test per group, values equal kick's
@@ -215,7 +231,7 @@ template <typename R> struct FImagReal : LineForm<R> {
             }
             if (small) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) v[g0 + i] = q[i] * (ex[i] * k.eyz * Series<R>::expm(y[i]));
+                for (int i = 0; i < G; ++i) v[g0 + i] = fma(q[i], kick_dev(ex[i], k.eyz, Series<R>::expm1m(y[i])), q[i]);
             } else {
 #pragma unroll
                 for (int i = 0; i < G; ++i) v[g0 + i] = kick(v[g0 + i], k, node0 + g0 + i);
@@ -244,8 +260,8 @@ template <typename R> struct FImagCplx : LineForm<cx<R>> {
     __device__ __forceinline__ static R abs2(V v) { return fma(v.re, v.re, v.im * v.im); }
     __device__ __forceinline__ static V kick(V p, const KickState<R> &k, int node) {
         const V q{p.re * k.s, p.im * k.s};
-        const R f = __ldg(k.ex + node) * k.eyz * kick_expm(k.dtg * abs2(q));
-        return V{q.re * f, q.im * f};
+        const R f = kick_dev(__ldg(k.ex + node), k.eyz, kick_expm1m(k.dtg * abs2(q)));
+        return V{fma(q.re, f, q.re), fma(q.im, f, q.im)};
     }
     static constexpr bool kChunkKick = true;
     template <int NB> __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<R> &k, int node0) {
@@ -266,8 +282,8 @@ template <typename R> struct FImagCplx : LineForm<cx<R>> {
             if (small) {
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
-                    const R f = ex[i] * k.eyz * Series<R>::expm(y[i]);
-                    v[g0 + i] = V{q[i].re * f, q[i].im * f};
+                    const R f = kick_dev(ex[i], k.eyz, Series<R>::expm1m(y[i]));
+                    v[g0 + i] = V{fma(q[i].re, f, q[i].re), fma(q[i].im, f, q[i].im)};
                 }
             } else {
 #pragma unroll
@@ -349,7 +365,7 @@ template <class F> struct FPair {
     using E = typename F::V;
     struct __align__(2 * sizeof(E)) V { E a, b; };
     using C = typename F::C;
-    static constexpr bool kPair = true;
+    static constexpr int kLines = 2;
     using MemV = V;
     __device__ __forceinline__ static V load(MemV m) { return m; }
     __device__ __forceinline__ static MemV store(V v) { return v; }
@@ -400,7 +416,7 @@ struct PRealTimeF {
     using C = cx<float>;
     struct __align__(16) V { float2 re, im; };  // (line a, line b) per component
     using MemV = typename FPair<F>::V;
-    static constexpr bool kPair = true;
+    static constexpr int kLines = 2;
     __device__ __forceinline__ static V load(MemV m) {
         return V{make_float2(m.a.re, m.b.re), make_float2(m.a.im, m.b.im)};
     }
@@ -497,9 +513,14 @@ struct PRealTimeF {
     }
 };
 
-// exp(-y) by the FP32 series of Series<float>::expm, on two lines at once.
-__device__ __forceinline__ float2 expm_series2(float2 y) {
-    return fma2(y, fma2(y, fma2(y, fma2(y, dup2(1.f / 24.f), dup2(-1.f / 6.f)), dup2(0.5f)), dup2(-1.f)), dup2(1.f));
+// exp(-y) - 1 by the FP32 series of Series<float>::expm1m, on two lines at once.
+__device__ __forceinline__ float2 expm1m_series2(float2 y) {
+    return mul2(y, fma2(y, fma2(y, fma2(y, dup2(1.f / 24.f), dup2(-1.f / 6.f)), dup2(0.5f)), dup2(-1.f)));
+}
+// kick_dev on two lines: the node's x deviation ex, the lines' deviations eyz.
+__device__ __forceinline__ float2 kick_dev2(float ex, float2 eyz, float2 m) {
+    const float2 t = fma2(dup2(ex), eyz, add2(dup2(ex), eyz));
+    return fma2(t, m, add2(t, m));
 }
 
 // Packed FP32 pairs of the imaginary-time forms, in the same operation order
@@ -510,7 +531,7 @@ struct PImagRealF {
     using C = float;
     using V = float2;                     // (line a, line b)
     using MemV = typename FPair<F>::V;
-    static constexpr bool kPair = true;
+    static constexpr int kLines = 2;
     __device__ __forceinline__ static V load(MemV m) { return make_float2(m.a, m.b); }
     __device__ __forceinline__ static MemV store(V v) { return MemV{v.x, v.y}; }
     __device__ __forceinline__ static V zero() { return dup2(0.f); }
@@ -534,17 +555,18 @@ struct PImagRealF {
     __device__ __forceinline__ static bool kick_small(float2 y) {
         return fabs(y.x) <= Series<float>::kExp && fabs(y.y) <= Series<float>::kExp;
     }
+    // q + q D, D the kick factor's deviation from one (m = exp(-y) - 1).
     __device__ __forceinline__ static V kick_apply(float2 q, float ex, const KickState<float> &ka,
-                                                   const KickState<float> &kb, float2 e) {
-        return mul2(q, mul2(mul2(dup2(ex), make_float2(ka.eyz, kb.eyz)), e));
+                                                   const KickState<float> &kb, float2 m) {
+        return fma2(q, kick_dev2(ex, make_float2(ka.eyz, kb.eyz), m), q);
     }
     __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
                                               int node) {
         float2 q;
         const float2 y = kick_arg(p, ka, q);
         const float ex = __ldg(ka.ex + node);
-        if (kick_small(y)) return kick_apply(q, ex, ka, kb, expm_series2(y));
-        return kick_apply(q, ex, ka, kb, make_float2(kick_expm(y.x), kick_expm(y.y)));
+        if (kick_small(y)) return kick_apply(q, ex, ka, kb, expm1m_series2(y));
+        return kick_apply(q, ex, ka, kb, make_float2(kick_expm1m(y.x), kick_expm1m(y.y)));
     }
     static constexpr bool kChunkKick = true;
     template <int NB>
@@ -565,7 +587,7 @@ struct PImagRealF {
             }
             if (small) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) v[g0 + i] = kick_apply(q[i], ex[i], ka, kb, expm_series2(y[i]));
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick_apply(q[i], ex[i], ka, kb, expm1m_series2(y[i]));
             } else {
 #pragma unroll
                 for (int i = 0; i < G; ++i) v[g0 + i] = kick2(v[g0 + i], ka, kb, node0 + g0 + i);
@@ -580,7 +602,7 @@ struct PImagCplxF {
     using C = float;
     struct __align__(16) V { float2 re, im; };  // (line a, line b) per component
     using MemV = typename FPair<F>::V;
-    static constexpr bool kPair = true;
+    static constexpr int kLines = 2;
     __device__ __forceinline__ static V load(MemV m) {
         return V{make_float2(m.a.re, m.b.re), make_float2(m.a.im, m.b.im)};
     }
@@ -610,17 +632,17 @@ struct PImagCplxF {
         return mul2(dup2(ka.dtg), fma2(q.re, q.re, mul2(q.im, q.im)));
     }
     __device__ __forceinline__ static V kick_apply(V q, float ex, const KickState<float> &ka,
-                                                   const KickState<float> &kb, float2 e) {
-        const float2 f = mul2(mul2(dup2(ex), make_float2(ka.eyz, kb.eyz)), e);
-        return V{mul2(q.re, f), mul2(q.im, f)};
+                                                   const KickState<float> &kb, float2 m) {
+        const float2 f = kick_dev2(ex, make_float2(ka.eyz, kb.eyz), m);
+        return V{fma2(q.re, f, q.re), fma2(q.im, f, q.im)};
     }
     __device__ __forceinline__ static V kick2(V p, const KickState<float> &ka, const KickState<float> &kb,
                                               int node) {
         V q;
         const float2 y = kick_arg(p, ka, q);
         const float ex = __ldg(ka.ex + node);
-        if (PImagRealF::kick_small(y)) return kick_apply(q, ex, ka, kb, expm_series2(y));
-        return kick_apply(q, ex, ka, kb, make_float2(kick_expm(y.x), kick_expm(y.y)));
+        if (PImagRealF::kick_small(y)) return kick_apply(q, ex, ka, kb, expm1m_series2(y));
+        return kick_apply(q, ex, ka, kb, make_float2(kick_expm1m(y.x), kick_expm1m(y.y)));
     }
     static constexpr bool kChunkKick = true;
     template <int NB>
@@ -642,10 +664,76 @@ struct PImagCplxF {
             }
             if (small) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) v[g0 + i] = kick_apply(q[i], ex[i], ka, kb, expm_series2(y[i]));
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick_apply(q[i], ex[i], ka, kb, expm1m_series2(y[i]));
             } else {
 #pragma unroll
                 for (int i = 0; i < G; ++i) v[g0 + i] = kick2(v[g0 + i], ka, kb, node0 + g0 + i);
+            }
+        }
+    }
+};
+
+// Four adjacent lines of a real field in imaginary time: lines (0, 1) in
+// the first float2 and (2, 3) in the second, every operation PImagRealF's
+// on both halves (results equal the scalar form's).  A node of the four
+// lines is one 16-byte access, so each row a warp reads or writes on a
+// strided axis is 512 contiguous bytes instead of the pair form's 256.
+struct PImagRealQ {
+    using Real = float;
+    using F = FImagReal<float>;
+    using C = float;
+    using P = PImagRealF;
+    struct __align__(16) V { float2 a, b; };
+    struct __align__(16) MemV { float x, y, z, w; };
+    static constexpr int kLines = 4;
+    static constexpr bool kChunkKick = true;
+    __device__ __forceinline__ static V load(MemV m) { return V{make_float2(m.x, m.y), make_float2(m.z, m.w)}; }
+    __device__ __forceinline__ static MemV store(V v) { return MemV{v.a.x, v.a.y, v.b.x, v.b.y}; }
+    __device__ __forceinline__ static V zero() { return V{dup2(0.f), dup2(0.f)}; }
+    __device__ __forceinline__ static V rhs(V pm, V p0, V p1, float k) {
+        return V{P::rhs(pm.a, p0.a, p1.a, k), P::rhs(pm.b, p0.b, p1.b, k)};
+    }
+    __device__ __forceinline__ static V fwd(V r, V dprev, float k, C ipm1) {
+        return V{P::fwd(r.a, dprev.a, k, ipm1), P::fwd(r.b, dprev.b, k, ipm1)};
+    }
+    __device__ __forceinline__ static V back(V dp, C cp, V phi) {
+        return V{P::back(dp.a, cp, phi.a), P::back(dp.b, cp, phi.b)};
+    }
+    __device__ __forceinline__ static float abs2(V v) { return P::abs2(v.a) + P::abs2(v.b); }
+    // Kick of the four lines (scale, dt g and the x factor shared; the line
+    // factors exp(-dt (V_y + V_z)) from each line's state).
+    __device__ __forceinline__ static V kick4(V p, const KickState<float> (&k)[4], int node) {
+        float2 qa, qb;
+        const float2 ya = P::kick_arg(p.a, k[0], qa), yb = P::kick_arg(p.b, k[0], qb);
+        const float ex = __ldg(k[0].ex + node);
+        const float2 ea = P::kick_small(ya) ? expm1m_series2(ya) : make_float2(kick_expm1m(ya.x), kick_expm1m(ya.y));
+        const float2 eb = P::kick_small(yb) ? expm1m_series2(yb) : make_float2(kick_expm1m(yb.x), kick_expm1m(yb.y));
+        return V{P::kick_apply(qa, ex, k[0], k[1], ea), P::kick_apply(qb, ex, k[2], k[3], eb)};
+    }
+    template <int NB>
+    __device__ __forceinline__ static void kick_chunk(V (&v)[NB], const KickState<float> (&k)[4], int node0) {
+#pragma unroll
+        for (int g0 = 0; g0 < NB; g0 += kKickGroup) {
+            constexpr int G = NB < kKickGroup ? NB : kKickGroup;
+            float ex[G];
+            float2 qa[G], qb[G], ya[G], yb[G];
+            bool small = true;
+#pragma unroll
+            for (int i = 0; i < G; ++i) ex[i] = __ldg(k[0].ex + node0 + g0 + i);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                ya[i] = P::kick_arg(v[g0 + i].a, k[0], qa[i]);
+                yb[i] = P::kick_arg(v[g0 + i].b, k[0], qb[i]);
+                small = small && P::kick_small(ya[i]) && P::kick_small(yb[i]);
+            }
+            if (small) {
+#pragma unroll
+                for (int i = 0; i < G; ++i)
+                    v[g0 + i] = V{P::kick_apply(qa[i], ex[i], k[0], k[1], expm1m_series2(ya[i])),
+                                  P::kick_apply(qb[i], ex[i], k[2], k[3], expm1m_series2(yb[i]))};
+            } else {
+#pragma unroll
+                for (int i = 0; i < G; ++i) v[g0 + i] = kick4(v[g0 + i], k, node0 + g0 + i);
             }
         }
     }
@@ -656,6 +744,10 @@ template <class F> struct PairForm { using type = FPair<F>; };
 template <> struct PairForm<FRealTime<float>> { using type = PRealTimeF; };
 template <> struct PairForm<FImagReal<float>> { using type = PImagRealF; };
 template <> struct PairForm<FImagCplx<float>> { using type = PImagCplxF; };
+// The four-line form of a single-line form, where there is one.
+template <class F> struct QuadForm { using type = void; };
+template <> struct QuadForm<FImagReal<float>> { using type = PImagRealQ; };
+template <class F> constexpr bool has_quad() { return !std::is_void<typename QuadForm<F>::type>::value; }
 
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
@@ -886,8 +978,12 @@ template <typename R, int KIND> __device__ __forceinline__ void kick_init(KickSt
     k.s = (R)__ldg(a.scale);
     k.dtg = (R)(a.dt * a.g);
     k.ex = static_cast<const R *>(a.kick_ex);
-    k.eyz = a.kick_ex ? __ldg(static_cast<const R *>(a.kick_ey) + j) * __ldg(static_cast<const R *>(a.kick_ez) + kk)
-                      : R(1);
+    if (a.kick_ex) {
+        const R ey = __ldg(static_cast<const R *>(a.kick_ey) + j), ez = __ldg(static_cast<const R *>(a.kick_ez) + kk);
+        k.eyz = fma(ey, ez, ey + ez);  // (1 + ey)(1 + ez) - 1
+    } else {
+        k.eyz = R(0);
+    }
     k.px = static_cast<const R *>(a.phase_ex);
     k.pyz = a.phase_ex ? __ldg(static_cast<const R *>(a.phase_ey) + j) + __ldg(static_cast<const R *>(a.phase_ez) + kk)
                        : R(0);
@@ -896,31 +992,36 @@ template <typename R, int KIND> __device__ __forceinline__ void kick_init(KickSt
     k.xc = (R)(a.dt * a.half_w2[0]);
 }
 
-// F is the single-line form; M is F (one line per thread) or its pair form.
+// F is the single-line form; M is F (one line per thread) or its pair or
+// quad form.
 template <class F, class M, typename R, int KIND> struct Hooks {
     using V = typename M::V;
-    KickState<R> ka, kb;
+    static constexpr int NL = M::kLines;
+    KickState<R> k[NL];
     Acc<R> *acc;
     __device__ __forceinline__ void init(const SweepArgs &a, long long L) {
         if (KIND == K_X) {
-            kick_init<R, KIND>(ka, a, L);
-            if constexpr (M::kPair) kick_init<R, KIND>(kb, a, L + 1);
+#pragma unroll
+            for (int q = 0; q < NL; ++q) kick_init<R, KIND>(k[q], a, L + q);
         }
     }
     __device__ __forceinline__ V on_load(int p, V v) const {
         if constexpr (KIND == K_X) {
-            if constexpr (M::kPair) v = M::kick2(v, ka, kb, p + 1);
-            else v = F::kick(v, ka, p + 1);
+            if constexpr (NL == 4) v = M::kick4(v, k, p + 1);
+            else if constexpr (NL == 2) v = M::kick2(v, k[0], k[1], p + 1);
+            else v = F::kick(v, k[0], p + 1);
         }
         return v;
     }
     // on_load of NB consecutive positions p .. p+NB-1.
     template <int NB> __device__ __forceinline__ void on_load_chunk(int p, V (&v)[NB]) const {
         if constexpr (KIND == K_X) {
-            if constexpr (M::kChunkKick && M::kPair) {
-                M::template kick_chunk<NB>(v, ka, kb, p + 1);
+            if constexpr (NL == 4) {
+                M::template kick_chunk<NB>(v, k, p + 1);
+            } else if constexpr (M::kChunkKick && NL == 2) {
+                M::template kick_chunk<NB>(v, k[0], k[1], p + 1);
             } else if constexpr (M::kChunkKick) {
-                M::template kick_chunk<NB>(v, ka, p + 1);
+                M::template kick_chunk<NB>(v, k[0], p + 1);
             } else {
 #pragma unroll
                 for (int q = 0; q < NB; ++q) v[q] = on_load(p + q, v[q]);
@@ -1010,9 +1111,10 @@ template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
 
 template <class F, int LPT> struct LinesPerThread { using M = F; };
 template <class F> struct LinesPerThread<F, 2> { using M = typename PairForm<F>::type; };
+template <class F> struct LinesPerThread<F, 4> { using M = typename QuadForm<F>::type; };
 
-// One thread per (line, segment), or per (pair of adjacent lines, segment)
-// when LPT = 2; blockIdx.y is the segment.  Window 0 selects the exact
+// One thread per (line, segment), or per (group of LPT = 2 or 4 adjacent
+// lines, segment); blockIdx.y is the segment.  Window 0 selects the exact
 // two-pass form over whole lines with direct access.
 template <class F, typename R, int W, int KIND, int LPT>
 __device__ __forceinline__ double lines_body(const SweepArgs &a, unsigned bx, unsigned seg,

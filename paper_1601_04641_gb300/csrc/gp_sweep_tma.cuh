@@ -47,6 +47,7 @@ constexpr int kTmaRowBytes = 64;                     // one box row = one swizzl
 constexpr int kTmaBoxBytes = kTmaRows * kTmaRowBytes;
 constexpr int kTmaAhead = 3;                         // boxes in flight beyond the one needed
 constexpr long long kTmaSpinCycles = 1LL << 31;
+static_assert(kTmaWarps * kTmaRows == kTmaBlockRows, "rows per block of the TMA z sweep");
 
 template <typename E> __host__ __device__ constexpr int tma_chunk() { return kTmaRowBytes / (int)sizeof(E); }
 // Ring slots: a chunk reads up to (W + B + 1) / B boxes past its own, two more
@@ -76,8 +77,8 @@ template <class F, int W> inline bool tma_usable(const SweepArgs &a) {
     if constexpr (!tma_supported<F, W>()) {
         return false;
     } else {
-        return a.n_seg == 1 && a.N - 2 >= tma_chunk<E>() + W + 2 && ((long long)a.N * sizeof(E)) % 16 == 0 &&
-               a.n_lines <= 0x7fffffffLL;
+        static_assert(tma_chunk<E>() == 64 / (int)sizeof(E), "tma_z_fits assumes 64-byte box rows");
+        return tma_z_fits((int)sizeof(E), W, a.N, a.n_seg, a.n_lines);
     }
 }
 
@@ -353,6 +354,30 @@ __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap
         if (lane == 0 && a.status) atomicOr(a.status, 1u);
     }
     return acc.value();
+}
+
+// Many condensates in one launch: instance q owns blocks [first[q], first[q+1])
+// (one block per 256 rows of its own grid) and its tensor maps maps.in[q],
+// maps.out[q]; each instance's norm is reduced over its own blocks, in the
+// same order as a single-condensate launch.
+template <class F, typename R, int W>
+__global__ void __launch_bounds__(kTmaWarps * 32, 1) batch_tma_kernel(BatchDesc d,
+                                                                     const __grid_constant__ BatchTmaMaps maps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                            ~static_cast<uintptr_t>(1023));
+    constexpr int S = tma_slots<typename F::V, W>();
+    const int q = find_instance(d, blockIdx.x);
+    const SweepArgs a = d.args[q];
+    const unsigned local = blockIdx.x - __ldg(d.first + q);
+    const unsigned nblocks = __ldg(d.first + q + 1) - __ldg(d.first + q);
+    const int warp = threadIdx.x >> 5;
+    const long long L0 = ((long long)local * kTmaWarps + warp) * kTmaRows;
+    double v = 0.0;
+    if (L0 < a.n_lines)
+        v = tma_body<F, R, W>(a, &maps.in[q], &maps.out[q], base + warp * S * kTmaBoxBytes,
+                              smem_u32(base + kTmaWarps * S * kTmaBoxBytes) + 8 * S * warp, (int)L0);
+    norm_finalize(v, a, local, nblocks);
 }
 
 template <class F, typename R, int W>

@@ -2,6 +2,9 @@
 // observables reduction (calcrms, calcmuen) and applying a pending scale.
 #include "gp_sweep.cuh"
 
+#include <algorithm>
+#include <atomic>
+
 namespace gpcn {
 
 namespace {
@@ -201,6 +204,30 @@ template <typename R> __device__ __forceinline__ Acc<R> acc_sum(const Acc<R> &a,
     return r;
 }
 
+// The observables from the 9 grid sums t (ObsSlot order) into a.out:
+// norm = dV sum|psi|^2, kinetic = dV/2 sum_a (link sum_a)/d_a^2, potential
+// dV sum V|psi|^2, interaction dV sum|psi|^4; mu = (K + P + g I)/norm,
+// E = (K + P + g I/2)/norm, rms_a = sqrt(dV sum a^2|psi|^2 / norm).
+__device__ __forceinline__ void obs_finish(const FieldArgs &a, const double *t) {
+    double *o = a.out;
+    for (int q = 0; q < 9; ++q) o[q] = t[q];
+    const double dv = a.dV;
+    const double nrm = dv * t[O_RHO];
+    const double kin = 0.5 * dv * (t[O_LX] / (a.d[0] * a.d[0]) + t[O_LY] / (a.d[1] * a.d[1]) +
+                                   t[O_LZ] / (a.d[2] * a.d[2]));
+    const double pot = dv * t[O_V];
+    const double inter = dv * t[O_RHO2];
+    o[O_NORM] = nrm;
+    o[O_MU] = (kin + pot + a.g * inter) / nrm;
+    o[O_E] = (kin + pot + 0.5 * a.g * inter) / nrm;
+    o[O_RMSX] = sqrt(dv * t[O_X2] / nrm);
+    o[O_RMSY] = sqrt(dv * t[O_Y2] / nrm);
+    o[O_RMSZ] = sqrt(dv * t[O_Z2] / nrm);
+    bool fin = true;
+    for (int q = 0; q < 15; ++q) fin = fin && isfinite(o[q]);
+    o[O_FINITE] = fin ? 1.0 : 0.0;
+}
+
 template <typename R, bool CPLX>
 __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned block, unsigned nblocks) {
     using E = Elem<R, CPLX>;
@@ -214,7 +241,7 @@ __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned bl
     enum { S_RHO, S_X2, S_RHO2, S_LX, S_LY, S_LZ, S_N };
     Acc<R> sum[S_N];
     Acc<R> acc[9];
-    if (L < plane) {
+    if (L < plane && i0 < i1) {
         const int j = (int)(L / a.n[2]), k = (int)(L % a.n[2]);
         const R x0 = (R)a.origin[0], dx = (R)a.d[0];
         const bool has_y = j + 1 < a.n[1], has_z = k + 1 < a.n[2];
@@ -283,25 +310,7 @@ __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned bl
 #pragma unroll
         for (int q = 0; q < 9; ++q) bs[q] = block_sum(acc[q].value(), red);
     }
-    finalize_partials<9>(bs, a, [&](const double *t) {
-        double *o = a.out;
-        for (int q = 0; q < 9; ++q) o[q] = t[q];
-        const double dv = a.dV;
-        const double nrm = dv * t[O_RHO];
-        const double kin = 0.5 * dv * (t[O_LX] / (a.d[0] * a.d[0]) + t[O_LY] / (a.d[1] * a.d[1]) +
-                                       t[O_LZ] / (a.d[2] * a.d[2]));
-        const double pot = dv * t[O_V];
-        const double inter = dv * t[O_RHO2];
-        o[O_NORM] = nrm;
-        o[O_MU] = (kin + pot + a.g * inter) / nrm;
-        o[O_E] = (kin + pot + 0.5 * a.g * inter) / nrm;
-        o[O_RMSX] = sqrt(dv * t[O_X2] / nrm);
-        o[O_RMSY] = sqrt(dv * t[O_Y2] / nrm);
-        o[O_RMSZ] = sqrt(dv * t[O_Z2] / nrm);
-        bool fin = true;
-        for (int q = 0; q < 15; ++q) fin = fin && isfinite(o[q]);
-        o[O_FINITE] = fin ? 1.0 : 0.0;
-    }, block, nblocks);
+    finalize_partials<9>(bs, a, [&](const double *t) { obs_finish(a, t); }, block, nblocks);
 }
 
 template <typename R, bool CPLX>
@@ -314,6 +323,155 @@ __global__ void __launch_bounds__(kReduceThreads) observables_kernel(FieldArgs a
 // showed it issue- and occupancy-bound).
 __global__ void __launch_bounds__(kReduceThreads, 3) observables_c64_kernel(FieldArgs a) {
     observables_body<float, true>(a, blockIdx.x, gridDim.x);
+}
+
+// Observables of a complex64 field with nz even.  One thread per (j, pair
+// of z nodes k, k+1) walks along i: each pair is one 16-byte load, read
+// once from DRAM (the +y neighbours come back through L2, the +z neighbour
+// k+2 through L1), and the pair's arithmetic is packed FP32x2, one node per
+// component.  The sums are observables_body's: |psi|^2 per node of the pair
+// (the y^2, z^2 and potential sums follow per work item), x^2 |psi|^2,
+// |psi|^4 and the three link sums; FP32 over kObsFold planes, then added to
+// compensated per-thread totals.  Work items (kObsZSeg planes x 256 pairs of
+// a plane) go to the blocks in a fixed grid-stride order over one resident
+// wave, so the summation order is fixed for a given grid.
+constexpr int kObsZSeg = 32;    // planes per work item
+constexpr int kObsPlanes = 4;   // planes whose loads are issued together
+constexpr int kObsFold = 8;     // planes summed in FP32 before a compensated fold
+static_assert(kObsZSeg % kObsFold == 0 && kObsFold % kObsPlanes == 0, "work item shape");
+
+__host__ __device__ inline long long obs_c64z_items(const int n[3]) {
+    const long long units = (long long)n[1] * n[2] / 2;
+    return (units + kReduceThreads - 1) / kReduceThreads * ((n[0] + kObsZSeg - 1) / kObsZSeg);
+}
+
+__global__ void __launch_bounds__(kReduceThreads, 2) observables_c64z_kernel(FieldArgs a) {
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const long long units = (long long)ny * nz / 2;          // z pairs per plane
+    const long long pst = units;                             // plane stride in float4
+    const unsigned pblocks = (unsigned)((units + kReduceThreads - 1) / kReduceThreads);
+    const unsigned items = (unsigned)obs_c64z_items(a.n);
+    const float4 *psi4 = static_cast<const float4 *>(a.psi);
+    const float x0 = (float)a.origin[0], dx = (float)a.d[0];
+    Acc<float> rho, y2, z2, x2, rho2, lx, ly, lz;
+    for (unsigned w = blockIdx.x; w < items; w += gridDim.x) {
+        const unsigned pb = w % pblocks, sg = w / pblocks;
+        const long long u = (long long)pb * kReduceThreads + threadIdx.x;
+        if (u >= units) continue;
+        const int j = (int)(2 * u / nz), k = (int)(2 * u % nz);
+        const bool has_y = j + 1 < ny, has_z = k + 2 < nz;
+        const int i0 = (int)sg * kObsZSeg, i1 = min(i0 + kObsZSeg, nx);
+        const float4 *row = psi4 + u;
+        float2 pre, pim;  // the previous plane's pair (the +x link into plane i0 is counted here)
+        {
+            const float4 v = __ldg(row + (long long)(i0 > 0 ? i0 - 1 : i0) * pst);
+            pre = make_float2(v.x, v.z);
+            pim = make_float2(v.y, v.w);
+        }
+        Acc<float> rk, rk1;  // this item's |psi|^2 per node of the pair
+        for (int c0 = i0; c0 < i1; c0 += kObsFold) {
+            float2 sr = dup2(0.f), sx2 = dup2(0.f), sr2 = dup2(0.f), slx = dup2(0.f), sly = dup2(0.f),
+                   slz = dup2(0.f);
+#pragma unroll
+            for (int h = 0; h < kObsFold; h += kObsPlanes) {
+                float4 P[kObsPlanes], QY[kObsPlanes];
+                float2 QZ[kObsPlanes];
+#pragma unroll
+                for (int t = 0; t < kObsPlanes; ++t) {
+                    const int i = min(c0 + h + t, i1 - 1);  // planes past i1 repeat the last, not summed
+                    const float4 *r = row + (long long)i * pst;
+                    P[t] = __ldg(r);
+                    QY[t] = has_y ? __ldg(r + nz / 2) : P[t];
+                    QZ[t] = has_z ? __ldg(reinterpret_cast<const float2 *>(r) + 2) : make_float2(P[t].z, P[t].w);
+                }
+#pragma unroll
+                for (int t = 0; t < kObsPlanes; ++t) {
+                    const int i = c0 + h + t;
+                    if (i < i1) {
+                        const float2 re = make_float2(P[t].x, P[t].z), im = make_float2(P[t].y, P[t].w);
+                        const float2 r2 = fma2(re, re, mul2(im, im));
+                        const float x = fmaf((float)i, dx, x0);
+                        sr = add2(sr, r2);
+                        sx2 = fma2(dup2(x * x), r2, sx2);
+                        sr2 = fma2(r2, r2, sr2);
+                        float2 dre = sub2(re, pre), dim = sub2(im, pim);
+                        slx = fma2(dre, dre, fma2(dim, dim, slx));
+                        dre = sub2(make_float2(QY[t].x, QY[t].z), re);
+                        dim = sub2(make_float2(QY[t].y, QY[t].w), im);
+                        sly = fma2(dre, dre, fma2(dim, dim, sly));
+                        dre = sub2(make_float2(re.y, QZ[t].x), re);   // links k -> k+1 and k+1 -> k+2
+                        dim = sub2(make_float2(im.y, QZ[t].y), im);
+                        slz = fma2(dre, dre, fma2(dim, dim, slz));
+                        pre = re;
+                        pim = im;
+                    }
+                }
+            }
+            rk.add(sr.x);
+            rk1.add(sr.y);
+            x2.add(sx2.x + sx2.y);
+            rho2.add(sr2.x + sr2.y);
+            lx.add(slx.x + slx.y);
+            ly.add(sly.x + sly.y);
+            lz.add(slz.x + slz.y);
+        }
+        const float y = (float)(a.origin[1] + j * a.d[1]);
+        const float zk = (float)(a.origin[2] + k * a.d[2]), zk1 = (float)(a.origin[2] + (k + 1) * a.d[2]);
+        const Acc<float> r = acc_sum(rk, rk1);
+        rho = acc_sum(rho, r);
+        y2 = acc_sum(y2, acc_scaled(r, y * y));
+        z2 = acc_sum(z2, acc_sum(acc_scaled(rk, zk * zk), acc_scaled(rk1, zk1 * zk1)));
+    }
+    const float sc = (float)__ldg(a.scale);
+    const float s2 = sc * sc;
+    Acc<float> acc[9];
+    acc[O_RHO] = acc_scaled(rho, s2);
+    acc[O_X2] = acc_scaled(x2, s2);
+    acc[O_Y2] = acc_scaled(y2, s2);
+    acc[O_Z2] = acc_scaled(z2, s2);
+    acc[O_RHO2] = acc_scaled(rho2, s2 * s2);
+    acc[O_LX] = acc_scaled(lx, s2);
+    acc[O_LY] = acc_scaled(ly, s2);
+    acc[O_LZ] = acc_scaled(lz, s2);
+    acc[O_V] = acc_sum(acc_sum(acc_scaled(acc[O_X2], (float)a.half_w2[0]), acc_scaled(acc[O_Y2], (float)a.half_w2[1])),
+                       acc_scaled(acc[O_Z2], (float)a.half_w2[2]));
+    float ps[9], pc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        ps[q] = acc[q].s;
+        pc[q] = acc[q].c;
+    }
+    double bs[9];
+    block_sum_pairs<9>(ps, pc, bs);
+    finalize_partials<9>(bs, a, [&](const double *t) { obs_finish(a, t); }, blockIdx.x, gridDim.x);
+}
+
+// Resident blocks of observables_c64z_kernel on each device (SMs x blocks
+// per SM), looked up once per device by prepare_field_launches (outside any
+// stream capture: the occupancy query may load the kernel's module).
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_c64z_resident[kMaxDevices];
+
+int c64z_resident(int dev) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, observables_c64z_kernel, kReduceThreads, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::max(1, sms) * std::max(1, per_sm);
+}
+
+// Blocks of observables_c64z_kernel: at most one resident wave, at most one
+// per work item.
+unsigned obs_c64z_grid(const FieldArgs &a) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    long long g = dev >= 0 && dev < kMaxDevices ? g_c64z_resident[dev].load() : 0;
+    if (g <= 0) g = 152LL * 2;  // not looked up on this device: the GB300's one wave
+    g = std::min(g, obs_c64z_items(a.n));
+    return (unsigned)std::max(1LL, g);
 }
 
 // Many condensates in one launch: instance i owns blocks [first[i], first[i+1]).
@@ -396,10 +554,13 @@ cudaError_t dispatch(int what, const FieldArgs &a, int blocks, void *dst, cudaSt
     case 0: gaussian_kernel<R, CPLX><<<fill_blocks(a.sites), 256, 0, s>>>(a); break;
     case 1: norm_kernel<R, CPLX><<<blocks, kReduceThreads, 0, s>>>(a); break;
     case 2:
-        if constexpr (sizeof(R) == 4 && CPLX)
-            observables_c64_kernel<<<observables_blocks(a), kReduceThreads, 0, s>>>(a);
-        else
-            observables_kernel<R, CPLX><<<observables_blocks(a), kReduceThreads, 0, s>>>(a);
+        if constexpr (sizeof(R) == 4 && CPLX) {
+            if (a.n[2] % 2 == 0)
+                observables_c64z_kernel<<<obs_c64z_grid(a), kReduceThreads, 0, s>>>(a);
+            else
+                observables_c64_kernel<<<observables_body_blocks(a), kReduceThreads, 0, s>>>(a);
+        } else
+            observables_kernel<R, CPLX><<<observables_body_blocks(a), kReduceThreads, 0, s>>>(a);
         break;
     case 3: apply_scale_kernel<R, CPLX><<<fill_blocks(a.sites), 256, 0, s>>>(a, dst); break;
     default: return cudaErrorInvalidValue;
@@ -416,6 +577,15 @@ cudaError_t dispatch_all(Prec p, bool cplx, int what, const FieldArgs &a, int bl
 }
 
 }  // namespace
+
+void prepare_field_launches() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return;
+    }
+    if (g_c64z_resident[dev].load() <= 0) g_c64z_resident[dev].store(c64z_resident(dev));
+}
 
 cudaError_t launch_kick(Prec p, const FieldArgs &a, double kdt, void *dst, cudaStream_t s) {
     return p == P_F64 ? launch_kick_r<double>(a, kdt, dst, s) : launch_kick_r<float>(a, kdt, dst, s);
@@ -434,10 +604,18 @@ cudaError_t launch_observables_batch(Prec p, bool cplx, const FieldArgs *args, c
     return cudaGetLastError();
 }
 
-int observables_blocks(const FieldArgs &a) {
+// Blocks of observables_body over one condensate (one per 256 (j, k) and
+// kObsSeg planes): the grid of observables_kernel and observables_c64_kernel,
+// and one condensate's share of observables_batch_kernel.
+int observables_body_blocks(const FieldArgs &a) {
     const long long plane = (long long)a.n[1] * a.n[2];
     const long long segs = (a.n[0] + kObsSeg - 1) / kObsSeg;
     return (int)((plane + kReduceThreads - 1) / kReduceThreads * segs);
+}
+
+// The most blocks (and so partials) any observables grid of this field has.
+int observables_blocks(const FieldArgs &a) {
+    return (int)std::max((long long)observables_body_blocks(a), obs_c64z_items(a.n));
 }
 
 cudaError_t launch_gaussian(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s) {

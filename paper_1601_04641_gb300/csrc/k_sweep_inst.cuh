@@ -80,6 +80,9 @@ static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cud
 
 template <class F, typename R, int W, int KIND>
 static cudaError_t launch_lines_w(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    if constexpr (has_quad<F>() && W > 0) {
+        if (L.lpt == 4) return launch_lines_wl<F, R, W, KIND, 4>(L, a, s);
+    }
     if constexpr (sizeof(typename F::V) <= 8) {
         if (L.lpt == 2) return launch_lines_wl<F, R, W, KIND, 2>(L, a, s);
     }
@@ -116,10 +119,14 @@ static cudaError_t launch_batch_lines_wl(const BatchLaunch &b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One line per thread, or adjacent line pairs (lpt 2; elements of 8 bytes or
-// less, windowed forms) for instances whose lines pair up in memory.
+// One line per thread, adjacent line pairs (lpt 2; elements of 8 bytes or
+// less, windowed forms) for instances whose lines pair up in memory, or
+// groups of four (lpt 4; forms that have a four-line form).
 template <class F, typename R, int W, int KIND>
 static cudaError_t launch_batch_lines_w(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    if constexpr (has_quad<F>() && W > 0) {
+        if (L.lpt == 4) return launch_batch_lines_wl<F, R, W, KIND, 4>(b, s);
+    }
     if constexpr (sizeof(typename F::V) <= 8 && W > 0) {
         if (L.lpt == 2) return launch_batch_lines_wl<F, R, W, KIND, 2>(b, s);
     }
@@ -142,8 +149,38 @@ static cudaError_t launch_batch_contig_w(const BatchLaunch &b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The batched z sweep through TMA tiles: every instance of the launch fits
+// the TMA form (tma_z_fits) and has its tensor maps in b.tma.
+template <class F, typename R, int W>
+static cudaError_t launch_batch_tma_w(const BatchLaunch &b, cudaStream_t s) {
+    if constexpr (tma_supported<F, W>()) {
+        if (b.n > kTmaBatch) return cudaErrorInvalidValue;
+        constexpr size_t smem = tma_smem_bytes<typename F::V, W>();
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(batch_tma_kernel<F, R, W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        BatchDesc d{b.args, b.first, b.gridx, b.n};
+        batch_tma_kernel<F, R, W><<<b.total_blocks, kTmaWarps * 32, smem, s>>>(d, *b.tma);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <class F, typename R, int KIND>
 static cudaError_t launch_batch_kind(const SweepLaunch &L, const BatchLaunch &b, cudaStream_t s) {
+    if (KIND == K_Z && L.contiguous && b.tma) {
+        switch (L.window) {
+        case 4: return launch_batch_tma_w<F, R, 4>(b, s);
+        case 8: return launch_batch_tma_w<F, R, 8>(b, s);
+        case 16: return launch_batch_tma_w<F, R, 16>(b, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (KIND == K_Z && L.contiguous) {
         switch (L.window) {
         case 4: return launch_batch_contig_w<F, R, 4>(b, s);

@@ -74,6 +74,15 @@ def imag_large() -> Problem:
                    name="imag 480x400x320, g 20, dt 0.1 d^2", meta={})
 
 
+def imag_large_half() -> Problem:
+    """480x400x160 slab of the imaginary-time 480x400x320 workload (same
+    spacing, dt, trap and g): a capture-sized case for profiling the same
+    kernels."""
+    p = imag_large()
+    return Problem((480, 400, 160), p.d, p.dt, p.omega, p.g,
+                   name="imag 480x400x160, g 20, dt 0.1 d^2 (half-depth profiling case)", meta={})
+
+
 def sized_box(shape, omega, g, dt_factor=0.1) -> Problem:
     """Grid spacing that holds both the g = 0 Gaussian (6 oscillator lengths)
     and 1.3x the Thomas-Fermi radius in the half-box, per axis."""

@@ -188,14 +188,24 @@ class GP:
         self._ck(self.lib.gp_set_axis_window(self.h, int(axis), int(window)))
 
     def set_pair_lines(self, on):
+        """Widest line groups per thread on the strided axes (on) or one line."""
         self._ck(self.lib.gp_set_pair_lines(self.h, int(bool(on))))
+
+    def set_lines_per_thread(self, axis, lines):
+        """Most adjacent lines per thread on axis 0 (x) or 1 (y): 1, 2 or 4."""
+        self._ck(self.lib.gp_set_lines_per_thread(self.h, int(axis), int(lines)))
+
+    def lines_per_thread(self, mode=0):
+        a = (ctypes.c_int * 3)()
+        self._ck(self.lib.gp_get_lines_per_thread(self.h, int(mode), a))
+        return tuple(a)
 
     def set_tma(self, on):
         """z sweep through TMA tiles (default where the grid allows it)."""
         self._ck(self.lib.gp_set_tma(self.h, int(bool(on))))
 
     def set_stop_rule(self, rule):
-        """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
+        """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol; 2: rule 1 at two consecutive checks."""
         self._ck(self.lib.gp_set_stop_rule(self.h, int(rule)))
 
     def set_splitting(self, order):
@@ -308,7 +318,7 @@ class Batch:
         return tuple(a), tuple(b)
 
     def set_stop_rule(self, rule):
-        """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol."""
+        """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol; 2: rule 1 at two consecutive checks."""
         self._ck(self.lib.gp_batch_set_stop_rule(self.h, int(rule)))
 
     def set_dt_scale(self, scale):
@@ -325,3 +335,54 @@ class Batch:
 
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_batch_set_graph_block(self.h, int(steps)))
+
+    def set_tma(self, on):
+        """z sweep through TMA tiles for the instances whose rows fit (default on)."""
+        self._ck(self.lib.gp_batch_set_tma(self.h, int(bool(on))))
+
+    def tma_count(self):
+        v = ctypes.c_int(0)
+        self._ck(self.lib.gp_batch_get_tma(self.h, ctypes.byref(v)))
+        return v.value
+
+
+def ground_state(shape, d, dt, omega, g, tol=1e-10, device=None, max_steps=200000,
+                 levels=((30.0, 1e-6), (10.0, 1e-7), (3.0, 1e-8), (1.0, 1e-9))):
+    """The imaginary-time ground state of one condensate at time step dt, as
+    a float64 CUDA tensor of `shape`: an FP32 real field from the Gaussian
+    through a dt schedule (`levels` of (dt scale, mu tolerance), stop rule 1),
+    then FP64 imaginary time at dt from that state until
+    |mu(n) - mu(n-10)| < tol.  Returns (psi, info); info holds the steps and
+    seconds of both stages, mu and the last |mu(n) - mu(n-10)|."""
+    import time
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g32 = GP(shape, d, dt, omega, g, "f32", "real", device=device)
+    g32.set_stop_rule(1)
+    g32.init_gaussian()
+    n32 = g32.run_imag_schedule(levels, 10, max_steps)
+    mu32 = g32.observables()["mu"]
+    psi = g32.get_psi(as_numpy=False).to(torch.float64)
+    g32.close()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g64 = GP(shape, d, dt, omega, g, "f64", "real", device=device)
+    g64.set_psi(psi)
+    mu_prev = g64.observables()["mu"]
+    n64, dmu = 0, float("inf")
+    while n64 < max_steps:
+        g64.step_imag(10)
+        n64 += 10
+        mu = g64.observables()["mu"]
+        dmu = abs(mu - mu_prev)
+        mu_prev = mu
+        if dmu < tol:
+            break
+    psi = g64.get_psi(as_numpy=False)
+    g64.close()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return psi, {"fp32_schedule_steps": n32, "fp32_s": t1 - t0, "mu_fp32": mu32,
+                 "fp64_steps": n64, "fp64_s": t2 - t1, "mu": mu_prev, "last_dmu": dmu, "tol": tol,
+                 "converged": dmu < tol}

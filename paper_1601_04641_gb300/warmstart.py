@@ -94,31 +94,73 @@ class Net:
         self._ck(self.lib.gp_nn_predict_batch(self.h, batch.h))
 
 
-def ground_states(problems, tol, max_steps=40000, chunk=256, device=None):
-    """Ground states of `problems` from the batched FP32 solver (real field),
-    run to |mu(n) - mu(n-10)| < tol.  Returns (data, offsets, psi_max, mu),
-    data a float32 CUDA tensor with the normalised amplitudes concatenated."""
+def ground_states(problems, tol, max_steps=40000, chunk=256, device=None, polish=False,
+                  levels=((10.0, 1e-5), (3.0, 1e-6), (1.0, 1e-7)), with_info=False):
+    """Ground states of `problems` from the batched solver (the method's own
+    ground states), in chunks of `chunk` condensates:
+    - polish False: FP32 real-field batches run to |mu(n) - mu(n-10)| < tol;
+    - polish True: FP32 real-field batches through the dt schedule `levels`
+      ((dt scale, mu tolerance), stop rule 1), then FP64 real-field batches
+      from those states to |mu(n) - mu(n-10)| < tol.
+    Returns (data, offsets, psi_max, mu), and a dict of steps and times with
+    with_info; data is a float32 CUDA tensor with the normalised amplitudes
+    concatenated."""
     import torch
     from .solver import Batch
     sizes = [p.sites for p in problems]
     offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
     data = torch.empty(int(sum(sizes)), dtype=torch.float32, device=device or "cuda")
     psi_max, mu = [], []
+    info = {"fp32_steps_max": 0, "fp64_steps_max": 0, "fp32_s": 0.0, "fp64_s": 0.0, "tol": tol,
+            "converged": 0, "of": len(problems)}
     for c0 in range(0, len(problems), chunk):
         part = problems[c0:c0 + chunk]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         b = Batch(part, "f32", "real", device=device)
         b.init_gaussian()
-        b.run_imag_until(tol, 10, max_steps)
+        if polish:
+            b.set_stop_rule(1)
+            steps = b.run_imag_schedule(list(levels), 10, max_steps)
+        else:
+            steps = b.run_imag_until(tol, 10, max_steps)
+        info["fp32_steps_max"] = max(info["fp32_steps_max"], max(steps))
+        if polish:
+            # FP64 from the FP32 states (the same fixed point up to FP32 rounding)
+            tmp = [torch.empty(p.shape, dtype=torch.float32, device=data.device) for p in part]
+            for i, t in enumerate(tmp):
+                N.check(b.lib.gp_batch_get_psi(b.h, i, ctypes.c_void_p(t.data_ptr()), 1), b.h, batch=True)
+            torch.cuda.synchronize()
+            b.close()
+            info["fp32_s"] += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            b = Batch(part, "f64", "real", device=device)
+            for i, t in enumerate(tmp):
+                t64 = t.to(torch.float64)
+                N.check(b.lib.gp_batch_set_psi(b.h, i, ctypes.c_void_p(t64.data_ptr()), 1), b.h, batch=True)
+                torch.cuda.synchronize()
+            del tmp
+            steps = b.run_imag_until(tol, 10, max_steps)
+            info["fp64_steps_max"] = max(info["fp64_steps_max"], max(steps))
+        info["converged"] += sum(x < max_steps for x in steps)
         mu += [o["mu"] for o in b.observables()]
         for i in range(len(part)):
             off = int(offsets[c0 + i])
             view = data[off:off + part[i].sites]
-            N.check(b.lib.gp_batch_get_psi(b.h, i, ctypes.c_void_p(view.data_ptr()), 1), b.h, batch=True)
+            if polish:
+                t64 = torch.empty(part[i].sites, dtype=torch.float64, device=data.device)
+                N.check(b.lib.gp_batch_get_psi(b.h, i, ctypes.c_void_p(t64.data_ptr()), 1), b.h, batch=True)
+                view.copy_(t64)
+            else:
+                N.check(b.lib.gp_batch_get_psi(b.h, i, ctypes.c_void_p(view.data_ptr()), 1), b.h, batch=True)
         torch.cuda.synchronize()
         for i in range(len(part)):
             off = int(offsets[c0 + i])
             psi_max.append(float(data[off:off + part[i].sites].abs().max().item()))
         b.close()
+        info["fp64_s" if polish else "fp32_s"] += time.perf_counter() - t0
+    if with_info:
+        return data, offsets, psi_max, mu, info
     return data, offsets, psi_max, mu
 
 

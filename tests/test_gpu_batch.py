@@ -37,6 +37,7 @@ def test_batch_instances_equal_single_runs(prec, field):
     b.init_gaussian()
     b.step_imag(23)                       # graph blocks of 16, then 7 single launches
     w = b.window()
+    n_tma = 0
     for i, p in enumerate(probs):
         gp = GP(p.shape, p.d, p.dt, p.omega, p.g, prec, field)
         # adjacent line pairs under the batch's rule (window 4, 8-byte
@@ -44,7 +45,10 @@ def test_batch_instances_equal_single_runs(prec, field):
         # lines into 8-node chunks, so both must pair alike to agree bit for bit
         assert w[0] == w[1]
         gp.set_pair_lines(prec == "f32" and field == "complex" and w[0] == 4)
-        gp.set_tma(False)  # the batched z sweep uses per-thread copies (same norm order)
+        # the batch takes the TMA z sweep for the instances whose rows fit
+        # it, by the single handle's rule (same line arithmetic, same norm
+        # summation order)
+        gp.set_tma(True)
         seg, _ = b.segments(i)
         for ax in range(3):
             gp.set_axis_window(ax, w[ax])
@@ -52,10 +56,39 @@ def test_batch_instances_equal_single_runs(prec, field):
         gp.init_gaussian()
         gp.step_imag(23)
         assert np.array_equal(b.get_psi(i), gp.get_psi()), p.name
+        n_tma += gp.tma_in_use()
         gp.close()
     obs = b.observables()
     assert all(o["step"] == 23 for o in obs)
+    assert b.tma_count() == n_tma
+    if prec == "f32":
+        assert 0 < n_tma < len(probs)  # both z-sweep launches of the batch ran
     b.close()
+
+
+@pytest.mark.parametrize("field", ["complex", "real"])
+def test_batch_tma_z_sweep_matches_copy_form_and_oracle(field):
+    """The batched z sweep with the TMA group on and off: psi agrees to FP32
+    rounding (same arithmetic per line, different chunking of the windowed
+    solve), and both follow the oracle's steps."""
+    from paper_1601_04641_gb300.solver import Batch
+    probs = uneven(6, seed=21, scale=0.6)
+    out = {}
+    for on in (True, False):
+        b = Batch(probs, "f32", field)
+        b.set_tma(on)
+        assert (b.tma_count() > 0) == on
+        b.init_gaussian()
+        b.step_imag(12)
+        out[on] = [b.get_psi(i).astype(np.float64 if field == "real" else np.complex128)
+                   for i in range(len(probs))]
+        b.close()
+    for i, p in enumerate(probs):
+        ref = oracle.gaussian(p.shape, p.d, p.omega)
+        oracle.step(ref, p.d, p.dt, p.omega, p.g, False, 12)
+        scale = float(np.max(np.abs(ref)))
+        assert float(np.max(np.abs(out[True][i] - out[False][i]))) <= 1e-6 * scale, p.name
+        assert float(np.max(np.abs(out[True][i] - ref))) <= 1e-5 * scale, p.name
 
 
 def test_batch_convergence_matches_oracle_fp64():
@@ -121,6 +154,32 @@ def test_stop_rule_with_energy_never_stops_earlier():
         assert abs(out[1][1][i] - mu_ref) <= abs(out[0][1][i] - mu_ref) + 1e-12
         assert abs(out[1][1][i] - mu_ref) <= 1e-5 * mu_ref
         assert abs(mu1 - mu_ref) <= 1e-5 * mu_ref
+
+
+def test_stop_rule_two_checks_matches_oracle():
+    """Rule 2 (rule 1's test at two consecutive checks): the FP64 batch and a
+    single handle take the oracle's number of steps, never fewer than rule 1."""
+    from paper_1601_04641_gb300.solver import GP, Batch
+    probs = uneven(4, seed=17, scale=0.3)
+    steps = {}
+    for rule in (1, 2):
+        b = Batch(probs, "f64", "real")
+        b.set_stop_rule(rule)
+        b.init_gaussian()
+        steps[rule] = b.run_imag_until(1e-8, 10, 20000)
+        b.close()
+    for i, p in enumerate(probs):
+        psi = oracle.gaussian(p.shape, p.d, p.omega)
+        n_ref, mu_ref = oracle.run_imag_until(psi, p.d, p.dt, p.omega, p.g, 1e-8, 10, 20000, rule=2)
+        gp = GP(p.shape, p.d, p.dt, p.omega, p.g, "f64", "real")
+        gp.set_stop_rule(2)
+        gp.init_gaussian()
+        n_h = gp.run_imag_until(1e-8, 10, 20000)
+        mu_h = gp.observables()["mu"]
+        gp.close()
+        assert steps[2][i] == n_ref == n_h, (p.name, steps[2][i], n_ref, n_h)
+        assert steps[2][i] >= steps[1][i]
+        assert abs(mu_h - mu_ref) <= 1e-12 * mu_ref
 
 
 @pytest.mark.parametrize("prec,field", [("f64", "real"), ("f32", "complex")])

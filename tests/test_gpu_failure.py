@@ -1,7 +1,9 @@
 """Failure detection without a GPU fault: the bounded device wait gives up and
 reports (a wait that nothing can satisfy, a short bound, nothing copied);
-allocation failures made on the host return GP_ERR_NOMEM and leave no device
-memory behind; odd line lengths (3, 5, 33, 127) against the oracle."""
+an expired wait's status word, raised from the host, is reported and makes
+psi unusable until it is set again; allocation failures made on the host
+return GP_ERR_NOMEM and leave no device memory behind; odd line lengths
+(3, 5, 33, 127) against the oracle."""
 import ctypes
 
 import numpy as np
@@ -35,6 +37,25 @@ def test_bounded_wait_gives_up_and_reports():
     assert abs(gp.observables()["norm"] - 1.0) < 1e-5
     gp.close()
     assert lib.gp_selftest_bounded_wait(0, None, ctypes.byref(done), ctypes.byref(expired)) == N.GP_ERR_ARG
+
+
+def test_reported_timeout_loses_psi_until_it_is_set_again():
+    from paper_1601_04641_gb300.solver import GP
+    gp = GP((16, 14, 32), (0.3, 0.3, 0.3), 0.01, (1, 1, 1), 1.0, "f32", "complex")
+    gp.init_gaussian()
+    gp.step_imag(2)
+    assert gp.lib.gp_debug_raise_status(gp.h) == N.GP_OK
+    with pytest.raises(N.GPError) as e:
+        gp.sync()
+    assert e.value.status == N.GP_ERR_TIMEOUT
+    for call in (lambda: gp.step_imag(1), gp.observables, gp.get_psi, lambda: gp.run_imag_until(1e-6, 10, 20)):
+        with pytest.raises(N.GPError) as e:
+            call()
+        assert e.value.status == N.GP_ERR_STATE
+    gp.init_gaussian()  # psi set again: usable
+    gp.step_imag(3)
+    assert abs(gp.observables()["norm"] - 1.0) < 1e-5
+    gp.close()
 
 
 def _creates():

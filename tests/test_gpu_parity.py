@@ -105,22 +105,33 @@ def test_every_window_fp32(window, realtime, shape):
     assert rel_max(gp.get_psi().astype(np.complex128), ref) <= 2e-6
 
 
-@pytest.mark.parametrize("prec,g,tol", [("f64", 3000.0, 1e-12), ("f32", 100.0, 1e-5)])
+@pytest.mark.parametrize("prec,g", [("f64", 3000.0), ("f32", 3000.0), ("f32", 100.0)])
 @pytest.mark.parametrize("realtime", [False, True])
-def test_kick_large_arguments(prec, g, tol, realtime):
+def test_kick_large_arguments(prec, g, realtime):
     """A stiff trap and a large g push the kick arguments dt V and dt g |psi|^2
-    past the range of the short series, onto the exp / sincos fallback.  FP32
-    resolves a phase theta only to ~1e-7 theta, so its case keeps theta near
-    2 rad (g = 100); FP64 takes g = 3000 (theta up to ~36 rad)."""
-    shape, d, dt, omega = (30, 28, 26), (0.3, 0.3, 0.3), 0.002, (6.0, 5.0, 4.0)
+    past the range of the short series, onto the expm1 / sincos fallback
+    (theta up to ~60 rad at g = 3000).  FP64 holds 1e-12.  FP32 forms theta
+    from three rounded terms, resolving it to a few units of 2^-24 theta, and
+    the modulus of psi carries a few units of rounding from every sweep,
+    which the nonlinear phase dt g |psi|^2 turns into a phase error 2 theta
+    times larger: per step a phase error of about 4 units of 2^-24 times
+    (theta + 2 theta_nl) <= 3 theta_max, on top of the 2e-6 of ordinary FP32
+    steps."""
+    shape, d, dt, omega, steps = (30, 28, 26), (0.3, 0.3, 0.3), 0.002, (6.0, 5.0, 4.0), 3
     psi0 = inputs.random_field(shape, seed=17) * 2.0
     if prec == "f32":
         psi0 = psi0.astype(np.complex64).astype(np.complex128)
     gp = make(shape, d, dt, omega, g, prec)
     gp.set_psi(psi0.astype(np.complex64) if prec == "f32" else psi0)
-    (gp.step_real if realtime else gp.step_imag)(3)
+    (gp.step_real if realtime else gp.step_imag)(steps)
     ref = psi0.copy()
-    oracle.step(ref, d, dt, omega, g, realtime, 3)
+    oracle.step(ref, d, dt, omega, g, realtime, steps)
+    ax = [(np.arange(n) - 0.5 * (n - 1)) * h for n, h in zip(shape, d)]
+    pot = 0.5 * ((omega[0] * ax[0][:, None, None]) ** 2 + (omega[1] * ax[1][None, :, None]) ** 2 +
+                 (omega[2] * ax[2][None, None, :]) ** 2)
+    theta_max = float(np.max(dt * (pot + g * np.abs(psi0) ** 2)))
+    assert theta_max > (30.0 if g > 1000 else 1.0)
+    tol = 1e-12 if prec == "f64" else 2e-6 + steps * 4 * 2.0 ** -24 * 3 * theta_max
     assert rel_max(gp.get_psi().astype(np.complex128), ref) <= tol
 
 
@@ -408,20 +419,19 @@ def test_full_size_one_step_sampled(which):
 
 def test_full_size_complex64_quench_accuracy():
     """The benchmark workload's precision form (480x400x320, complex64 psi,
-    FP64 coefficients and reductions), 500 real-time steps of the quench,
-    against the FP64 path (held to the oracle within 1e-12 by the tests
-    above) from the same start state: |dmu|/mu <= 1e-5, relative L2 of psi
-    <= 1e-4."""
+    FP64 coefficients and reductions), 500 real-time steps of the quench
+    from the imaginary-time ground state at g = 20 (converged in FP64 to
+    |dmu| < 1e-10 between checks 10 steps apart, reading R8), against the
+    FP64 path (held to the oracle within 1e-12 by the tests above) from the
+    same start state: |dmu|/mu <= 1e-5, relative L2 of psi <= 1e-4."""
     import torch
+    from paper_1601_04641_gb300.solver import ground_state
     p = inputs.real_large()
+    psi, info = ground_state(p.shape, p.d, 0.1 * p.d[0] ** 2, p.omega, p.meta["g_prepare"], tol=1e-10)
+    assert info["converged"] and info["last_dmu"] < 1e-10, info
     g64 = make(p.shape, p.d, p.dt, p.omega, p.g, "f64", "complex")
-    g64.init_gaussian()
-    g64.set_g(p.meta["g_prepare"])
-    g64.set_dt(0.1 * p.d[0] ** 2)
-    g64.step_imag(100)
-    g64.set_g(p.g)
-    g64.set_dt(p.dt)
-    start = g64.get_psi(as_numpy=False).to(torch.complex64)
+    start = psi.to(torch.complex64)
+    del psi
     g64.set_psi(start.to(torch.complex128))
     g32 = make(p.shape, p.d, p.dt, p.omega, p.g, "f32", "complex")
     g32.set_psi(start)
