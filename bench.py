@@ -65,9 +65,9 @@ FP64_PEAK_GFLOPS = 1250.0
 NCU_TRAFFIC = {
     # ncu --set full of the 480x400x160 half-depth case (profiles/), scaled x2
     # by sites to a full 480x400x320 launch: (read + write) bytes per launch
-    ("real_large", "zsweep_norm"): (2 * (246.290944e6 + 199.825152e6), "ffc8bb149e21534f"),
-    ("real_large", "kick_xsweep"): (2 * (257.212160e6 + 194.386176e6), "ffc8bb149e21534f"),
-    ("real_large", "ysweep"): (2 * (250.992640e6 + 193.096192e6), "ffc8bb149e21534f"),
+    ("real_large", "zsweep_norm"): (2 * (246.244608e6 + 200.039168e6), "388e2deadb188d15"),
+    ("real_large", "kick_xsweep"): (2 * (257.208320e6 + 194.405888e6), "388e2deadb188d15"),
+    ("real_large", "ysweep"): (2 * (251.276800e6 + 193.513984e6), "388e2deadb188d15"),
 }
 
 
@@ -628,12 +628,13 @@ def time_to_ground_state(torch, dev, count, tol, peak, max_steps=20000):
 
 
 def warm_start(torch, dev, n_train, n_held, steps, mustar64=None, bar64=None, tol=1e-7):
-    """The learned warm start on 128x96x80 condensates (BASELINE config 5):
-    targets are the method's own ground states (FP32 real-field batches
-    through a dt schedule to |dmu| < 1e-7, then FP64 batches to |dmu| < 1e-9
-    from them), GPU training of the network, then FP64 imaginary time to
-    |dmu|, |dE| < tol on held-out parameters from the Gaussian and from the
-    network's prediction (energy fallback)."""
+    """The learned warm start on 128x96x80 condensates: targets are the
+    method's own ground states (FP32 real-field batches through a dt schedule
+    and then at dt to |dmu| < 1e-9, where the FP32 iteration settles at its
+    fixed point, then 100 FP64 steps), GPU training of the network, then
+    imaginary time (FP32 real-field batches) to |dmu|, |dE| < tol on held-out
+    parameters from the Gaussian and from the network's prediction (energy
+    fallback)."""
     import numpy as np
     from paper_1601_04641_gb300 import warmstart as W
     shape = (128, 96, 80)
@@ -641,7 +642,7 @@ def warm_start(torch, dev, n_train, n_held, steps, mustar64=None, bar64=None, to
     hp = [inputs.sized_box(shape, p.omega, p.g) for p in inputs.batch_problems(n_held, seed=2, g_max=500.0)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    data, offs, pmax, _, gs_info = W.ground_states(tp, 1e-9, max_steps=60000, device=dev, polish=True,
+    data, offs, pmax, _, gs_info = W.ground_states(tp, 1e-9, max_steps=60000, device=dev, polish=100,
                                                    with_info=True)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
@@ -652,7 +653,7 @@ def warm_start(torch, dev, n_train, n_held, steps, mustar64=None, bar64=None, to
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     max_steps = 60000
-    r = W.run_from_starts(net, hp, tol, precision="f64", field="real", max_steps=max_steps, device=dev)
+    r = W.run_from_starts(net, hp, tol, precision="f32", field="real", max_steps=max_steps, device=dev)
     ttgs = schedule_from_starts(torch, dev, net, 64, 1e-6, mustar64, bar64)
     net.close()
     del data
@@ -664,10 +665,10 @@ def warm_start(torch, dev, n_train, n_held, steps, mustar64=None, bar64=None, to
     # forward + backward multiply-adds per sample point of the 16-64-64-64-1 net
     macs = (16 * 64 + 64 * 64 + 64 * 64 + 64) * 2 + (64 * 64 + 64 * 64 + 64)
     return {"workload": "128x96x80 condensates, gamma,nu,lambda ~ U[0.5,3], log g ~ U[0, ln 500]; "
-                        "%d training ground states (FP32 real-field batches through a dt schedule to "
-                        "|dmu| < 1e-7, then FP64 to |dmu| < 1e-9), %d held-out, FP64 imaginary "
-                        "time to |dmu| < %g and |dE| < %g (at most %d steps)" % (n_train, n_held, tol, tol,
-                                                                                 max_steps),
+                        "%d training ground states (FP32 real-field batches, dt schedule then dt to "
+                        "|dmu| < 1e-9, then 100 FP64 steps), %d held-out, FP32 real-field batches in "
+                        "imaginary time to |dmu| < %g and |dE| < %g (at most %d steps)" % (n_train, n_held, tol,
+                                                                                         tol, max_steps),
             "targets": gs_info,
             "data_s": t_data, "train_s": t_train, "train_steps": steps, "final_loss": losses[-1],
             "train_tflops": 2.0 * macs * 32768 * steps / t_train / 1e12,
@@ -859,7 +860,9 @@ def run_ours(args):
                    if res["field"] == "complex" else {"f32": "float32", "f64": "float64"}[res["prec"]],
                    "reductions": "fp64", "dt": p.dt, "g": p.g, "omega": list(p.omega),
                    "track_every": TRACK_EVERY,
-                   "l2": "inputs larger than L2 (psi %.0f MB > 129 MB)" % (elem * sites / 1e6),
+                   "l2": ("inputs larger than L2 (psi %.0f MB > 129 MB)" if elem * sites > 129e6 else
+                          "psi %.0f MB fits in the 129 MB L2 (no flush: a timing of L2-resident data)") %
+                         (elem * sites / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

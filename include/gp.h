@@ -414,8 +414,21 @@ gp_status gp_batch_run_imag_schedule(gp_batch b, int levels, const double *dt_sc
 gp_status gp_batch_get_window(gp_batch b, int window[3]);
 /* Segment length and count per axis of instance i. */
 gp_status gp_batch_get_segments(gp_batch b, int i, int seg_len[3], int n_seg[3]);
+/* Interior nodes per segment on the strided axes (x, y) of every instance
+ * (seg_len >= 1, at most the line; 0, the default: about 128, in whole
+ * chunks), for windowed solves.  Shorter segments give more threads per line
+ * at the cost of W + 1 warm-up nodes per segment; psi is the same to
+ * roundoff.  GP_ERR_ARG for seg_len < 0. */
+gp_status gp_batch_set_segments(gp_batch b, int seg_len);
 /* Steps per CUDA graph (default 16; 0 or 1: launch by launch). */
 gp_status gp_batch_set_graph_block(gp_batch b, int steps);
+/* Stream groups of a batched step (1..16, default 2): the active instances
+ * are split into groups balanced by sites, and each group's x, y and z
+ * sweeps run as one chain of launches on a stream of its own, forked from
+ * and joined back into the batch's stream (and captured into its graphs as
+ * parallel branches), so launches of different groups overlap.  psi is the
+ * same for every setting. */
+gp_status gp_batch_set_streams(gp_batch b, int streams);
 /* z sweep of the instances whose rows fit the TMA form (the rules of
  * gp_set_tma, at the batch's z window; at most 64 instances, the first ones
  * in creation order) through TMA tiles (1, the default) or every instance

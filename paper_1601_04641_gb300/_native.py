@@ -93,6 +93,8 @@ SIGNATURES = {
     "gp_batch_run_imag_until": (_i, [Handle, _d, _i, _i, ctypes.POINTER(_i)]),
     "gp_batch_get_window": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_batch_get_segments": (_i, [Handle, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "gp_batch_set_segments": (_i, [Handle, _i]),
+    "gp_batch_set_streams": (_i, [Handle, _i]),
     "gp_batch_set_graph_block": (_i, [Handle, _i]),
     "gp_batch_set_tma": (_i, [Handle, _i]),
     "gp_batch_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),

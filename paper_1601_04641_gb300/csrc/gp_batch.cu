@@ -44,13 +44,21 @@ struct Inst {
 // that advance one line per thread, group 1 those that advance adjacent line
 // pairs.  z sweep: group 0 the per-thread-copy form, group 1 the TMA form
 // (at most kTmaBatch instances whose rows fit it, with their tensor maps).
-struct LaunchSet {
+struct SweepSet {
     SweepArgs *args[3][2][2] = {};   // [sweep][group][parity]
     unsigned *first[3][2] = {};
     unsigned *gridx[3][2] = {};
     unsigned total[3][2] = {};
     int count[3][2] = {};
     std::vector<BatchTmaMaps> zmaps;  // [parity]: maps of the z sweep's TMA group
+};
+
+// The active instances, split into stream groups: each group's x, y and z
+// sweeps form one chain of launches on its own stream (the groups'
+// condensates are independent), so the launches of different groups overlap
+// and fill each other's ramp-up and tail.
+struct LaunchSet {
+    std::vector<SweepSet> sets;   // one per stream group
     FieldArgs *fargs = nullptr;   // observables of the instances, for their current parity
     unsigned *ofirst = nullptr;
     unsigned ototal = 0;
@@ -81,7 +89,11 @@ struct gp_batch_s {
     int window[3] = {0, 0, 0};
     bool contiguous_z = false;
     bool use_tma = true;           // z sweep through TMA for the instances whose rows fit
+    int seg_len = 0;               // interior nodes per segment on the strided axes (0: automatic)
     LaunchSet act;                 // the active instances
+    int streams = 2;               // stream groups of a step (1: one chain of launches)
+    std::vector<cudaStream_t> gstream;   // the groups' streams (created on first use)
+    std::vector<cudaEvent_t> gevent;     // fork event, then one join event per group
     bool dirty = true;
     int graph_block = 16;
     int stop_rule = 0;             // as gp_set_stop_rule (0, 1 or 2)
@@ -148,6 +160,8 @@ void assign_ztma(gp_batch b) {
     }
 }
 
+void assign_segments(gp_batch b);
+
 // Tables, windows and segments of every instance for dt = dt0 * scale.  One
 // window per axis for the whole batch: the largest of the instances' smallest
 // admissible windows (0 if any instance admits none, or FP64).
@@ -171,6 +185,13 @@ void configure(gp_batch b, double scale, std::vector<char> &host) {
     }
     b->contiguous_z = b->window[2] > 0;
     assign_ztma(b);
+    assign_segments(b);
+    b->dt_scale = scale;
+}
+
+// Lines per thread and segments of every instance and axis at the batch's
+// windows (segment length override b->seg_len on the strided axes).
+void assign_segments(gp_batch b) {
     for (Inst &I : b->inst)
         for (int ax = 0; ax < 3; ++ax) {
             // adjacent line pairs on a strided axis (window 4, 8-byte
@@ -186,10 +207,9 @@ void configure(gp_batch b, double scale, std::vector<char> &host) {
             const bool pair = ax < 2 && b->window[ax] == 4 && b->elem == 8 && axis_lines(I.G, ax) % 2 == 0 &&
                               (ax != 1 || I.G.n[2] % 2 == 0);
             I.lpt[ax] = pair ? 2 : 1;
-            choose_segments(I.G, ax, b->window[ax], I.lpt[ax], (int)b->elem, ax == 2 && b->contiguous_z, 0,
-                            &I.seg_len[ax], &I.n_seg[ax]);
+            choose_segments(I.G, ax, b->window[ax], I.lpt[ax], (int)b->elem, ax == 2 && b->contiguous_z,
+                            ax < 2 ? b->seg_len : 0, &I.seg_len[ax], &I.n_seg[ax]);
         }
-    b->dt_scale = scale;
 }
 
 // Norm / observables partials an instance may need under any window choice
@@ -220,45 +240,82 @@ gp_status build_set(gp_batch b) {
     LaunchSet &S = b->act;
     for (int i = 0; i < b->n; ++i)
         if (b->inst[i].active) S.members.push_back(i);
-    S.zmaps.assign(2, BatchTmaMaps());
-    for (int k = 0; k < 3; ++k) {
-        for (int g = 0; g < 2; ++g) {
-            std::vector<SweepArgs> args[2];
-            std::vector<unsigned> first{0}, gridx;
-            for (int i : S.members) {
-                const Inst &I = b->inst[i];
-                const bool tma = k == 2 && I.ztma;
-                if (k == 2 ? (tma != (g == 1)) : I.lpt[k] != g + 1) continue;
-                for (int p = 0; p < 2; ++p) {
-                    // sweep k of a step that starts with psi in buffer I.cur ^ p
-                    const int in = I.cur ^ p ^ (k & 1);
-                    const char *src = b->d_psi[in] + I.psi_off;
-                    char *dst = b->d_psi[in ^ 1] + I.psi_off;
-                    args[p].push_back(sweep_args(I.G, k, false, src, dst, b->d_tab, I.tab, I.seg_len[k],
-                                                 I.n_seg[k], b->d_scal + 2 * i, b->d_partials + I.part_off,
-                                                 b->d_counters + i, b->d_scal + 2 * i + 1, b->d_scal + 2 * i));
-                    if (tma) {
-                        const size_t q = args[p].size() - 1;
-                        const long long rows = axis_lines(I.G, 2);
-                        if (!encode_z_map(&S.zmaps[p].in[q], src, I.G.n[2], rows, (int)b->elem) ||
-                            !encode_z_map(&S.zmaps[p].out[q], dst, I.G.n[2], rows, (int)b->elem))
-                            return bfail(b, GP_ERR_CUDA, "encoding a tensor map of the batched z sweep failed");
-                    }
-                }
-                // TMA: one block per kTmaWarps * 64 rows, as a single-condensate launch
-                const unsigned gx = tma ? (unsigned)((axis_lines(I.G, 2) + kTmaBlockRows - 1) / kTmaBlockRows)
-                                        : sweep_gridx(b, I, k, I.lpt[k]);
-                gridx.push_back(gx);
-                first.push_back(first.back() + gx * (unsigned)I.n_seg[k]);
-            }
-            S.total[k][g] = first.back();
-            S.count[k][g] = (int)gridx.size();
-            gp_status st;
-            if ((st = upload(b, args[0], &S.args[k][g][0])) != GP_OK) return st;
-            if ((st = upload(b, args[1], &S.args[k][g][1])) != GP_OK) return st;
-            if ((st = upload(b, first, &S.first[k][g])) != GP_OK) return st;
-            if ((st = upload(b, gridx, &S.gridx[k][g])) != GP_OK) return st;
+    // stream groups balanced by sites: largest instance first to the least
+    // loaded group
+    const int ng = std::max(1, std::min(b->streams, (int)S.members.size()));
+    std::vector<std::vector<int>> groups(ng);
+    {
+        std::vector<int> bysize(S.members);
+        std::stable_sort(bysize.begin(), bysize.end(),
+                         [&](int a, int c) { return b->inst[a].sites > b->inst[c].sites; });
+        std::vector<size_t> load(ng, 0);
+        for (int i : bysize) {
+            const int gi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            groups[gi].push_back(i);
+            load[gi] += b->inst[i].sites;
         }
+    }
+    S.sets.assign(ng, SweepSet());
+    for (int gs = 0; gs < ng; ++gs) {
+        SweepSet &T = S.sets[gs];
+        T.zmaps.assign(2, BatchTmaMaps());
+        for (int k = 0; k < 3; ++k) {
+            // longest lines first: a block's run time grows with its lines'
+            // length, and blocks start in grid order, so the long ones should
+            // not be left for the end of the launch (instances are independent;
+            // their order changes no result)
+            std::vector<int> order(groups[gs]);
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int a, int c) { return b->inst[a].G.n[k] > b->inst[c].G.n[k]; });
+            for (int g = 0; g < 2; ++g) {
+                std::vector<SweepArgs> args[2];
+                std::vector<unsigned> first{0}, gridx;
+                for (int i : order) {
+                    const Inst &I = b->inst[i];
+                    const bool tma = k == 2 && I.ztma;
+                    if (k == 2 ? (tma != (g == 1)) : I.lpt[k] != g + 1) continue;
+                    for (int p = 0; p < 2; ++p) {
+                        // sweep k of a step that starts with psi in buffer I.cur ^ p
+                        const int in = I.cur ^ p ^ (k & 1);
+                        const char *src = b->d_psi[in] + I.psi_off;
+                        char *dst = b->d_psi[in ^ 1] + I.psi_off;
+                        args[p].push_back(sweep_args(I.G, k, false, src, dst, b->d_tab, I.tab, I.seg_len[k],
+                                                     I.n_seg[k], b->d_scal + 2 * i, b->d_partials + I.part_off,
+                                                     b->d_counters + i, b->d_scal + 2 * i + 1, b->d_scal + 2 * i));
+                        if (tma) {
+                            const size_t q = args[p].size() - 1;
+                            const long long rows = axis_lines(I.G, 2);
+                            if (!encode_z_map(&T.zmaps[p].in[q], src, I.G.n[2], rows, (int)b->elem) ||
+                                !encode_z_map(&T.zmaps[p].out[q], dst, I.G.n[2], rows, (int)b->elem))
+                                return bfail(b, GP_ERR_CUDA, "encoding a tensor map of the batched z sweep failed");
+                        }
+                    }
+                    // TMA: one block per kTmaWarps * 64 rows, as a single-condensate launch
+                    const unsigned gx = tma ? (unsigned)((axis_lines(I.G, 2) + kTmaBlockRows - 1) / kTmaBlockRows)
+                                            : sweep_gridx(b, I, k, I.lpt[k]);
+                    gridx.push_back(gx);
+                    first.push_back(first.back() + gx * (unsigned)I.n_seg[k]);
+                }
+                T.total[k][g] = first.back();
+                T.count[k][g] = (int)gridx.size();
+                gp_status st;
+                if ((st = upload(b, args[0], &T.args[k][g][0])) != GP_OK) return st;
+                if ((st = upload(b, args[1], &T.args[k][g][1])) != GP_OK) return st;
+                if ((st = upload(b, first, &T.first[k][g])) != GP_OK) return st;
+                if ((st = upload(b, gridx, &T.gridx[k][g])) != GP_OK) return st;
+            }
+        }
+    }
+    // the groups' streams and events, made here, outside any stream capture
+    while ((int)b->gstream.size() < ng && ng > 1) {
+        cudaStream_t gs = nullptr;
+        GPB_CK(b, cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+        b->gstream.push_back(gs);
+    }
+    while ((int)b->gevent.size() < ng + 1 && ng > 1) {
+        cudaEvent_t e = nullptr;
+        GPB_CK(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->gevent.push_back(e);
     }
     std::vector<FieldArgs> fa;
     std::vector<unsigned> of{0};
@@ -275,8 +332,7 @@ gp_status build_set(gp_batch b) {
     return GP_OK;
 }
 
-gp_status launch_step(gp_batch b, cudaStream_t s, int parity) {
-    LaunchSet &S = b->act;
+gp_status launch_sweeps(gp_batch b, const SweepSet &T, cudaStream_t s, int parity) {
     for (int k = 0; k < 3; ++k) {
         SweepLaunch L;
         L.prec = b->prec == GP_F32 ? P_F32 : P_F64;
@@ -286,12 +342,33 @@ gp_status launch_step(gp_batch b, cudaStream_t s, int parity) {
         L.threads = kSweepThreads;
         L.contiguous = (k == 2 && b->contiguous_z) ? 1 : 0;
         for (int g = 0; g < 2; ++g) {
-            if (S.count[k][g] == 0) continue;
+            if (T.count[k][g] == 0) continue;
             L.lpt = k < 2 ? g + 1 : 1;
-            BatchLaunch bl{S.args[k][g][parity], S.first[k][g], S.gridx[k][g], S.count[k][g], S.total[k][g]};
-            if (k == 2 && g == 1) bl.tma = &S.zmaps[parity];
+            BatchLaunch bl{T.args[k][g][parity], T.first[k][g], T.gridx[k][g], T.count[k][g], T.total[k][g]};
+            if (k == 2 && g == 1) bl.tma = &T.zmaps[parity];
             GPB_CK(b, launch_sweep_batch(L, bl, s));
         }
+    }
+    return GP_OK;
+}
+
+// One step of the active instances queued on s: with one stream group, the
+// sweeps on s; with several, each group's sweeps on its own stream, forked
+// from and joined back into s by events (a capture on s records the groups
+// as parallel branches of the graph).
+gp_status launch_step(gp_batch b, cudaStream_t s, int parity) {
+    LaunchSet &S = b->act;
+    const int ng = (int)S.sets.size();
+    if (ng == 1) return launch_sweeps(b, S.sets[0], s, parity);
+    if ((int)b->gstream.size() < ng || (int)b->gevent.size() < ng + 1)
+        return bfail(b, GP_ERR_STATE, "stream groups not set up");
+    GPB_CK(b, cudaEventRecord(b->gevent[0], s));
+    for (int g = 0; g < ng; ++g) {
+        GPB_CK(b, cudaStreamWaitEvent(b->gstream[g], b->gevent[0], 0));
+        gp_status st = launch_sweeps(b, S.sets[g], b->gstream[g], parity);
+        if (st != GP_OK) return st;
+        GPB_CK(b, cudaEventRecord(b->gevent[g + 1], b->gstream[g]));
+        GPB_CK(b, cudaStreamWaitEvent(s, b->gevent[g + 1], 0));
     }
     return GP_OK;
 }
@@ -389,6 +466,8 @@ void release_batch(gp_batch b) {
     cudaFree(b->d_partials);
     cudaFree(b->d_counters);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (cudaStream_t gs : b->gstream) cudaStreamDestroy(gs);
+    for (cudaEvent_t e : b->gevent) cudaEventDestroy(e);
     cudaGetLastError();
     delete b;
 }
@@ -724,6 +803,29 @@ gp_status gp_batch_set_tma(gp_batch b, int on) {
     GPB_CK(b, cudaStreamSynchronize(b->stream));
     b->use_tma = on != 0;
     assign_ztma(b);
+    free_set(b);
+    b->dirty = true;
+    return GP_OK;
+}
+
+gp_status gp_batch_set_streams(gp_batch b, int streams) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (streams < 1 || streams > 16) return bfail(b, GP_ERR_ARG, "streams must be in [1, 16]");
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    b->streams = streams;
+    free_set(b);
+    b->dirty = true;
+    return GP_OK;
+}
+
+gp_status gp_batch_set_segments(gp_batch b, int seg_len) {
+    gp_status st = benter(b);
+    if (st != GP_OK) return st;
+    if (seg_len < 0) return bfail(b, GP_ERR_ARG, "seg_len must be >= 0");
+    GPB_CK(b, cudaStreamSynchronize(b->stream));
+    b->seg_len = seg_len;
+    assign_segments(b);
     free_set(b);
     b->dirty = true;
     return GP_OK;

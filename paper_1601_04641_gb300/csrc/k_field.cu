@@ -464,14 +464,14 @@ int c64z_resident(int dev) {
 }
 
 // Blocks of observables_c64z_kernel: at most one resident wave, at most one
-// per work item.
+// per work item; 0 where the resident wave has not been looked up on the
+// current device, and then the per-(j, k) kernel runs instead.
 unsigned obs_c64z_grid(const FieldArgs &a) {
     int dev = 0;
     cudaGetDevice(&dev);
-    long long g = dev >= 0 && dev < kMaxDevices ? g_c64z_resident[dev].load() : 0;
-    if (g <= 0) g = 152LL * 2;  // not looked up on this device: the GB300's one wave
-    g = std::min(g, obs_c64z_items(a.n));
-    return (unsigned)std::max(1LL, g);
+    const long long g = dev >= 0 && dev < kMaxDevices ? g_c64z_resident[dev].load() : 0;
+    if (g <= 0) return 0;
+    return (unsigned)std::max(1LL, std::min(g, obs_c64z_items(a.n)));
 }
 
 // Many condensates in one launch: instance i owns blocks [first[i], first[i+1]).
@@ -555,8 +555,9 @@ cudaError_t dispatch(int what, const FieldArgs &a, int blocks, void *dst, cudaSt
     case 1: norm_kernel<R, CPLX><<<blocks, kReduceThreads, 0, s>>>(a); break;
     case 2:
         if constexpr (sizeof(R) == 4 && CPLX) {
-            if (a.n[2] % 2 == 0)
-                observables_c64z_kernel<<<obs_c64z_grid(a), kReduceThreads, 0, s>>>(a);
+            const unsigned g = a.n[2] % 2 == 0 ? obs_c64z_grid(a) : 0;
+            if (g > 0)
+                observables_c64z_kernel<<<g, kReduceThreads, 0, s>>>(a);
             else
                 observables_c64_kernel<<<observables_body_blocks(a), kReduceThreads, 0, s>>>(a);
         } else

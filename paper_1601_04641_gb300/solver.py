@@ -336,6 +336,14 @@ class Batch:
     def set_graph_block(self, steps):
         self._ck(self.lib.gp_batch_set_graph_block(self.h, int(steps)))
 
+    def set_streams(self, streams):
+        """Stream groups of a step (1..16): independent chains of sweeps that overlap."""
+        self._ck(self.lib.gp_batch_set_streams(self.h, int(streams)))
+
+    def set_segments(self, seg_len):
+        """Interior nodes per segment on the strided axes (0: automatic)."""
+        self._ck(self.lib.gp_batch_set_segments(self.h, int(seg_len)))
+
     def set_tma(self, on):
         """z sweep through TMA tiles for the instances whose rows fit (default on)."""
         self._ck(self.lib.gp_batch_set_tma(self.h, int(bool(on))))

@@ -94,14 +94,16 @@ class Net:
         self._ck(self.lib.gp_nn_predict_batch(self.h, batch.h))
 
 
-def ground_states(problems, tol, max_steps=40000, chunk=256, device=None, polish=False,
-                  levels=((10.0, 1e-5), (3.0, 1e-6), (1.0, 1e-7)), with_info=False):
+def ground_states(problems, tol, max_steps=40000, chunk=256, device=None, polish=0,
+                  levels=((10.0, 1e-5), (3.0, 1e-6)), with_info=False):
     """Ground states of `problems` from the batched solver (the method's own
     ground states), in chunks of `chunk` condensates:
-    - polish False: FP32 real-field batches run to |mu(n) - mu(n-10)| < tol;
-    - polish True: FP32 real-field batches through the dt schedule `levels`
-      ((dt scale, mu tolerance), stop rule 1), then FP64 real-field batches
-      from those states to |mu(n) - mu(n-10)| < tol.
+    - polish 0: FP32 real-field batches run to |mu(n) - mu(n-10)| < tol;
+    - polish > 0: FP32 real-field batches through the dt schedule `levels`
+      ((dt scale, mu tolerance)) and then at dt to |mu(n) - mu(n-10)| < tol
+      (stop rule 1; the FP32 iteration settles bit for bit at its fixed
+      point, so any tolerance is reached), then `polish` FP64 imaginary-time
+      steps of each state at dt.
     Returns (data, offsets, psi_max, mu), and a dict of steps and times with
     with_info; data is a float32 CUDA tensor with the normalised amplitudes
     concatenated."""
@@ -121,7 +123,7 @@ def ground_states(problems, tol, max_steps=40000, chunk=256, device=None, polish
         b.init_gaussian()
         if polish:
             b.set_stop_rule(1)
-            steps = b.run_imag_schedule(list(levels), 10, max_steps)
+            steps = b.run_imag_schedule(list(levels) + [(1.0, tol)], 10, max_steps)
         else:
             steps = b.run_imag_until(tol, 10, max_steps)
         info["fp32_steps_max"] = max(info["fp32_steps_max"], max(steps))
@@ -140,9 +142,9 @@ def ground_states(problems, tol, max_steps=40000, chunk=256, device=None, polish
                 N.check(b.lib.gp_batch_set_psi(b.h, i, ctypes.c_void_p(t64.data_ptr()), 1), b.h, batch=True)
                 torch.cuda.synchronize()
             del tmp
-            steps = b.run_imag_until(tol, 10, max_steps)
-            info["fp64_steps_max"] = max(info["fp64_steps_max"], max(steps))
-        info["converged"] += sum(x < max_steps for x in steps)
+            b.step_imag(polish)
+            info["fp64_steps_max"] = polish
+        info["converged"] += sum(x < max_steps * ((len(levels) + 1) if polish else 1) for x in steps)
         mu += [o["mu"] for o in b.observables()]
         for i in range(len(part)):
             off = int(offsets[c0 + i])

@@ -219,3 +219,62 @@ def test_dt_schedule_reaches_the_target_fixed_point(prec, field):
         assert abs(mu_p[i] - mu_ref) <= tol * mu_ref
         assert abs(mu_h - mu_ref) <= 1e-5 * mu_ref
         assert abs(mu_after - mu_ref) <= 1e-7 * mu_ref  # dt restored (a wrong dt moves mu by ~1e-4)
+
+
+def test_batch_segment_override_keeps_results():
+    """Shorter segments on the strided axes (more threads per line, W + 1
+    warm-up nodes each): psi agrees with the automatic segments to FP32
+    rounding and with the oracle; negative lengths are refused."""
+    from paper_1601_04641_gb300 import _native as N
+    from paper_1601_04641_gb300.solver import Batch
+    probs = uneven(4, seed=5, scale=0.6)
+    out = {}
+    for seg in (0, 24, 7):
+        b = Batch(probs, "f32", "complex")
+        b.set_segments(seg)
+        if seg:
+            assert all(b.segments(i)[0][0] == min(seg, p.shape[0] - 2) for i, p in enumerate(probs))
+        b.init_gaussian()
+        b.step_imag(12)
+        out[seg] = [b.get_psi(i).astype(np.complex128) for i in range(len(probs))]
+        b.close()
+    b = Batch(probs, "f32", "complex")
+    with pytest.raises(N.GPError) as e:
+        b.set_segments(-1)
+    assert e.value.status == N.GP_ERR_ARG
+    b.close()
+    for i, p in enumerate(probs):
+        ref = oracle.gaussian(p.shape, p.d, p.omega)
+        oracle.step(ref, p.d, p.dt, p.omega, p.g, False, 12)
+        scale = float(np.max(np.abs(ref)))
+        for seg in (24, 7):
+            assert float(np.max(np.abs(out[seg][i] - out[0][i]))) <= 1e-6 * scale, (p.name, seg)
+        assert float(np.max(np.abs(out[7][i] - ref))) <= 1e-5 * scale, p.name
+
+
+@pytest.mark.parametrize("field", ["complex", "real"])
+def test_batch_stream_groups_are_bit_identical(field):
+    """Independent instance groups on their own streams (forked and joined
+    by events, captured as parallel graph branches) change no result: every
+    instance's launches and norm order are the same with 1, 3 or 16 groups."""
+    from paper_1601_04641_gb300 import _native as N
+    from paper_1601_04641_gb300.solver import Batch
+    probs = uneven(7, seed=5, scale=0.5)
+    out = {}
+    for streams in (1, 3, 16):
+        b = Batch(probs, "f32", field)
+        b.set_streams(streams)
+        b.init_gaussian()
+        b.step_imag(23)  # graph blocks of 16, then 7 single launches
+        out[streams] = ([b.get_psi(i) for i in range(len(probs))], [o["norm"] for o in b.observables()])
+        b.close()
+    for streams in (3, 16):
+        for i in range(len(probs)):
+            assert np.array_equal(out[streams][0][i], out[1][0][i]), (streams, i)
+        assert out[streams][1] == out[1][1]
+    b = Batch(probs, "f32", field)
+    for bad in (0, 17):
+        with pytest.raises(N.GPError) as e:
+            b.set_streams(bad)
+        assert e.value.status == N.GP_ERR_ARG
+    b.close()
