@@ -34,6 +34,12 @@
  *       (the exact discrete Rayleigh quotient of the CN Laplacian).
  *   R5  first-order (Lie) splitting: kick, then x, y, z sweeps, each with
  *       the full dt; imaginary time then renormalises.
+ *   R20 lower-dimensional condensates (the 1D and 2D programs of the
+ *       predecessor package): an axis with a single node is absent.  It
+ *       has no line solve, no links and no boundary nodes, its coordinate
+ *       is 0 (so it adds nothing to V), and the cell measure dV is the
+ *       product of the present axes' spacings; g is then the 1D or 2D
+ *       coupling of the same equation R1 in the present coordinates.
  *
  * Imaginary time uses t -> -i tau, so the kick is exp(-dt (V + g|psi|^2))
  * and each sweep is CN for dpsi/dtau = (1/2) d^2 psi / dx^2; real time uses
@@ -80,11 +86,30 @@ static double node_coord(int idx, int n, double d)
 
 static int valid_grid(const int n[3], const double d[3])
 {
+    int present = 0;
     for (int a = 0; a < 3; a++) {
-        if (n[a] < 3 || !(d[a] > 0.0) || !isfinite(d[a]))
+        if ((n[a] < 3 && n[a] != 1) || !(d[a] > 0.0) || !isfinite(d[a]))
             return 0;
+        present += n[a] > 1;
     }
-    return 1;
+    return present > 0;
+}
+
+/* Cell measure: the product of the present axes' spacings (reading R20). */
+static double cell_volume(const int n[3], const double d[3])
+{
+    double v = 1.0;
+    for (int a = 0; a < 3; a++)
+        if (n[a] > 1)
+            v *= d[a];
+    return v;
+}
+
+/* Whether index idx is a boundary node of an axis of n nodes (R3); an
+ * absent axis (n = 1, R20) has none. */
+static int boundary(int idx, int n)
+{
+    return n > 1 && (idx == 0 || idx == n - 1);
 }
 
 static size_t n_sites(const int n[3])
@@ -174,20 +199,21 @@ int oracle_gaussian(const int n[3], const double d[3], const double omega[3], do
         for (int j = 0; j < n[1]; j++)
             for (int k = 0; k < n[2]; k++) {
                 double v = 0.0;
-                int edge = (i == 0 || i == n[0] - 1 || j == 0 || j == n[1] - 1 ||
-                            k == 0 || k == n[2] - 1);
+                int edge = boundary(i, n[0]) || boundary(j, n[1]) || boundary(k, n[2]);
                 if (!edge) {
                     double x = node_coord(i, n[0], d[0]);
                     double y = node_coord(j, n[1], d[1]);
                     double z = node_coord(k, n[2], d[2]);
-                    v = pow(omega[0] / M_PI, 0.25) * exp(-0.5 * omega[0] * x * x) *
-                        pow(omega[1] / M_PI, 0.25) * exp(-0.5 * omega[1] * y * y) *
-                        pow(omega[2] / M_PI, 0.25) * exp(-0.5 * omega[2] * z * z);
+                    /* an absent axis contributes no factor (R20) */
+                    double fx = n[0] > 1 ? pow(omega[0] / M_PI, 0.25) * exp(-0.5 * omega[0] * x * x) : 1.0;
+                    double fy = n[1] > 1 ? pow(omega[1] / M_PI, 0.25) * exp(-0.5 * omega[1] * y * y) : 1.0;
+                    double fz = n[2] > 1 ? pow(omega[2] / M_PI, 0.25) * exp(-0.5 * omega[2] * z * z) : 1.0;
+                    v = fx * fy * fz;
                 }
                 psi[site(n, i, j, k)] = v;
                 sum += v * v;
             }
-    double dv = d[0] * d[1] * d[2];
+    double dv = cell_volume(n, d);
     double scale = 1.0 / sqrt(dv * sum);
     for (size_t s = 0; s < n_sites(n); s++)
         psi[s] *= scale;
@@ -237,6 +263,8 @@ int oracle_sweep(const int n[3], const double d[3], double *psi_ri, int axis, do
     cplx *psi = (cplx *)psi_ri;
     const int len = n[axis];
     const int m_int = len - 2;
+    if (len == 1)
+        return ORACLE_OK; /* an absent axis has no line solve (R20) */
     const cplx c = (realtime ? I : 1.0) * dt / (4.0 * d[axis] * d[axis]);
 
     /* The two axes that label the lines, and the strides of all three. */
@@ -302,7 +330,7 @@ static double grid_norm(const int n[3], const double d[3], const cplx *psi)
     double sum = 0.0;
     for (size_t s = 0; s < n_sites(n); s++)
         sum += creal(psi[s] * conj(psi[s]));
-    return d[0] * d[1] * d[2] * sum;
+    return cell_volume(n, d) * sum;
 }
 
 /* Imaginary-time renormalisation psi <- psi / sqrt(norm). */
@@ -409,7 +437,7 @@ int oracle_observables(const int n[3], const double d[3], const double *psi_ri,
                     links[2] += creal(df * conj(df));
                 }
             }
-    const double dv = d[0] * d[1] * d[2];
+    const double dv = cell_volume(n, d);
     double norm = dv * s_rho;
     if (!(norm > 0.0))
         return ORACLE_EARG;

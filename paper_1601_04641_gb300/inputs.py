@@ -113,7 +113,8 @@ def batch_problems(count=64, seed=0, g_max=200.0) -> List[Problem]:
 
 
 def random_field(shape, seed=0, complex_=True, envelope=True) -> np.ndarray:
-    """A seeded random field that is zero on the boundary nodes.
+    """A seeded random field that is zero on the boundary nodes (of the axes
+    with more than one node).
 
     With ``envelope`` the values are a smooth bump times (1 + 0.25 noise) with a
     random phase, which resembles a perturbed condensate; without it they are
@@ -124,7 +125,8 @@ def random_field(shape, seed=0, complex_=True, envelope=True) -> np.ndarray:
     re = rng.standard_normal((nx, ny, nz))
     im = rng.standard_normal((nx, ny, nz)) if complex_ else None
     if envelope:
-        ax = [np.linspace(-1.0, 1.0, n) for n in (nx, ny, nz)]
+        # an axis of one node (an absent axis of a 1D or 2D grid) sits at the centre
+        ax = [np.linspace(-1.0, 1.0, n) if n > 1 else np.zeros(1) for n in (nx, ny, nz)]
         bump = (np.cos(0.5 * math.pi * ax[0])[:, None, None] *
                 np.cos(0.5 * math.pi * ax[1])[None, :, None] *
                 np.cos(0.5 * math.pi * ax[2])[None, None, :])
@@ -137,10 +139,10 @@ def random_field(shape, seed=0, complex_=True, envelope=True) -> np.ndarray:
     else:
         f = re + 1j * im if complex_ else re
     f = np.array(f, dtype=np.complex128 if complex_ else np.float64)
-    f[0, :, :] = 0
-    f[-1, :, :] = 0
-    f[:, 0, :] = 0
-    f[:, -1, :] = 0
-    f[:, :, 0] = 0
-    f[:, :, -1] = 0
+    for axis, n in enumerate((nx, ny, nz)):
+        if n > 1:  # an axis of one node has no boundary nodes
+            sl = [slice(None)] * 3
+            for end in (0, -1):
+                sl[axis] = end
+                f[tuple(sl)] = 0
     return f

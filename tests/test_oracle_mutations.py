@@ -30,7 +30,7 @@ MUTATIONS = {
                                       "x[m] = dp[m] + cp[m] * x[m + 1];"),
     "thomas forward sign": ("dp[m] = (rhs[m] - sub[m] * dp[m - 1]) / den;",
                             "dp[m] = (rhs[m] + sub[m] * dp[m - 1]) / den;"),
-    "norm without dV": ("return d[0] * d[1] * d[2] * sum;", "return sum;"),
+    "norm without dV": ("return cell_volume(n, d) * sum;", "return sum;"),
     "kinetic without 1/2": ("double kin = 0.5 * dv *", "double kin = dv *"),
     "mu with half interaction": ("out[1] = (kin + pot + g * inter) / norm;",
                                  "out[1] = (kin + pot + 0.5 * g * inter) / norm;"),
