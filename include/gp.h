@@ -77,9 +77,22 @@ typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_precision; /* element precision of ps
 typedef enum { GP_COMPLEX = 0, GP_REAL = 1 } gp_field;
 
 typedef struct {
-    int nx, ny, nz;       /* nodes per axis, each >= 3 */
-    double dx, dy, dz;    /* spacings, > 0 */
+    int nx, ny, nz;       /* nodes per axis: nx >= 3; ny, nz >= 3, or 1 for an
+                             absent axis (see below) */
+    double dx, dy, dz;    /* spacings, > 0 (ignored for an absent axis) */
 } gp_grid;
+
+/* Lower-dimensional condensates (the 1D and 2D programs of the paper's
+ * predecessor package, on which the 3D programs build): a y or z axis of
+ * one node is absent.  It has no line solve, no links and no boundary
+ * nodes, its coordinate is 0 (its trap frequency does not enter), and it
+ * adds no spacing to the cell measure dV, so the norm is the 1D or 2D
+ * integral and g is the 1D or 2D coupling of the same equation in the
+ * present coordinates.  1D: (nx, 1, 1); 2D: (nx, ny, 1) or (nx, 1, nz) --
+ * the latter keeps the stride-1 axis present, which the z sweep's TMA form
+ * needs.  With nz = 1 the z stage of imaginary time is a norm reduction
+ * only.  The single-condensate calls take these grids; the batched form and
+ * gp_observables_noalloc take 3D grids. */
 
 /* Observables of the current psi (paper, "Summary of revisions": norm,
  * rms radii from calcrms, chemical potential and energy from calcmuen),

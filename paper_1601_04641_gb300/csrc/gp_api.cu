@@ -166,7 +166,9 @@ gp_status check_args(gp_grid grid, double dt, double gamma, double nu, double la
     const int n[3] = {grid.nx, grid.ny, grid.nz};
     const double d[3] = {grid.dx, grid.dy, grid.dz};
     for (int a = 0; a < 3; ++a) {
-        if (n[a] < 3) return fail(nullptr, GP_ERR_ARG, "every axis needs at least 3 nodes");
+        // a y or z axis of one node is absent (1D and 2D condensates)
+        if (n[a] < 3 && !(a > 0 && n[a] == 1))
+            return fail(nullptr, GP_ERR_ARG, "nx needs at least 3 nodes, ny and nz at least 3 or exactly 1");
         if (!finite_pos(d[a])) return fail(nullptr, GP_ERR_ARG, "spacings must be finite and > 0");
     }
     if ((long long)n[0] * n[1] * n[2] > (1LL << 40))
@@ -243,7 +245,7 @@ gp_status alloc_scratch(gp_handle h) {
     prepare_field_launches();
     // z sweep: at most one block per 32 (line, segment) threads, segments of >= 1 node
     size_t cap = kNormBlocks;
-    cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32) * (size_t)(h->n[2] - 2));
+    if (h->n[2] > 1) cap = std::max(cap, blocks_for(sweep_lines(h, 2), 32) * (size_t)(h->n[2] - 2));
     FieldArgs fa = handle_field_args(h);
     cap = std::max(cap, (size_t)observables_blocks(fa) * 9);
     if (gpcn::dev_malloc(&h->d_partials, cap * sizeof(double)) != cudaSuccess ||
@@ -299,8 +301,8 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
     h->n[1] = grid.ny;
     h->n[2] = grid.nz;
     h->d[0] = grid.dx;
-    h->d[1] = grid.dy;
-    h->d[2] = grid.dz;
+    h->d[1] = grid.ny > 1 ? grid.dy : 1.0;  // an absent axis adds no spacing to the cell measure
+    h->d[2] = grid.nz > 1 ? grid.dz : 1.0;
     h->dt = dt;
     h->w[0] = gamma;
     h->w[1] = nu;
@@ -407,8 +409,26 @@ void segments(gp_handle h, int ax, int window, int *seg_len, int *n_seg) {
                     h->seg_override[ax], seg_len, n_seg);
 }
 
+// The stage of an absent axis (one node: a 1D or 2D condensate) solves no
+// lines.  Its bookkeeping stays: in imaginary time the z stage's norm and
+// renormalisation factor come from a reduction over the last sweep's output;
+// in symmetric real time the trailing half kick becomes pending.
+gp_status absent_stage(gp_handle h, int stage, bool realtime) {
+    if (stage != 2) return GP_OK;
+    if (!realtime) {
+        FieldArgs a = field_args(geom(h), h->buf[h->cur], h->d_scal + S_ONE, h->d_partials, h->d_counter,
+                                 h->d_obs, h->d_scal + S_SCALE, h->d_scal + S_NORM_SWEEP);
+        GP_CK(h, launch_norm(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
+        h->scale_pending = true;
+    } else if (h->splitting == 2) {
+        h->kick_pending = true;
+    }
+    return GP_OK;
+}
+
 // One stage of a step: 0 = kick + x sweep, 1 = y sweep, 2 = z sweep + norm.
 gp_status run_stage(gp_handle h, int stage, bool realtime) {
+    if (h->n[stage] == 1) return absent_stage(h, stage, realtime);
     SweepLaunch L;
     L.prec = h->prec == GP_F32 ? P_F32 : P_F64;
     L.form = realtime ? F_REALTIME : (h->field == GP_REAL ? F_IMAG_REAL : F_IMAG_CPLX);
@@ -974,7 +994,7 @@ gp_status gp_set_window(gp_handle h, int window) {
         for (int mode = 0; mode < modes_of(h); ++mode)
             for (int ax = 0; ax < 3; ++ax) {
                 const AxisTables &at = h->tab.ax[mode][ax];
-                if (at.min_window == 0 || window < at.min_window)
+                if (h->n[ax] > 1 && (at.min_window == 0 || window < at.min_window))
                     return fail(h, GP_ERR_ARG, "window too small for the accuracy of this dt");
             }
     }
@@ -994,7 +1014,7 @@ gp_status gp_set_axis_window(gp_handle h, int axis, int window) {
         return fail(h, GP_ERR_ARG, "window must be -1 (automatic), 0, 4, 8 or 16");
     for (int mode = 0; mode < modes_of(h); ++mode) {
         const AxisTables &at = h->tab.ax[mode][axis];
-        if (window > 0 && (at.min_window == 0 || window < at.min_window))
+        if (h->n[axis] > 1 && window > 0 && (at.min_window == 0 || window < at.min_window))
             return fail(h, GP_ERR_ARG, "window too small for the accuracy of this dt");
     }
     for (int mode = 0; mode < modes_of(h); ++mode)
@@ -1172,6 +1192,7 @@ gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) 
     GP_CK(h, cudaEventCreate(&e0));
     GP_CK(h, cudaEventCreate(&e1));
     for (int ax = 0; ax < 3 && st == GP_OK; ++ax) {
+        if (h->n[ax] == 1) continue;  // an absent axis has no sweep
         const std::string key = tune_key(h, realtime, ax);
         TuneChoice best{h->threads[ax], h->seg_override[ax], ax < 2 ? h->max_lpt[ax] : 1};
         if (cache_lookup(path, key, &best)) {

@@ -47,11 +47,12 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
     for (int mode = 0; mode < modes; ++mode) {
         for (int ax = 0; ax < 3; ++ax) {
             const size_t esz = (mode == 1 ? 2 : 1) * rsz;
+            const size_t nint = G.n[ax] > 2 ? (size_t)(G.n[ax] - 2) : 0;  // an absent axis has none
             AxisTables &at = T.ax[mode][ax];
             at.off_cp = off;
-            off = align_up(off + esz * (G.n[ax] - 2), 256);
+            off = align_up(off + esz * nint, 256);
             at.off_ip = off;
-            off = align_up(off + esz * (G.n[ax] - 2), 256);
+            off = align_up(off + esz * nint, 256);
         }
     }
     for (int ax = 0; ax < 3; ++ax) {
@@ -79,6 +80,7 @@ void append_tables(const Geometry &G, bool f32, int modes, std::vector<char> &ho
     for (int mode = 0; mode < modes; ++mode) {
         for (int ax = 0; ax < 3; ++ax) {
             const int n = G.n[ax] - 2;
+            if (n < 1) continue;  // an absent axis (one node) has no line solve
             const double kap = G.dt / (4.0 * G.d[ax] * G.d[ax]);
             const std::complex<double> c = mode == 1 ? std::complex<double>(0.0, kap)
                                                      : std::complex<double>(kap, 0.0);
@@ -137,6 +139,10 @@ long long axis_lines(const Geometry &G, int ax) {
 void choose_segments(const Geometry &G, int ax, int window, int lpt, int elem_bytes, bool contiguous_z,
                      int override_len, int *seg_len, int *n_seg) {
     const int n = G.n[ax] - 2;
+    if (n < 1) {  // an absent axis (one node) has no line solve
+        *seg_len = *n_seg = 0;
+        return;
+    }
     const int chunk = (elem_bytes * lpt >= 16) ? 8 : 16;
     int len = n;
     if (window > 0) {

@@ -44,13 +44,18 @@ __global__ void gaussian_kernel(FieldArgs a) {
     using E = Elem<R, CPLX>;
     typename E::V *psi = static_cast<typename E::V *>(a.psi);
     const double pi = 3.14159265358979323846;
-    const double c0 = pow(a.w[0] / pi, 0.25) * pow(a.w[1] / pi, 0.25) * pow(a.w[2] / pi, 0.25);
+    // an absent axis (one node: 1D and 2D condensates) contributes no factor
+    // and has no boundary nodes
+    double c0 = 1.0;
+    for (int q = 0; q < 3; ++q)
+        if (a.n[q] > 1) c0 *= pow(a.w[q] / pi, 0.25);
+    auto inside = [](int idx, int n) { return n == 1 || (idx > 0 && idx < n - 1); };
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < a.sites; s += grid_stride()) {
         const int k = (int)(s % a.n[2]);
         const int j = (int)((s / a.n[2]) % a.n[1]);
         const int i = (int)(s / ((long long)a.n[2] * a.n[1]));
         double v = 0.0;
-        if (i > 0 && i < a.n[0] - 1 && j > 0 && j < a.n[1] - 1 && k > 0 && k < a.n[2] - 1) {
+        if (inside(i, a.n[0]) && inside(j, a.n[1]) && inside(k, a.n[2])) {
             const double x = a.origin[0] + i * a.d[0];
             const double y = a.origin[1] + j * a.d[1];
             const double z = a.origin[2] + k * a.d[2];
