@@ -196,7 +196,11 @@ gp_status gp_run_imag_schedule(gp_handle h, int levels, const double *dt_scale, 
 gp_status gp_set_stop_rule(gp_handle h, int rule);
 
 /* Compute the observables of the current psi into *out (synchronises).
- * GP_ERR_NONFINITE if any reduction is NaN or Inf. */
+ * GP_ERR_NONFINITE if any reduction is NaN or Inf.  GP_ERR_TIMEOUT if the
+ * FP32 observables kernel gave up waiting for its bulk copies (each wait is
+ * bounded to about a second): *out is then invalid, psi is unchanged and
+ * usable; or if a sweep kernel's wait expired since the last check (see
+ * gp_sync). */
 gp_status gp_observables(gp_handle h, gp_obs *out);
 
 /* Track observables during stepping: after every `every` steps of
@@ -515,13 +519,16 @@ const char *gp_last_error(gp_handle h);
  * gp_debug_fail_alloc(n) makes the n-th next device allocation of the library
  * fail as if the device were out of memory (n <= 0: no failure); every
  * creating call then returns GP_ERR_NOMEM and frees what it had allocated.
- * gp_debug_raise_status(h) sets the handle's device status word from the
- * host, as a sweep kernel does when a bounded wait expires (nothing waits or
- * faults on the device): the next synchronising call reports
- * GP_ERR_TIMEOUT and psi is lost until set again (see gp_sync). */
+ * gp_debug_raise_status(h, bits) or-s `bits` into the handle's device status
+ * word from the host, as a kernel does when a bounded wait expires (nothing
+ * waits or faults on the device): 1 as a sweep kernel does, 2 as the
+ * observables kernel does (3: both); GP_ERR_ARG for other bits.  The next
+ * synchronising call reports GP_ERR_TIMEOUT; with bit 1, psi is lost until
+ * set again (see gp_sync); with bit 2 alone, only the observables computed
+ * since are invalid and psi stays usable. */
 gp_status gp_selftest_bounded_wait(long long cycles, void *cuda_stream, int *completed, int *expired);
 void gp_debug_fail_alloc(int n);
-gp_status gp_debug_raise_status(gp_handle h);
+gp_status gp_debug_raise_status(gp_handle h, unsigned int bits);
 
 /* Library version string. */
 const char *gp_version(void);

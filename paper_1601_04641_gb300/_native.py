@@ -67,7 +67,7 @@ SIGNATURES = {
     "gp_set_splitting": (_i, [Handle, _i]),
     "gp_selftest_bounded_wait": (_i, [ctypes.c_longlong, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "gp_debug_fail_alloc": (None, [_i]),
-    "gp_debug_raise_status": (_i, [Handle]),
+    "gp_debug_raise_status": (_i, [Handle, ctypes.c_uint]),
     "gp_run_imag_schedule": (_i, [Handle, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, _i,
                                   ctypes.POINTER(_i)]),
     "gp_get_tma": (_i, [Handle, ctypes.POINTER(_i)]),

@@ -235,8 +235,10 @@ long long sweep_lines(gp_handle h, int ax) { return axis_lines(geom(h), ax); }
 size_t blocks_for(long long items, int threads) { return (size_t)((items + threads - 1) / threads); }
 
 FieldArgs handle_field_args(gp_handle h) {
-    return field_args(geom(h), h->buf[h->cur], h->d_scal + (h->scale_pending ? S_SCALE : S_ONE),
-                      h->d_partials, h->d_counter, h->d_obs, h->d_scal + S_SCALE, h->d_scal + S_NORM_INIT);
+    FieldArgs a = field_args(geom(h), h->buf[h->cur], h->d_scal + (h->scale_pending ? S_SCALE : S_ONE),
+                             h->d_partials, h->d_counter, h->d_obs, h->d_scal + S_SCALE, h->d_scal + S_NORM_INIT);
+    a.status = h->d_status;
+    return a;
 }
 
 constexpr int kNormBlocks = 152 * 4;
@@ -384,8 +386,14 @@ gp_status check_status(gp_handle h) {
     GP_CK(h, cudaMemcpy(&flag, h->d_status, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag) {
         cudaMemset(h->d_status, 0, sizeof(flag));
-        h->psi_lost = true;
-        return fail(h, GP_ERR_TIMEOUT, "a sweep kernel's wait for its TMA copies expired; psi is lost until set again");
+        if (flag & 1u) {
+            h->psi_lost = true;
+            return fail(h, GP_ERR_TIMEOUT,
+                        "a sweep kernel's wait for its TMA copies expired; psi is lost until set again");
+        }
+        return fail(h, GP_ERR_TIMEOUT,
+                    "the observables kernel's wait for its bulk copies expired; these observables are invalid "
+                    "(psi is unchanged)");
     }
     return GP_OK;
 }
@@ -1112,10 +1120,11 @@ gp_status gp_psi_device_ptr(gp_handle h, void **ptr, int *pending_scale) {
     return GP_OK;
 }
 
-gp_status gp_debug_raise_status(gp_handle h) {
+gp_status gp_debug_raise_status(gp_handle h, unsigned int bits) {
+    if (!h || bits == 0u || bits > 3u) return fail(h, GP_ERR_ARG, "status bits must be 1, 2 or 3");
     gp_status st = enter(h);
     if (st != GP_OK) return st;
-    const unsigned int flag = 1u;
+    const unsigned int flag = bits;
     GP_CK(h, cudaMemcpyAsync(h->d_status, &flag, sizeof(flag), cudaMemcpyHostToDevice, h->stream));
     GP_CK(h, cudaStreamSynchronize(h->stream));
     return GP_OK;

@@ -55,7 +55,7 @@ struct SweepArgs {
     double *scale_out;     // 1 / sqrt(norm) when want_scale
     double dV;
     int want_scale;
-    unsigned int *status;  // set to nonzero by a kernel whose bounded wait expired (may be null)
+    unsigned int *status;  // 1 is or-ed in by a sweep kernel whose bounded wait expired (may be null)
 };
 
 // Tensor maps of the z sweep's input and output arrays, each a 2D array of
@@ -118,6 +118,7 @@ struct FieldArgs {
     double *scale_out;
     double *norm_out;
     long long sites;
+    unsigned int *status;  // 2 is or-ed in by an observables kernel whose bounded wait expired (may be null)
 };
 
 cudaError_t launch_gaussian(Prec p, bool cplx, const FieldArgs &a, cudaStream_t s);

@@ -33,6 +33,7 @@
 
 #include <type_traits>
 
+#include "gp_async.cuh"
 #include "gp_sweep.cuh"
 
 namespace gpcn {
@@ -46,7 +47,6 @@ constexpr int kTmaRows = 64;                         // lines per warp (two per 
 constexpr int kTmaRowBytes = 64;                     // one box row = one swizzle span
 constexpr int kTmaBoxBytes = kTmaRows * kTmaRowBytes;
 constexpr int kTmaAhead = 3;                         // boxes in flight beyond the one needed
-constexpr long long kTmaSpinCycles = 1LL << 31;
 static_assert(kTmaWarps * kTmaRows == kTmaBlockRows, "rows per block of the TMA z sweep");
 
 template <typename E> __host__ __device__ constexpr int tma_chunk() { return kTmaRowBytes / (int)sizeof(E); }
@@ -82,42 +82,6 @@ template <class F, int W> inline bool tma_usable(const SweepArgs &a) {
     }
 }
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// Wait for the phase of `bar` with the given parity, for at most `cycles`
-// clock cycles (none at all once `ok` is false).  Returns false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, bool ok,
-                                                  long long cycles = kTmaSpinCycles) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (!ok) return false;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > cycles) return false;
-    return true;
-}
 __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(

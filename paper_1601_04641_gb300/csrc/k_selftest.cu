@@ -6,15 +6,6 @@
 namespace gpcn {
 namespace {
 
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-    asm volatile(
-        "{\n"
-        ".reg .b64 state;\n"
-        "mbarrier.arrive.shared::cta.b64 state, [%0];\n"
-        "}\n" ::"r"(bar)
-        : "memory");
-}
-
 // One warp: a bounded wait on an mbarrier whose phase completes (lane 0
 // arrives first) and one on an mbarrier that nothing arrives at.  Nothing is
 // copied, so the second wait can only run out; it gives up after `cycles`.

@@ -44,7 +44,7 @@ def test_reported_timeout_loses_psi_until_it_is_set_again():
     gp = GP((16, 14, 32), (0.3, 0.3, 0.3), 0.01, (1, 1, 1), 1.0, "f32", "complex")
     gp.init_gaussian()
     gp.step_imag(2)
-    assert gp.lib.gp_debug_raise_status(gp.h) == N.GP_OK
+    assert gp.lib.gp_debug_raise_status(gp.h, 1) == N.GP_OK
     with pytest.raises(N.GPError) as e:
         gp.sync()
     assert e.value.status == N.GP_ERR_TIMEOUT
@@ -55,6 +55,29 @@ def test_reported_timeout_loses_psi_until_it_is_set_again():
     gp.init_gaussian()  # psi set again: usable
     gp.step_imag(3)
     assert abs(gp.observables()["norm"] - 1.0) < 1e-5
+    gp.close()
+
+
+def test_reported_observables_timeout_keeps_psi():
+    """An expired wait of the observables kernel (status 2) invalidates that
+    call's observables only: psi stays usable and the next call succeeds."""
+    from paper_1601_04641_gb300.solver import GP
+    gp = GP((16, 14, 32), (0.3, 0.3, 0.3), 0.01, (1, 1, 1), 1.0, "f32", "complex")
+    gp.init_gaussian()
+    gp.step_imag(2)
+    ref = gp.observables()
+    for bad in (0, 4, 7):
+        with pytest.raises(N.GPError) as e:
+            N.check(gp.lib.gp_debug_raise_status(gp.h, bad), gp.h)
+        assert e.value.status == N.GP_ERR_ARG
+    assert gp.lib.gp_debug_raise_status(gp.h, 2) == N.GP_OK
+    with pytest.raises(N.GPError) as e:
+        gp.observables()
+    assert e.value.status == N.GP_ERR_TIMEOUT
+    again = gp.observables()
+    assert again["mu"] == ref["mu"] and again["norm"] == ref["norm"]
+    gp.step_imag(1)
+    gp.get_psi()
     gp.close()
 
 

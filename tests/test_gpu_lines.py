@@ -8,9 +8,10 @@ against the FP64 oracle on the same seeded inputs (GPU only).
   form into 16-node chunks; both windowed solves are exact to roundoff).
 - Junk in the end nodes of x and y lines is never read and zeros are
   written there (reading R3 of the boundary).
-- The packed complex64 observables (nz even) agree with the oracle and with
-  the FP64 kernel on the same field, on grids that span several work items
-  with ragged tails.
+- The FP32 observables (for real fields the bulk-copy kernel where a plane
+  is whole 16-byte units and a stage fits; the other kernels elsewhere)
+  agree with the oracle and with the FP64 kernel on the same field, on grids
+  that span several tiles or work items with ragged tails.
 """
 import numpy as np
 import pytest
@@ -134,6 +135,29 @@ def test_observables_complex64_match_oracle_and_fp64(shape):
     for k in OBS:
         assert abs(got["f64"][k] - ref[k]) <= 1e-12 * abs(ref[k]), (k, got["f64"][k], ref[k])
         assert abs(got["f32"][k] - ref[k]) <= 1e-6 * abs(ref[k]), (k, got["f32"][k], ref[k])
+
+
+# FP32 real fields through the bulk-copy kernel (planes of whole 16-byte
+# units, a stage of tile + nz + 1 sites within 12 KB): tiles of 1024 sites,
+# several tiles with a ragged last one, planes smaller than a tile, runs of
+# planes that start inside a column, nz at the stage limit (2046); shapes
+# just past the limit or with planes that are not whole 16-byte units (the
+# per-(j, k) kernel); complex64 grids (the packed and per-(j, k) kernels)
+@pytest.mark.parametrize("field,shape", [
+    ("complex", (70, 33, 50)), ("complex", (9, 5, 6)), ("complex", (5, 3, 510)),
+    ("complex", (5, 3, 512)), ("complex", (23, 45, 47)),
+    ("real", (70, 36, 50)), ("real", (33, 52, 84)), ("real", (4, 4, 2046)),
+    ("real", (4, 4, 2048)), ("real", (41, 27, 37)), ("real", (6, 6, 1030))])
+def test_observables_fp32_match_oracle(field, shape):
+    psi0 = inputs.random_field(shape, seed=14, complex_=(field == "complex"))
+    psi32 = psi0.astype(np.complex64 if field == "complex" else np.float32)
+    ref = oracle.observables(psi32.astype(np.complex128), D, OMEGA, 25.0)
+    gp = make(shape, D, 0.01, OMEGA, 25.0, "f32", field)
+    gp.set_psi(psi32)
+    got = gp.observables()
+    gp.close()
+    for k in OBS:
+        assert abs(got[k] - ref[k]) <= 1e-6 * abs(ref[k]), (k, got[k], ref[k])
 
 
 def test_observables_complex64_with_pending_scale():
