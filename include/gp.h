@@ -282,6 +282,21 @@ gp_status gp_get_lines_per_thread(gp_handle h, int mode, int lines[3]);
 gp_status gp_set_tma(gp_handle h, int on);
 gp_status gp_get_tma(gp_handle h, int *in_use);
 
+/* The x and y sweeps (strided axes) reading through tensor-memory-
+ * accelerator boxes (1, the default): a warp streams 32 adjacent line groups
+ * (1, 2 or 4 lines each, as gp_set_lines_per_thread gives) in boxes of one
+ * chunk of nodes x 32 groups, one bulk tensor copy each; or through
+ * per-thread asynchronous copies (0).  Results are stored by the threads in
+ * both forms.  The TMA form is taken where a windowed solve runs (window >
+ * 0), the line groups of one plane (x) or one row of planes (y: nz / lines
+ * per thread) are a multiple of 32, and a line's node stride is a multiple
+ * of 16 bytes; elsewhere the other form runs.  Both forms do the same
+ * arithmetic in the same order, so their results are identical.
+ * gp_get_tma_lines gives the axes that take it in either mode under the
+ * current settings (bit 0: x, bit 1: y). */
+gp_status gp_set_tma_lines(gp_handle h, int on);
+gp_status gp_get_tma_lines(gp_handle h, int *axes);
+
 /* Threads per block of the line-solve kernel of one axis (multiple of 32,
  * 32..256). */
 gp_status gp_set_threads(gp_handle h, int axis, int threads);

@@ -63,6 +63,8 @@ SIGNATURES = {
     "gp_set_lines_per_thread": (_i, [Handle, _i, _i]),
     "gp_get_lines_per_thread": (_i, [Handle, _i, ctypes.POINTER(_i)]),
     "gp_set_tma": (_i, [Handle, _i]),
+    "gp_set_tma_lines": (_i, [Handle, _i]),
+    "gp_get_tma_lines": (_i, [Handle, ctypes.POINTER(_i)]),
     "gp_set_stop_rule": (_i, [Handle, _i]),
     "gp_set_splitting": (_i, [Handle, _i]),
     "gp_selftest_bounded_wait": (_i, [ctypes.c_longlong, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),

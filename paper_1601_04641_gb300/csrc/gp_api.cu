@@ -117,6 +117,7 @@ struct gp_handle_s {
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     bool tma_z = true;         // ... through TMA tiles where the grid allows it
+    bool tma_lines = true;     // x and y sweeps through TMA boxes where the grid allows it
     int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol; 2 rule 1 twice in a row
     int splitting = 1;         // real time: 1 Lie (kick, sweeps), 2 symmetric (half kick, sweeps, half kick)
     bool kick_pending = false; // symmetric splitting: buf[cur] still lacks its trailing half kick
@@ -463,6 +464,13 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
         maps.in = h->zmap[h->cur];
         maps.out = h->zmap[h->cur ^ 1];
         L.tma = &maps;
+    }
+    TmaMaps lmaps;  // the strided TMA form reads through lmaps.in and stores lane by lane
+    std::memset(&lmaps, 0, sizeof(lmaps));
+    if (ax < 2 && h->tma_lines && line_tma_fits((int)h->elem, L.lpt, L.window, a.inner, a.stride, a.N)) {
+        const int box_nodes = h->elem * L.lpt >= 16 ? 8 : 16;  // the kernel's chunk of MemV nodes
+        if (encode_line_map(&lmaps.in, h->buf[h->cur], ax, h->n, (int)h->elem, L.lpt, box_nodes))
+            L.lmaps = &lmaps;
     }
     const int zthreads = L.contiguous ? 32 : L.threads;
     if (stage == 2 && blocks_for(a.n_lines, zthreads) * (size_t)a.n_seg > h->partial_cap)
@@ -1083,6 +1091,30 @@ gp_status gp_get_tma(gp_handle h, int *in_use) {
                  tma_z_fits((int)h->elem, w, h->n[2], n_seg, sweep_lines(h, 2))) ? 1 : 0;
     }
     *in_use = used;
+    return GP_OK;
+}
+
+gp_status gp_set_tma_lines(gp_handle h, int on) {
+    if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    h->tma_lines = on != 0;
+    drop_graphs(h);
+    return GP_OK;
+}
+
+gp_status gp_get_tma_lines(gp_handle h, int *axes) {
+    if (!h || !axes) return fail(h, GP_ERR_ARG, "bad arguments");
+    int used = 0;
+    for (int mode = 0; mode < modes_of(h); ++mode) {
+        for (int ax = 0; ax < 2; ++ax) {
+            if (h->n[ax] == 1) continue;
+            const int w = h->window[mode][ax];
+            const long long plane = (long long)h->n[1] * h->n[2];
+            const long long inner = ax == 0 ? plane : h->n[2];
+            if (h->tma_lines && line_tma_fits((int)h->elem, lines_per_thread(h, ax, w), w, inner, inner, h->n[ax]))
+                used |= 1 << ax;
+        }
+    }
+    *axes = used;
     return GP_OK;
 }
 

@@ -311,4 +311,39 @@ bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool line_tma_fits(int elem_bytes, int lpt, int window, long long inner, long long stride, int N) {
+    const int mv = elem_bytes * lpt;
+    if (window <= 0 || N < 3 || (mv != 4 && mv != 8 && mv != 16)) return false;
+    if (inner % (32LL * lpt) != 0) return false;
+    return (stride * elem_bytes) % 16 == 0;
+}
+
+// Words of 4 bytes: d0 = the elements of one node of an outer group, d1 =
+// the n interior nodes (origin at node 1), d2 = the outer groups (1 for x,
+// nx planes for y).  No swizzle: box row q (node) is 32 MemV contiguous in
+// shared memory.  Zero fill outside the array.
+bool encode_line_map(CUtensorMap *map, const void *psi, int axis, const int n[3], int elem_bytes, int lpt,
+                     int box_nodes) {
+    if (axis != 0 && axis != 1) return false;
+    const long long plane = (long long)n[1] * n[2];
+    const long long inner = axis == 0 ? plane : n[2];
+    const long long stride = axis == 0 ? plane : n[2];
+    const int N = n[axis];
+    if (!line_tma_fits(elem_bytes, lpt, 1, inner, stride, N)) return false;
+    const long long s1 = stride * elem_bytes;  // bytes between nodes of a line
+    const long long s2 = axis == 0 ? s1 * n[0] : plane * elem_bytes;
+    const unsigned char *node1 = static_cast<const unsigned char *>(psi) + s1;
+    if ((reinterpret_cast<uintptr_t>(node1) & 15u) != 0 || s2 % 16 != 0) return false;
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)(inner * elem_bytes / 4), (cuuint64_t)(N - 2),
+                                (cuuint64_t)(axis == 0 ? 1 : n[0])};
+    const cuuint64_t strides[2] = {(cuuint64_t)s1, (cuuint64_t)s2};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 * lpt * elem_bytes / 4), (cuuint32_t)box_nodes, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<unsigned char *>(node1), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace gpcn

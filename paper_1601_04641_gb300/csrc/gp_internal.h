@@ -95,6 +95,7 @@ struct SweepLaunch {
     int lpt;               // lines per thread of the strided kernel (1, or 2 or 4 adjacent lines)
     int contiguous;        // 1: warp-tiled kernel for the stride-1 axis
     const TmaMaps *tma = nullptr;  // z sweep through TMA tiles where the grid allows it
+    const TmaMaps *lmaps = nullptr;  // x or y sweep through TMA boxes (encode_line_map; windowed)
 };
 
 cudaError_t launch_sweep(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s);
@@ -172,6 +173,17 @@ void set_fail_alloc(int n);
 // elem_bytes (4 or 8) for the TMA z sweep; false if the layout does not allow
 // one (row pitch or base not 16-byte aligned) or the CUDA driver offers no encoder.
 bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, int elem_bytes);
+// Whether the x or y sweep (stride `stride` elements along the line, `inner`
+// lines per outer group) of elem_bytes elements, lpt lines per thread, can
+// take the strided TMA form: a windowed solve, line groups per outer group a
+// multiple of 32, a line stride of whole 16-byte units, and MemV of 4, 8 or
+// 16 bytes.
+bool line_tma_fits(int elem_bytes, int lpt, int window, long long inner, long long stride, int N);
+// Encode the tensor map of the strided TMA form over the array at `psi`
+// for axis 0 (x) or 1 (y) of an (nx, ny, nz) grid, boxes of 32 * lpt
+// elements x `box_nodes` nodes; false if the layout does not allow one.
+bool encode_line_map(CUtensorMap *map, const void *psi, int axis, const int n[3], int elem_bytes, int lpt,
+                     int box_nodes);
 constexpr int kReduceThreads = 256;
 
 }  // namespace gpcn

@@ -95,6 +95,13 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, unsigned sr
                  "r"(x), "r"(y), "r"(src)
                  : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, unsigned bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 // Wait until at most `pending` of this thread's newest bulk groups still read
 // shared memory (more than 3 waits for 3).
@@ -357,6 +364,148 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) sweep_tma_kernel(SweepArgs 
         v = tma_body<F, R, W>(a, &maps.in, &maps.out, base + warp * S * kTmaBoxBytes,
                               smem_u32(base + kTmaWarps * S * kTmaBoxBytes) + 8 * S * warp, (int)L0);
     norm_finalize(v, a, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------------------ strided axes through TMA
+// The x and y lines as a 3D array of 4-byte words [outer][node][word]: for
+// the x sweep one outer group (the y-z plane, ny*nz elements per node); for
+// the y sweep nx groups (planes) of nz elements per node.  The tensor map's
+// origin is node 1 of the line and its node extent the n = N - 2 interior
+// nodes, so every position outside [0, n) reads zeros (TMA fill).  A warp owns 32 consecutive line groups (LPT
+// adjacent lines each, one MemV per node) of one outer group and streams
+// them in boxes of B nodes x 32 MemV: one lane issues box b (positions
+// s0 + bB ...) into the warp's ring of kRingChunks slots, one mbarrier each,
+// and lane l reads column l of a box row -- one conflict-free shared-memory
+// row per node, no per-element copy or address arithmetic.  Results are
+// stored lane by lane (each warp store instruction writes one contiguous
+// row of 32 MemV).
+// Every wait is bounded; on expiry the warp stops waiting, finishes
+// without trusting its data and raises SweepArgs::status.
+constexpr int kLineTmaWarps = 4;  // warps per block
+
+template <typename MV, int B> __host__ __device__ constexpr int line_box_bytes() {
+    return B * 32 * (int)sizeof(MV);
+}
+template <typename MV> __host__ __device__ constexpr size_t line_tma_smem() {
+    return 128 + (size_t)kLineTmaWarps * (kRingChunks * line_box_bytes<MV, chunk_len<MV>()>() + 8 * kRingChunks);
+}
+
+template <class F, class M, typename R, int B, int KIND> struct TmaColumnIO {
+    using V = typename M::V;
+    using MV = typename M::MemV;
+    static constexpr int RC = kRingChunks, RL = RC * B;
+    static constexpr int BOXB = line_box_bytes<MV, B>();
+    const CUtensorMap *tin;
+    const MV *rp;     // this warp's ring: position p at rp[((p - s0) % RL) * 32 + lane]
+    unsigned ring_s, bar0;
+    int cx, cz, lane;
+    int s0, limit, issued, ready;
+    bool ok;
+    MV *out;          // the line group's node 0 in the output
+    long long st;
+    Hooks<F, M, R, KIND> hk;
+    __device__ __forceinline__ void issue() {
+        if (lane == 0) {
+            const unsigned slot = (unsigned)(issued % RC);
+            mbar_arrive_expect_tx(bar0 + 8 * slot, BOXB);
+            tma_load_3d(ring_s + slot * BOXB, tin, bar0 + 8 * slot, cx, s0 + issued * B, cz);
+        }
+        ++issued;
+    }
+    __device__ __forceinline__ void start(int first, int lim) {
+        s0 = first;
+        limit = lim;
+        issued = ready = 0;
+        ok = true;
+        while (issued < RC - 1 && s0 + issued * B < limit) issue();
+    }
+    // Make positions < p_end readable; keep up to two more boxes in flight.
+    // The box refilled into a slot is the one two boxes behind the newest
+    // readable one, which no later read needs, and the __syncwarp makes the
+    // whole warp done with it first.
+    __device__ __forceinline__ void need(int p_end) {
+        const int c = (p_end - 1 - s0) / B;
+        if (c < ready) return;
+        while (issued <= c) issue();  // not reached by the solve's access pattern; a guard
+        for (; ready <= c; ++ready) ok = mbar_wait_bounded(bar0 + 8 * (ready % RC), (ready / RC) & 1, ok) && ok;
+        __syncwarp();
+        while (issued <= c + RC - 2 && s0 + issued * B < limit) issue();
+    }
+    __device__ __forceinline__ V val(int p) const {
+        return hk.on_load(p, M::load(rp[((p - s0) & (RL - 1)) * 32 + lane]));
+    }
+    template <int NB> __device__ __forceinline__ void vals(int p, V (&v)[NB]) const {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q] = M::load(rp[((p + q - s0) & (RL - 1)) * 32 + lane]);
+        hk.on_load_chunk(p, v);
+    }
+    __device__ __forceinline__ void put(int t0, int q, V v) const {
+        out[(long long)(t0 + q + 1) * st] = M::store(v);
+        hk.on_store(v);
+    }
+    __device__ __forceinline__ void flush(int, int) const {}
+    // After an expired wait, a fresh bound for the loads that may still be
+    // landing before the shared memory is released.
+    __device__ __forceinline__ void finish(unsigned int *status) {
+        if (!ok) {
+            for (int b = max(0, issued - RC); b < issued; ++b) mbar_wait_bounded(bar0 + 8 * (b % RC), (b / RC) & 1, true);
+            if (lane == 0 && status) atomicOr(status, 1u);
+        }
+    }
+};
+
+// One warp per 32 line groups of one outer group (the host checks that the
+// line groups of an outer group are a multiple of 32); blockIdx.y is the
+// segment.  Windowed solves only.
+template <class F, typename R, int W, int KIND, int LPT>
+__global__ void __launch_bounds__(kLineTmaWarps * 32) sweep_lines_tma_kernel(SweepArgs a,
+                                                                             const __grid_constant__ TmaMaps maps) {
+    static_assert(W > 0 && KIND != K_Z, "strided windowed sweeps only");
+    using M = typename LinesPerThread<F, LPT>::M;
+    using MV = typename M::MemV;
+    using C = typename F::C;
+    constexpr int B = chunk_len<MV>();
+    constexpr int BOXB = line_box_bytes<MV, B>();
+    constexpr int RC = kRingChunks;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                            ~static_cast<uintptr_t>(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long L0 = ((long long)blockIdx.x * kLineTmaWarps + warp) * 32 * LPT;  // the warp's first line
+    if (L0 >= a.n_lines) return;  // warps are independent: no block-wide barrier below
+    unsigned char *wb = base + warp * RC * BOXB;
+    const unsigned bar0 = smem_u32(base + kLineTmaWarps * RC * BOXB) + 8 * RC * warp;
+    if (lane == 0) {
+        for (int q = 0; q < RC; ++q) mbar_init(bar0 + 8 * q, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const long long L = L0 + (long long)lane * LPT;
+    const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
+    MV *out = reinterpret_cast<MV *>(static_cast<typename F::V *>(a.psi_out) + off);
+    const long long st = a.stride / LPT;
+    const int n = a.N - 2;
+    const unsigned seg = blockIdx.y;
+    if (seg == 0) out[0] = M::store(M::zero());
+    if ((int)seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::store(M::zero());
+    Acc<R> acc;
+    TmaColumnIO<F, M, R, B, KIND> io;
+    io.tin = &maps.in;
+    io.rp = reinterpret_cast<const MV *>(wb);
+    io.ring_s = smem_u32(wb);
+    io.bar0 = bar0;
+    io.cx = (int)((L0 % a.inner) * (long long)sizeof(typename F::V) / 4);
+    io.cz = (int)(L0 / a.inner);
+    io.lane = lane;
+    io.out = out;
+    io.st = st;
+    io.hk.acc = &acc;
+    io.hk.init(a, L);
+    const int tb = seg * a.seg_len;
+    const int te = (int)seg == a.n_seg - 1 ? n : tb + a.seg_len;
+    solve_segment<M, R, B, W>(n, tb, te, a.t_const, (R)a.kappa, static_cast<const C *>(a.cp),
+                              static_cast<const C *>(a.ip), io);
+    io.finish(a.status);
 }
 
 }  // namespace gpcn

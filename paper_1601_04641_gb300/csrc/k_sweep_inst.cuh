@@ -61,8 +61,28 @@ static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaS
 }
 
 template <class F, typename R, int W, int KIND, int LPT>
+static cudaError_t launch_lines_tma_wl(const SweepArgs &a, const TmaMaps &m, cudaStream_t s) {
+    using MV = typename LinesPerThread<F, LPT>::M::MemV;
+    const long long warps = a.n_lines / (32LL * LPT);
+    const dim3 grid((unsigned)((warps + kLineTmaWarps - 1) / kLineTmaWarps), (unsigned)a.n_seg);
+    constexpr size_t smem = line_tma_smem<MV>();
+    static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_lines_tma_kernel<F, R, W, KIND, LPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    sweep_lines_tma_kernel<F, R, W, KIND, LPT><<<grid, kLineTmaWarps * 32, smem, s>>>(a, m);
+    return cudaGetLastError();
+}
+
+template <class F, typename R, int W, int KIND, int LPT>
 static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     using V = typename LinesPerThread<F, LPT>::M::MemV;
+    if constexpr (W > 0 && KIND != K_Z) {
+        if (L.lmaps) return launch_lines_tma_wl<F, R, W, KIND, LPT>(a, *L.lmaps, s);
+    }
     const unsigned threads = (unsigned)L.threads;
     const long long units = (a.n_lines + LPT - 1) / LPT;
     const dim3 grid((unsigned)((units + threads - 1) / threads), (unsigned)a.n_seg);

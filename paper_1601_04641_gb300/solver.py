@@ -204,6 +204,16 @@ class GP:
         """z sweep through TMA tiles (default where the grid allows it)."""
         self._ck(self.lib.gp_set_tma(self.h, int(bool(on))))
 
+    def set_tma_lines(self, on):
+        """x and y sweeps through TMA boxes (default where the grid allows it)."""
+        self._ck(self.lib.gp_set_tma_lines(self.h, int(bool(on))))
+
+    def tma_lines_in_use(self):
+        """Axes (bit 0: x, bit 1: y) whose sweeps take the TMA box form."""
+        v = ctypes.c_int(0)
+        self._ck(self.lib.gp_get_tma_lines(self.h, ctypes.byref(v)))
+        return v.value
+
     def set_stop_rule(self, rule):
         """0: |dmu| < tol (default); 1: |dmu| < tol and |dE| < tol; 2: rule 1 at two consecutive checks."""
         self._ck(self.lib.gp_set_stop_rule(self.h, int(rule)))
