@@ -117,7 +117,7 @@ struct gp_handle_s {
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     bool tma_z = true;         // ... through TMA tiles where the grid allows it
-    bool tma_lines = true;     // x and y sweeps through TMA boxes where the grid allows it
+    int tma_lines = 1;         // axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid allows it
     int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol; 2 rule 1 twice in a row
     int splitting = 1;         // real time: 1 Lie (kick, sweeps), 2 symmetric (half kick, sweeps, half kick)
     bool kick_pending = false; // symmetric splitting: buf[cur] still lacks its trailing half kick
@@ -467,7 +467,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     }
     TmaMaps lmaps;  // the strided TMA form reads through lmaps.in and stores lane by lane
     std::memset(&lmaps, 0, sizeof(lmaps));
-    if (ax < 2 && h->tma_lines && line_tma_fits((int)h->elem, L.lpt, L.window, a.inner, a.stride, a.N)) {
+    if (ax < 2 && (h->tma_lines >> ax & 1) && line_tma_fits((int)h->elem, L.lpt, L.window, a.inner, a.stride, a.N)) {
         const int box_nodes = h->elem * L.lpt >= 16 ? 8 : 16;  // the kernel's chunk of MemV nodes
         if (encode_line_map(&lmaps.in, h->buf[h->cur], ax, h->n, (int)h->elem, L.lpt, box_nodes))
             L.lmaps = &lmaps;
@@ -1094,9 +1094,10 @@ gp_status gp_get_tma(gp_handle h, int *in_use) {
     return GP_OK;
 }
 
-gp_status gp_set_tma_lines(gp_handle h, int on) {
+gp_status gp_set_tma_lines(gp_handle h, int axes) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
-    h->tma_lines = on != 0;
+    if (axes < 0 || axes > 3) return fail(h, GP_ERR_ARG, "axes must be a mask of bit 0 (x) and bit 1 (y)");
+    h->tma_lines = axes;
     drop_graphs(h);
     return GP_OK;
 }
@@ -1110,7 +1111,10 @@ gp_status gp_get_tma_lines(gp_handle h, int *axes) {
             const int w = h->window[mode][ax];
             const long long plane = (long long)h->n[1] * h->n[2];
             const long long inner = ax == 0 ? plane : h->n[2];
-            if (h->tma_lines && line_tma_fits((int)h->elem, lines_per_thread(h, ax, w), w, inner, inner, h->n[ax]))
+            const int lpt = lines_per_thread(h, ax, w);
+            CUtensorMap probe;  // the map the launch would encode (x and y: inner is the node stride)
+            if ((h->tma_lines >> ax & 1) && line_tma_fits((int)h->elem, lpt, w, inner, inner, h->n[ax]) &&
+                encode_line_map(&probe, h->buf[0], ax, h->n, (int)h->elem, lpt, h->elem * lpt >= 16 ? 8 : 16))
                 used |= 1 << ax;
         }
     }

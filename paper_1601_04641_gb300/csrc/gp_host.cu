@@ -314,7 +314,7 @@ bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, 
 bool line_tma_fits(int elem_bytes, int lpt, int window, long long inner, long long stride, int N) {
     const int mv = elem_bytes * lpt;
     if (window <= 0 || N < 3 || (mv != 4 && mv != 8 && mv != 16)) return false;
-    if (inner % (32LL * lpt) != 0) return false;
+    if (inner % lpt != 0 || inner * elem_bytes / 4 > 0xffffffffLL) return false;
     return (stride * elem_bytes) % 16 == 0;
 }
 

@@ -175,9 +175,8 @@ void set_fail_alloc(int n);
 bool encode_z_map(CUtensorMap *map, const void *base, int N, long long n_lines, int elem_bytes);
 // Whether the x or y sweep (stride `stride` elements along the line, `inner`
 // lines per outer group) of elem_bytes elements, lpt lines per thread, can
-// take the strided TMA form: a windowed solve, line groups per outer group a
-// multiple of 32, a line stride of whole 16-byte units, and MemV of 4, 8 or
-// 16 bytes.
+// take the strided TMA form: a windowed solve, a line stride of whole
+// 16-byte units, and MemV of 4, 8 or 16 bytes.
 bool line_tma_fits(int elem_bytes, int lpt, int window, long long inner, long long stride, int N);
 // Encode the tensor map of the strided TMA form over the array at `psi`
 // for axis 0 (x) or 1 (y) of an (nx, ny, nz) grid, boxes of 32 * lpt

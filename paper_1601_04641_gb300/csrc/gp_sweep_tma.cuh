@@ -401,6 +401,7 @@ template <class F, class M, typename R, int B, int KIND> struct TmaColumnIO {
     int cx, cz, lane;
     int s0, limit, issued, ready;
     bool ok;
+    bool valid;       // the lane owns a line group (else it solves zeros and stores nothing)
     MV *out;          // the line group's node 0 in the output
     long long st;
     Hooks<F, M, R, KIND> hk;
@@ -440,7 +441,7 @@ template <class F, class M, typename R, int B, int KIND> struct TmaColumnIO {
         hk.on_load_chunk(p, v);
     }
     __device__ __forceinline__ void put(int t0, int q, V v) const {
-        out[(long long)(t0 + q + 1) * st] = M::store(v);
+        if (valid) out[(long long)(t0 + q + 1) * st] = M::store(v);
         hk.on_store(v);
     }
     __device__ __forceinline__ void flush(int, int) const {}
@@ -454,9 +455,10 @@ template <class F, class M, typename R, int B, int KIND> struct TmaColumnIO {
     }
 };
 
-// One warp per 32 line groups of one outer group (the host checks that the
-// line groups of an outer group are a multiple of 32); blockIdx.y is the
-// segment.  Windowed solves only.
+// One warp per 32 line groups of one outer group; the last warp of an outer
+// group may be partial: its box columns past the group read the zero fill,
+// and its lanes past the group solve those zeros and store nothing.
+// blockIdx.y is the segment.  Windowed solves only.
 template <class F, typename R, int W, int KIND, int LPT>
 __global__ void __launch_bounds__(kLineTmaWarps * 32) sweep_lines_tma_kernel(SweepArgs a,
                                                                              const __grid_constant__ TmaMaps maps) {
@@ -471,8 +473,14 @@ __global__ void __launch_bounds__(kLineTmaWarps * 32) sweep_lines_tma_kernel(Swe
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                                             ~static_cast<uintptr_t>(127));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long L0 = ((long long)blockIdx.x * kLineTmaWarps + warp) * 32 * LPT;  // the warp's first line
-    if (L0 >= a.n_lines) return;  // warps are independent: no block-wide barrier below
+    const long long U = a.inner / LPT;        // line groups per outer group
+    const long long wpr = (U + 31) / 32;      // warps per outer group
+    const long long gw = (long long)blockIdx.x * kLineTmaWarps + warp;
+    if (gw >= (a.n_lines / a.inner) * wpr) return;  // warps are independent: no block-wide barrier below
+    const long long o = gw / wpr, u0 = (gw % wpr) * 32;
+    const bool valid = u0 + lane < U;
+    const long long L0 = o * a.inner + u0 * LPT;                   // the warp's first line
+    const long long L = valid ? L0 + (long long)lane * LPT : L0;  // lanes past the group: the first line's state
     unsigned char *wb = base + warp * RC * BOXB;
     const unsigned bar0 = smem_u32(base + kLineTmaWarps * RC * BOXB) + 8 * RC * warp;
     if (lane == 0) {
@@ -480,22 +488,22 @@ __global__ void __launch_bounds__(kLineTmaWarps * 32) sweep_lines_tma_kernel(Swe
         mbar_init_fence();
     }
     __syncwarp();
-    const long long L = L0 + (long long)lane * LPT;
     const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
     MV *out = reinterpret_cast<MV *>(static_cast<typename F::V *>(a.psi_out) + off);
     const long long st = a.stride / LPT;
     const int n = a.N - 2;
     const unsigned seg = blockIdx.y;
-    if (seg == 0) out[0] = M::store(M::zero());
-    if ((int)seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::store(M::zero());
+    if (valid && seg == 0) out[0] = M::store(M::zero());
+    if (valid && (int)seg == a.n_seg - 1) out[(long long)(a.N - 1) * st] = M::store(M::zero());
     Acc<R> acc;
     TmaColumnIO<F, M, R, B, KIND> io;
+    io.valid = valid;
     io.tin = &maps.in;
     io.rp = reinterpret_cast<const MV *>(wb);
     io.ring_s = smem_u32(wb);
     io.bar0 = bar0;
-    io.cx = (int)((L0 % a.inner) * (long long)sizeof(typename F::V) / 4);
-    io.cz = (int)(L0 / a.inner);
+    io.cx = (int)(u0 * LPT * (long long)sizeof(typename F::V) / 4);
+    io.cz = (int)o;
     io.lane = lane;
     io.out = out;
     io.st = st;

@@ -63,7 +63,8 @@ static cudaError_t launch_contig(const SweepLaunch &L, const SweepArgs &a, cudaS
 template <class F, typename R, int W, int KIND, int LPT>
 static cudaError_t launch_lines_tma_wl(const SweepArgs &a, const TmaMaps &m, cudaStream_t s) {
     using MV = typename LinesPerThread<F, LPT>::M::MemV;
-    const long long warps = a.n_lines / (32LL * LPT);
+    const long long wpr = (a.inner / LPT + 31) / 32;  // warps per outer group (the last one may be partial)
+    const long long warps = (a.n_lines / a.inner) * wpr;
     const dim3 grid((unsigned)((warps + kLineTmaWarps - 1) / kLineTmaWarps), (unsigned)a.n_seg);
     constexpr size_t smem = line_tma_smem<MV>();
     static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory

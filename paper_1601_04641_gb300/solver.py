@@ -204,9 +204,9 @@ class GP:
         """z sweep through TMA tiles (default where the grid allows it)."""
         self._ck(self.lib.gp_set_tma(self.h, int(bool(on))))
 
-    def set_tma_lines(self, on):
-        """x and y sweeps through TMA boxes (default where the grid allows it)."""
-        self._ck(self.lib.gp_set_tma_lines(self.h, int(bool(on))))
+    def set_tma_lines(self, axes):
+        """Axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid allows it (default 1)."""
+        self._ck(self.lib.gp_set_tma_lines(self.h, int(axes)))
 
     def tma_lines_in_use(self):
         """Axes (bit 0: x, bit 1: y) whose sweeps take the TMA box form."""

@@ -6,9 +6,9 @@ per-thread-copy form and the FP64 oracle (GPU only).
   (imaginary time on real and complex fields, real time), 1, 2 and 4 lines
   per thread, windows 4, 8 and 16, whole lines and lines cut into segments
   at and off chunk boundaries, odd line lengths.
-- The axes that take the TMA form follow the rule: a windowed solve, line
-  groups per plane (x) or per row of a plane (y) a multiple of 32, a node
-  stride of whole 16-byte units.
+- The axes that take the TMA form follow the rule: a windowed solve and a
+  node stride of whole 16-byte units; the last warp of a plane (x) or of a
+  row (y) may be partial (its box columns past the row read the zero fill).
 - Junk in the Dirichlet end nodes is never read (the maps start at node 1)
   and zeros are written there: tests/test_gpu_lines.py runs with the TMA
   form on, its default.
@@ -44,10 +44,10 @@ def start_field(shape, prec, field, seed):
     return psi
 
 
-def run(shape, prec, field, realtime, tma, window=None, seg=None, lines=None, steps=4, seed=5):
+def run(shape, prec, field, realtime, tma_axes, window=None, seg=None, lines=None, steps=4, seed=5):
     dt, g = (0.002, 9.0) if realtime else (0.004, 12.0)
     gp = make(shape, dt, g, prec, field)
-    gp.set_tma_lines(tma)
+    gp.set_tma_lines(tma_axes)
     if window is not None:  # the strided axes only (z keeps its own smallest admissible window)
         for ax in (0, 1):
             gp.set_axis_window(ax, window)
@@ -69,11 +69,11 @@ def run(shape, prec, field, realtime, tma, window=None, seg=None, lines=None, st
     return out, axes, lpt
 
 
-def expected_axes(shape, elem, lpt, window):
+def expected_axes(shape, elem, window):
     nx, ny, nz = shape
     bits = 0
-    for ax, inner in ((0, ny * nz), (1, nz)):
-        if window > 0 and inner % (32 * lpt[ax]) == 0 and (inner * elem) % 16 == 0 and shape[ax] >= 3:
+    for ax, stride in ((0, ny * nz), (1, nz)):
+        if window > 0 and (stride * elem) % 16 == 0 and shape[ax] >= 3:
             bits |= 1 << ax
     return bits
 
@@ -84,7 +84,10 @@ CASES = [
     ((20, 18, 64), "f32", "complex", True, None, None, None),    # real time, pairs
     ((37, 24, 128), "f32", "real", False, None, None, None),     # quads on x and y
     ((37, 24, 128), "f32", "real", False, 16, 24, None),         # quads, segments of 24 (off chunk bounds)
-    ((41, 34, 32), "f32", "complex", False, 8, None, None),      # pairs: x on TMA, y (16 pairs a row) not
+    ((41, 34, 32), "f32", "complex", False, 8, None, None),      # pairs: 16 a row on y (a partial warp per row)
+    ((23, 19, 50), "f32", "complex", True, 4, None, None),       # partial warps on x (475 pairs) and y (25 a row)
+    ((23, 19, 52), "f32", "real", False, 8, 9, None),            # quads: 13 a row on y, 247 on x; segments of 9
+    ((23, 19, 50), "f32", "real", False, 4, None, None),         # node strides of 3800 / 200 bytes: neither axis
     ((41, 33, 32), "f32", "complex", False, 8, None, 1),         # single complex64 lines on both
     ((41, 33, 32), "f32", "real", False, 4, 5, 1),               # single lines, segments of 5
     ((24, 20, 32), "f64", "complex", False, 8, None, None),      # 16-byte elements, one line per thread
@@ -97,24 +100,40 @@ CASES = [
 @pytest.mark.parametrize("case", CASES, ids=[str(i) for i in range(len(CASES))])
 def test_tma_lines_bit_identical_to_copy_form(case):
     shape, prec, field, realtime, window, seg, lines = case
-    on, axes, lpt = run(shape, prec, field, realtime, True, window, seg, lines)
-    off, axes_off, _ = run(shape, prec, field, realtime, False, window, seg, lines)
+    on, axes, lpt = run(shape, prec, field, realtime, 3, window, seg, lines)
+    off, axes_off, _ = run(shape, prec, field, realtime, 0, window, seg, lines)
     elem = {"f32": 4, "f64": 8}[prec] * (2 if field == "complex" else 1)
     w = window if window is not None else 1  # the FP32 default is windowed
-    assert axes == expected_axes(shape, elem, lpt, w), (axes, lpt)
+    assert axes == expected_axes(shape, elem, w), (axes, lpt)
     assert axes_off == 0
-    assert axes != 0  # every case exercises the TMA form on some axis
     assert np.array_equal(on, off), float(np.max(np.abs(on.astype(np.complex128) - off.astype(np.complex128))))
 
 
-@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[7], CASES[8]], ids=["c64", "real", "c128", "c128rt"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[5], CASES[10], CASES[11]],
+                         ids=["c64", "real", "c64partial", "c128", "c128rt"])
 def test_tma_lines_match_oracle(case):
     shape, prec, field, realtime, window, seg, lines = case
     steps = 4
-    out, _, _ = run(shape, prec, field, realtime, True, window, seg, lines, steps=steps)
+    out, _, _ = run(shape, prec, field, realtime, 3, window, seg, lines, steps=steps)
     dt, g = (0.002, 9.0) if realtime else (0.004, 12.0)
     ref = start_field(shape, prec, field, 5).astype(np.complex128)
     oracle.step(ref, D, dt, OMEGA, g, realtime, steps)
     scale = float(np.max(np.abs(ref)))
     err = float(np.max(np.abs(out.astype(np.complex128) - ref)))
     assert err <= (1e-12 if prec == "f64" else 2e-6) * scale, err
+
+
+def test_tma_lines_axis_mask():
+    """The default reads x through TMA boxes and y through per-thread copies;
+    the mask selects the axes; masks outside 0..3 are refused."""
+    from paper_1601_04641_gb300 import _native as N
+    gp = make((20, 18, 64), 0.004, 12.0, "f32", "complex")
+    assert gp.tma_lines_in_use() == 1
+    for m in (0, 1, 2, 3):
+        gp.set_tma_lines(m)
+        assert gp.tma_lines_in_use() == m
+    for bad in (-1, 4):
+        with pytest.raises(N.GPError) as e:
+            gp.set_tma_lines(bad)
+        assert e.value.status == N.GP_ERR_ARG
+    gp.close()
