@@ -283,8 +283,10 @@ gp_status gp_set_tma(gp_handle h, int on);
 gp_status gp_get_tma(gp_handle h, int *in_use);
 
 /* The x and y sweeps (strided axes) reading through tensor-memory-
- * accelerator boxes: `axes` is a mask, bit 0 for x (the default, 1) and bit
- * 1 for y; a masked axis reads through per-thread asynchronous copies.  A
+ * accelerator boxes: `axes` is a mask, bit 0 for x and bit 1 for y, in both
+ * modes; -1 (the default) takes x in imaginary time and neither axis in real
+ * time.  An axis outside the mask reads through per-thread asynchronous
+ * copies.  A
  * warp streams 32 adjacent line groups (1, 2 or 4 lines each, as
  * gp_set_lines_per_thread gives) in boxes of one chunk of nodes x 32 groups,
  * one bulk tensor copy each; the last warp of a plane (x) or of a row of
@@ -293,11 +295,12 @@ gp_status gp_get_tma(gp_handle h, int *in_use);
  * a line's node stride is a multiple of 16 bytes (ny * nz * element size
  * for x, nz * element size for y); elsewhere the other form runs.  Both
  * forms do the same arithmetic in the same order, so their results are
- * identical.  It is the default on x only: on 480x400x320 it shortened the
- * x sweeps (FP32 real field 0.101 -> 0.096 ms) and lengthened the y sweeps
- * (0.082 -> 0.086 ms).  gp_get_tma_lines gives the axes that take it in
- * either mode under the current settings (bit 0: x, bit 1: y); GP_ERR_ARG
- * for a mask outside 0..3. */
+ * identical.  Measured on 480x400x320: it shortens the imaginary-time x
+ * sweeps (FP32 real field 0.101 -> 0.096 ms, complex64 0.166 -> 0.164 ms),
+ * lengthens the y sweeps (FP32 real 0.082 -> 0.086 ms) and the complex64
+ * real-time x sweep (0.170 -> 0.173 ms).  gp_get_tma_lines gives the axes
+ * that take it in either mode under the current settings (bit 0: x, bit 1:
+ * y); GP_ERR_ARG for a mask outside -1..3. */
 gp_status gp_set_tma_lines(gp_handle h, int axes);
 gp_status gp_get_tma_lines(gp_handle h, int *axes);
 

@@ -117,7 +117,8 @@ struct gp_handle_s {
     int threads[3] = {64, 64, 64};
     bool contiguous_z = true;  // warp-tiled kernel for the stride-1 axis
     bool tma_z = true;         // ... through TMA tiles where the grid allows it
-    int tma_lines = 1;         // axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid allows it
+    int tma_lines = -1;        // axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid
+                               // allows it; -1: x in imaginary time (measured faster), none in real time
     int stop_rule = 0;         // gp_run_imag_until: 0 |dmu| < tol; 1 |dmu| < tol and |dE| < tol; 2 rule 1 twice in a row
     int splitting = 1;         // real time: 1 Lie (kick, sweeps), 2 symmetric (half kick, sweeps, half kick)
     bool kick_pending = false; // symmetric splitting: buf[cur] still lacks its trailing half kick
@@ -435,6 +436,11 @@ gp_status absent_stage(gp_handle h, int stage, bool realtime) {
     return GP_OK;
 }
 
+// Axes whose sweeps read through TMA boxes in a mode (0 imaginary, 1 real
+// time): the mask set, or by default x in imaginary time only (the real-time
+// x sweep, bound by its kick arithmetic, measured 2 % slower that way).
+int tma_line_axes(gp_handle h, int mode) { return h->tma_lines >= 0 ? h->tma_lines : (mode == 0 ? 1 : 0); }
+
 // One stage of a step: 0 = kick + x sweep, 1 = y sweep, 2 = z sweep + norm.
 gp_status run_stage(gp_handle h, int stage, bool realtime) {
     if (h->n[stage] == 1) return absent_stage(h, stage, realtime);
@@ -467,7 +473,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
     }
     TmaMaps lmaps;  // the strided TMA form reads through lmaps.in and stores lane by lane
     std::memset(&lmaps, 0, sizeof(lmaps));
-    if (ax < 2 && (h->tma_lines >> ax & 1) && line_tma_fits((int)h->elem, L.lpt, L.window, a.inner, a.stride, a.N)) {
+    if (ax < 2 && (tma_line_axes(h, mode) >> ax & 1) && line_tma_fits((int)h->elem, L.lpt, L.window, a.inner, a.stride, a.N)) {
         const int box_nodes = h->elem * L.lpt >= 16 ? 8 : 16;  // the kernel's chunk of MemV nodes
         if (encode_line_map(&lmaps.in, h->buf[h->cur], ax, h->n, (int)h->elem, L.lpt, box_nodes))
             L.lmaps = &lmaps;
@@ -1096,7 +1102,7 @@ gp_status gp_get_tma(gp_handle h, int *in_use) {
 
 gp_status gp_set_tma_lines(gp_handle h, int axes) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
-    if (axes < 0 || axes > 3) return fail(h, GP_ERR_ARG, "axes must be a mask of bit 0 (x) and bit 1 (y)");
+    if (axes < -1 || axes > 3) return fail(h, GP_ERR_ARG, "axes must be -1 or a mask of bit 0 (x) and bit 1 (y)");
     h->tma_lines = axes;
     drop_graphs(h);
     return GP_OK;
@@ -1113,7 +1119,7 @@ gp_status gp_get_tma_lines(gp_handle h, int *axes) {
             const long long inner = ax == 0 ? plane : h->n[2];
             const int lpt = lines_per_thread(h, ax, w);
             CUtensorMap probe;  // the map the launch would encode (x and y: inner is the node stride)
-            if ((h->tma_lines >> ax & 1) && line_tma_fits((int)h->elem, lpt, w, inner, inner, h->n[ax]) &&
+            if ((tma_line_axes(h, mode) >> ax & 1) && line_tma_fits((int)h->elem, lpt, w, inner, inner, h->n[ax]) &&
                 encode_line_map(&probe, h->buf[0], ax, h->n, (int)h->elem, lpt, h->elem * lpt >= 16 ? 8 : 16))
                 used |= 1 << ax;
         }

@@ -205,7 +205,8 @@ class GP:
         self._ck(self.lib.gp_set_tma(self.h, int(bool(on))))
 
     def set_tma_lines(self, axes):
-        """Axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid allows it (default 1)."""
+        """Axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid allows it;
+        -1 (default): x in imaginary time only."""
         self._ck(self.lib.gp_set_tma_lines(self.h, int(axes)))
 
     def tma_lines_in_use(self):

@@ -123,16 +123,18 @@ def test_tma_lines_match_oracle(case):
     assert err <= (1e-12 if prec == "f64" else 2e-6) * scale, err
 
 
-def test_tma_lines_axis_mask():
-    """The default reads x through TMA boxes and y through per-thread copies;
-    the mask selects the axes; masks outside 0..3 are refused."""
+@pytest.mark.parametrize("field", ["real", "complex"])
+def test_tma_lines_axis_mask(field):
+    """The default reads x through TMA boxes in imaginary time only (a real
+    field has no real-time mode); a mask selects the axes in both modes;
+    masks outside -1..3 are refused."""
     from paper_1601_04641_gb300 import _native as N
-    gp = make((20, 18, 64), 0.004, 12.0, "f32", "complex")
+    gp = make((20, 18, 64), 0.004, 12.0, "f32", field)
     assert gp.tma_lines_in_use() == 1
-    for m in (0, 1, 2, 3):
+    for m in (0, 1, 2, 3, -1):
         gp.set_tma_lines(m)
-        assert gp.tma_lines_in_use() == m
-    for bad in (-1, 4):
+        assert gp.tma_lines_in_use() == (1 if m == -1 else m)
+    for bad in (-2, 4):
         with pytest.raises(N.GPError) as e:
             gp.set_tma_lines(bad)
         assert e.value.status == N.GP_ERR_ARG
