@@ -43,6 +43,8 @@ WORKLOADS = {
     "imag_large_real": (inputs.imag_large, "f32", "real", False),
     "imag_large_cplx": (inputs.imag_large, "f32", "complex", False),
     "imag_large_real_half": (inputs.imag_large_half, "f32", "real", False),
+    "imag_xl_real": (inputs.imag_xl, "f32", "real", False),
+    "imag_xl_f16": (inputs.imag_xl, "f16", "real", False),
 }
 # batched workloads (run_batch_workload): the 64 uneven condensates, every
 # instance active, FP32 complex or real field
@@ -835,7 +837,7 @@ def run_ours(args):
 
     kb = kernel_breakdown(torch, res, min(args.steps, 200))
     top = max(kb, key=kb.get)
-    elem = 8 if res["prec"] == "f32" else 16
+    elem = {"f16": 4, "f32": 8, "f64": 16}[res["prec"]]
     if res["field"] == "real":
         elem //= 2
     alg_bytes = 2 * elem * sites  # each kernel reads and writes psi once
@@ -857,7 +859,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": res["prec"], "data": "synthetic",
         "config": {"workload": p.name, "grid": list(p.shape), "sites": sites,
                    "psi": {"f32": "complex64", "f64": "complex128"}[res["prec"]]
-                   if res["field"] == "complex" else {"f32": "float32", "f64": "float64"}[res["prec"]],
+                   if res["field"] == "complex" else {"f16": "float16", "f32": "float32", "f64": "float64"}[res["prec"]],
                    "reductions": "fp64", "dt": p.dt, "g": p.g, "omega": list(p.omega),
                    "track_every": TRACK_EVERY,
                    "l2": ("inputs larger than L2 (psi %.0f MB > 129 MB)" if elem * sites > 129e6 else
@@ -886,7 +888,7 @@ def run_ours(args):
                 el2 = timed_region(torch, r2, args.also_steps, None)
                 kb2 = kernel_breakdown(torch, r2, min(args.also_steps, 50))
                 p2 = r2["problem"]
-                elem2 = (8 if r2["prec"] == "f32" else 16) // (2 if r2["field"] == "real" else 1)
+                elem2 = {"f16": 4, "f32": 8, "f64": 16}[r2["prec"]] // (2 if r2["field"] == "real" else 1)
                 bytes2 = 2 * elem2 * p2.sites  # algorithmic bytes per sweep launch
                 if r2["prec"] == "f64" and r2["field"] == "complex" and r2["realtime"]:
                     # FP64 is bound by the FP64 units, not by HBM: flops against the FP64 peak
@@ -898,7 +900,7 @@ def run_ours(args):
                 else:
                     alu = None
                 also[name] = {"workload": p2.name, "grid": list(p2.shape),
-                              "psi": {(4, "real"): "float32", (8, "real"): "float64",
+                              "psi": {(2, "real"): "float16", (4, "real"): "float32", (8, "real"): "float64",
                                       (8, "complex"): "complex64",
                                       (16, "complex"): "complex128"}[(elem2, r2["field"])],
                               "time": "real" if r2["realtime"] else "imaginary",
@@ -944,7 +946,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS), default="real_large")
-    ap.add_argument("--also", default="real_medium,imag_large_real,imag_large_cplx",
+    ap.add_argument("--also", default="real_medium,imag_large_real,imag_large_cplx,imag_xl_real,imag_xl_f16",
                     help="comma-separated secondary workloads timed after the main one")
     ap.add_argument("--also-steps", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

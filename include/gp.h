@@ -72,8 +72,24 @@ typedef enum {
     GP_ERR_IO = 7         /* a file could not be opened or written */
 } gp_status;
 
-typedef enum { GP_F64 = 0, GP_F32 = 1 } gp_precision; /* element precision of psi;
-                                                         reductions are always FP64 */
+typedef enum { GP_F64 = 0, GP_F32 = 1, GP_F16 = 2 } gp_precision; /* element precision of psi;
+                                                                     reductions are always FP64 */
+/* GP_F16: psi stored in IEEE half precision (2 bytes a site) with every
+ * operation in FP32 -- the sweeps, the kick and the observables widen on
+ * load and round to nearest on store; the norm that sets the
+ * renormalisation is summed from the FP32 results before rounding.  A
+ * precision variant of the imaginary-time path (the paper computes in FP64
+ * throughout): GP_REAL fields only, nz a multiple of 8 and at least 56 (the
+ * z sweep is the TMA form, a chunk of 32 nodes plus its window), windowed
+ * solves with two or four lines per thread on x and y (calls that would
+ * select another form return GP_ERR_ARG).  Each sweep rounds psi to 2^-11
+ * relative: where a step changes psi by less than that (dt small against
+ * 2^-11 / (gap of the low modes)) the evolution stalls short of the ground
+ * state, and the fixed point sits far from FP32's -- on the 640x480x400
+ * benchmark grid mu was 4.7 % high after 250 steps at dt = 0.1 d^2 and
+ * 0.2 % at dt = d^2.  A coarse stage at a large dt before an FP32 or FP64
+ * finish.  gp_density_profiles, gp_write_wavefunction, gp_nn_predict, the
+ * batched form and gp_observables_noalloc do not take it. */
 typedef enum { GP_COMPLEX = 0, GP_REAL = 1 } gp_field;
 
 typedef struct {

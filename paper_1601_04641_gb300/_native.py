@@ -16,7 +16,7 @@ GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_NOMEM, GP_ERR_NONFINITE, GP_ERR_TIMEOUT, 
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_CUDA", 3: "GP_ERR_NOMEM",
                 4: "GP_ERR_NONFINITE", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_STATE", 7: "GP_ERR_IO"}
 GP_OUT_PSI, GP_OUT_DENSITY = 0, 1
-GP_F64, GP_F32 = 0, 1
+GP_F64, GP_F32, GP_F16 = 0, 1, 2
 GP_COMPLEX, GP_REAL = 0, 1
 
 

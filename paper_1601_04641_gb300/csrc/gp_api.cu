@@ -28,6 +28,7 @@ cudaError_t launch_sweep_f32_rt(const SweepLaunch &, const SweepArgs &, cudaStre
 cudaError_t launch_sweep_f64_ir(const SweepLaunch &, const SweepArgs &, cudaStream_t);
 cudaError_t launch_sweep_f64_ic(const SweepLaunch &, const SweepArgs &, cudaStream_t);
 cudaError_t launch_sweep_f64_rt(const SweepLaunch &, const SweepArgs &, cudaStream_t);
+cudaError_t launch_sweep_f16_ir(const SweepLaunch &, const SweepArgs &, cudaStream_t);
 
 cudaError_t launch_sweep_f32_ir_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
 cudaError_t launch_sweep_f32_ic_batch(const SweepLaunch &, const BatchLaunch &, cudaStream_t);
@@ -54,6 +55,7 @@ cudaError_t launch_sweep_batch(const SweepLaunch &L, const BatchLaunch &b, cudaS
 }
 
 cudaError_t launch_sweep(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    if (L.prec == P_F16) return L.form == F_IMAG_REAL ? launch_sweep_f16_ir(L, a, s) : cudaErrorInvalidValue;
     if (L.prec == P_F32) {
         switch (L.form) {
         case F_IMAG_REAL: return launch_sweep_f32_ir(L, a, s);
@@ -181,12 +183,22 @@ gp_status check_args(gp_grid grid, double dt, double gamma, double nu, double la
         if (!std::isfinite(x) || x < 0.0)
             return fail(nullptr, GP_ERR_ARG, "trap frequencies must be finite and >= 0");
     if (!std::isfinite(g)) return fail(nullptr, GP_ERR_ARG, "g must be finite");
-    if (prec != GP_F64 && prec != GP_F32) return fail(nullptr, GP_ERR_ARG, "unknown precision");
+    if (prec != GP_F64 && prec != GP_F32 && prec != GP_F16) return fail(nullptr, GP_ERR_ARG, "unknown precision");
     if (field != GP_COMPLEX && field != GP_REAL) return fail(nullptr, GP_ERR_ARG, "unknown field");
+    if (prec == GP_F16) {
+        // FP16 storage: real fields (imaginary time), the TMA z sweep on whole
+        // rows of 16-byte units with room for a chunk of 32 nodes and the widest
+        // window, and line pairs on x and y
+        if (field != GP_REAL) return fail(nullptr, GP_ERR_ARG, "FP16 storage is for real fields (imaginary time) only");
+        if (n[2] % 8 != 0 || n[2] < 56) return fail(nullptr, GP_ERR_ARG, "FP16 storage needs nz a multiple of 8, at least 56");
+    }
     return GP_OK;
 }
 
 int modes_of(gp_handle h) { return h->field == GP_COMPLEX ? 2 : 1; }
+
+Prec prec_of(gp_handle h) { return h->prec == GP_F64 ? P_F64 : (h->prec == GP_F32 ? P_F32 : P_F16); }
+bool fp16(gp_handle h) { return h->prec == GP_F16; }
 
 Geometry geom(gp_handle h) {
     Geometry G;
@@ -203,7 +215,7 @@ Geometry geom(gp_handle h) {
 // Build and upload the coefficient tables of both modes and all axes, and
 // pick the window of the windowed backward sweep for each.
 gp_status build_coefficients(gp_handle h) {
-    const bool f32 = h->prec == GP_F32;
+    const bool f32 = h->prec != GP_F64;  // FP32 tables for FP32 arithmetic (FP32 and FP16 storage)
     std::vector<char> host;
     append_tables(geom(h), f32, modes_of(h), host, h->tab);
     const size_t off = host.size();
@@ -315,7 +327,7 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
     h->prec = prec;
     h->field = field;
     h->stream = static_cast<cudaStream_t>(stream);
-    h->elem = (prec == GP_F64 ? 8 : 4) * (field == GP_COMPLEX ? 2 : 1);
+    h->elem = (prec == GP_F64 ? 8 : (prec == GP_F32 ? 4 : 2)) * (field == GP_COMPLEX ? 2 : 1);
     h->sites = (size_t)grid.nx * grid.ny * grid.nz;
     h->bytes = h->sites * h->elem;
     if (dev_psi) {
@@ -349,6 +361,13 @@ gp_status create_common(gp_handle *out, gp_grid grid, double dt, double gamma, d
         const long long rows = (long long)grid.nx * grid.ny;
         h->zmap_ok = encode_z_map(&h->zmap[0], h->buf[0], grid.nz, rows, (int)h->elem) &&
                      encode_z_map(&h->zmap[1], h->buf[1], grid.nz, rows, (int)h->elem);
+    }
+    if (st == GP_OK && prec == GP_F16) {
+        // every FP16 sweep is windowed and its z sweep is the TMA form
+        for (int ax = 0; ax < 3 && st == GP_OK; ++ax)
+            if (h->n[ax] > 1 && h->tab.ax[0][ax].min_window == 0)
+                st = fail(h, GP_ERR_ARG, "FP16 storage needs a windowed solve: dt too large for this spacing");
+        if (st == GP_OK && !h->zmap_ok) st = fail(h, GP_ERR_ARG, "FP16 storage: no tensor map for the z sweep");
     }
     if (st != GP_OK) {
         g_create_error = h->err;
@@ -408,7 +427,7 @@ gp_status check_status(gp_handle h) {
 int lines_per_thread(gp_handle h, int ax, int window) {
     if (ax == 2 || h->elem > 8) return 1;
     auto fits = [&](int g) { return sweep_lines(h, ax) % g == 0 && (ax != 1 || h->n[2] % g == 0); };
-    if (h->max_lpt[ax] >= 4 && h->elem == 4 && window > 0 && fits(4)) return 4;
+    if (h->max_lpt[ax] >= 4 && (h->elem == 4 || h->elem == 2) && window > 0 && fits(4)) return 4;  // real fields
     if (h->max_lpt[ax] >= 2 && fits(2)) return 2;
     return 1;
 }
@@ -428,7 +447,7 @@ gp_status absent_stage(gp_handle h, int stage, bool realtime) {
     if (!realtime) {
         FieldArgs a = field_args(geom(h), h->buf[h->cur], h->d_scal + S_ONE, h->d_partials, h->d_counter,
                                  h->d_obs, h->d_scal + S_SCALE, h->d_scal + S_NORM_SWEEP);
-        GP_CK(h, launch_norm(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
+        GP_CK(h, launch_norm(prec_of(h), h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
         h->scale_pending = true;
     } else if (h->splitting == 2) {
         h->kick_pending = true;
@@ -445,7 +464,7 @@ int tma_line_axes(gp_handle h, int mode) { return h->tma_lines >= 0 ? h->tma_lin
 gp_status run_stage(gp_handle h, int stage, bool realtime) {
     if (h->n[stage] == 1) return absent_stage(h, stage, realtime);
     SweepLaunch L;
-    L.prec = h->prec == GP_F32 ? P_F32 : P_F64;
+    L.prec = prec_of(h);
     L.form = realtime ? F_REALTIME : (h->field == GP_REAL ? F_IMAG_REAL : F_IMAG_CPLX);
     L.kind = static_cast<Kind>(stage);
     const int mode = realtime ? 1 : 0;
@@ -478,6 +497,9 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
         if (encode_line_map(&lmaps.in, h->buf[h->cur], ax, h->n, (int)h->elem, L.lpt, box_nodes))
             L.lmaps = &lmaps;
     }
+    if (fp16(h) && (L.window == 0 || (ax < 2 && L.lpt < 2) ||
+                    (ax == 2 && !(L.tma && tma_z_fits((int)h->elem, L.window, a.N, a.n_seg, a.n_lines)))))
+        return fail(h, GP_ERR_STATE, "FP16 storage: no kernel for this axis under the current settings");
     const int zthreads = L.contiguous ? 32 : L.threads;
     if (stage == 2 && blocks_for(a.n_lines, zthreads) * (size_t)a.n_seg > h->partial_cap)
         return fail(h, GP_ERR_STATE, "z sweep grid exceeds the partials buffer");
@@ -494,7 +516,7 @@ gp_status run_stage(gp_handle h, int stage, bool realtime) {
 gp_status settle(gp_handle h) {
     if (!h->kick_pending) return GP_OK;
     FieldArgs a = handle_field_args(h);
-    GP_CK(h, launch_kick(h->prec == GP_F32 ? P_F32 : P_F64, a, 0.5 * h->dt, h->buf[h->cur ^ 1], h->stream));
+    GP_CK(h, launch_kick(prec_of(h), a, 0.5 * h->dt, h->buf[h->cur ^ 1], h->stream));
     h->cur ^= 1;
     h->scale_pending = false;
     h->kick_pending = false;
@@ -631,7 +653,7 @@ gp_status queue_observables(gp_handle h, double *dst) {
     a.out = dst;
     if ((size_t)observables_blocks(a) * 9 > h->partial_cap)
         return fail(h, GP_ERR_STATE, "observables grid exceeds the partials buffer");
-    GP_CK(h, launch_observables(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a,
+    GP_CK(h, launch_observables(prec_of(h), h->field == GP_COMPLEX, a,
                                 h->stream));
     return GP_OK;
 }
@@ -686,7 +708,7 @@ gp_status gp_init_gaussian(gp_handle h) {
     gp_status st = enter(h);
     if (st != GP_OK) return st;
     FieldArgs a = handle_field_args(h);
-    const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
+    const Prec p = prec_of(h);
     const bool cplx = h->field == GP_COMPLEX;
     GP_CK(h, launch_gaussian(p, cplx, a, h->stream));
     GP_CK(h, launch_norm(p, cplx, a, kNormBlocks, h->stream));
@@ -720,7 +742,7 @@ gp_status gp_get_psi(gp_handle h, void *psi, int on_device) {
     if (!psi) return fail(h, GP_ERR_ARG, "psi is NULL");
     if ((st = settle(h)) != GP_OK) return st;
     FieldArgs a = handle_field_args(h);
-    const Prec p = h->prec == GP_F32 ? P_F32 : P_F64;
+    const Prec p = prec_of(h);
     const bool cplx = h->field == GP_COMPLEX;
     if (on_device) {
         GP_CK(h, launch_apply_scale(p, cplx, a, psi, h->stream));
@@ -837,6 +859,7 @@ gp_status gp_observables(gp_handle h, gp_obs *out) {
 gp_status gp_density_profiles(gp_handle h, double *rho_x, double *rho_y, double *rho_z) {
     gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
+    if (fp16(h)) return fail(h, GP_ERR_STATE, "not for FP16 storage");
     if (!rho_x && !rho_y && !rho_z) return GP_OK;
     FieldArgs a = handle_field_args(h);  // the pending scale enters as s^2; a pending half kick is a phase
     const size_t nd = profile_scratch_doubles(a);
@@ -848,7 +871,7 @@ gp_status gp_density_profiles(gp_handle h, double *rho_x, double *rho_y, double 
     }
     double *out = scratch + (nd - (size_t)total);
     std::vector<double> host((size_t)total);
-    cudaError_t e = launch_density_profiles(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a, scratch,
+    cudaError_t e = launch_density_profiles(prec_of(h), h->field == GP_COMPLEX, a, scratch,
                                             out, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host.data(), out, (size_t)total * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -867,6 +890,7 @@ gp_status gp_density_profiles(gp_handle h, double *rho_x, double *rho_y, double 
 gp_status gp_write_wavefunction(gp_handle h, const char *path, int what) {
     gp_status st = enter_psi(h);
     if (st != GP_OK) return st;
+    if (fp16(h)) return fail(h, GP_ERR_STATE, "not for FP16 storage (read psi with gp_get_psi)");
     if (!path) return fail(h, GP_ERR_ARG, "path is NULL");
     if (what != GP_OUT_PSI && what != GP_OUT_DENSITY) return fail(h, GP_ERR_ARG, "what must be GP_OUT_PSI or GP_OUT_DENSITY");
     const bool f32 = h->prec == GP_F32, cplx = h->field == GP_COMPLEX;
@@ -1012,6 +1036,7 @@ gp_status gp_set_window(gp_handle h, int window) {
     if (st != GP_OK) return st;
     if (window != -1 && window != 0 && window != 4 && window != 8 && window != 16)
         return fail(h, GP_ERR_ARG, "window must be -1 (automatic), 0, 4, 8 or 16");
+    if (window == 0 && fp16(h)) return fail(h, GP_ERR_ARG, "FP16 storage needs a windowed solve");
     if (window > 0) {
         for (int mode = 0; mode < modes_of(h); ++mode)
             for (int ax = 0; ax < 3; ++ax) {
@@ -1022,7 +1047,7 @@ gp_status gp_set_window(gp_handle h, int window) {
     }
     for (int mode = 0; mode < modes_of(h); ++mode)
         for (int ax = 0; ax < 3; ++ax)
-            h->window[mode][ax] = window >= 0 ? window : default_window(h->tab.ax[mode][ax], h->prec == GP_F32);
+            h->window[mode][ax] = window >= 0 ? window : default_window(h->tab.ax[mode][ax], h->prec != GP_F64);
     h->forced_window = window;
     drop_graphs(h);
     return GP_OK;
@@ -1034,19 +1059,21 @@ gp_status gp_set_axis_window(gp_handle h, int axis, int window) {
     if (axis < 0 || axis > 2) return fail(h, GP_ERR_ARG, "bad axis");
     if (window != -1 && window != 0 && window != 4 && window != 8 && window != 16)
         return fail(h, GP_ERR_ARG, "window must be -1 (automatic), 0, 4, 8 or 16");
+    if (window == 0 && fp16(h)) return fail(h, GP_ERR_ARG, "FP16 storage needs a windowed solve");
     for (int mode = 0; mode < modes_of(h); ++mode) {
         const AxisTables &at = h->tab.ax[mode][axis];
         if (h->n[axis] > 1 && window > 0 && (at.min_window == 0 || window < at.min_window))
             return fail(h, GP_ERR_ARG, "window too small for the accuracy of this dt");
     }
     for (int mode = 0; mode < modes_of(h); ++mode)
-        h->window[mode][axis] = window >= 0 ? window : default_window(h->tab.ax[mode][axis], h->prec == GP_F32);
+        h->window[mode][axis] = window >= 0 ? window : default_window(h->tab.ax[mode][axis], h->prec != GP_F64);
     drop_graphs(h);
     return GP_OK;
 }
 
 gp_status gp_set_pair_lines(gp_handle h, int on) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    if (!on && fp16(h)) return fail(h, GP_ERR_ARG, "FP16 storage moves two or four lines per thread");
     h->max_lpt[0] = h->max_lpt[1] = on ? 4 : 1;
     drop_graphs(h);
     return GP_OK;
@@ -1055,6 +1082,7 @@ gp_status gp_set_pair_lines(gp_handle h, int on) {
 gp_status gp_set_lines_per_thread(gp_handle h, int axis, int lines) {
     if (!h || axis < 0 || axis > 1) return fail(h, GP_ERR_ARG, "axis must be 0 (x) or 1 (y)");
     if (lines != 1 && lines != 2 && lines != 4) return fail(h, GP_ERR_ARG, "lines must be 1, 2 or 4");
+    if (lines == 1 && fp16(h)) return fail(h, GP_ERR_ARG, "FP16 storage moves two or four lines per thread");
     h->max_lpt[axis] = lines;
     drop_graphs(h);
     return GP_OK;
@@ -1079,6 +1107,7 @@ gp_status gp_set_splitting(gp_handle h, int order) {
 
 gp_status gp_set_tma(gp_handle h, int on) {
     if (!h) return fail(h, GP_ERR_ARG, "NULL handle");
+    if (!on && fp16(h)) return fail(h, GP_ERR_ARG, "the FP16 z sweep is the TMA form");
     h->tma_z = on != 0;
     drop_graphs(h);
     return GP_OK;
@@ -1195,7 +1224,7 @@ struct TuneChoice {
 
 std::string tune_key(gp_handle h, int realtime, int ax) {
     std::ostringstream k;
-    k << h->n[0] << "x" << h->n[1] << "x" << h->n[2] << (h->prec == GP_F32 ? "/f32" : "/f64")
+    k << h->n[0] << "x" << h->n[1] << "x" << h->n[2] << (h->prec == GP_F32 ? "/f32" : (h->prec == GP_F16 ? "/f16" : "/f64"))
       << (h->field == GP_COMPLEX ? "/c" : "/r") << (realtime ? "/rt" : "/it") << "/w" << h->window[realtime][ax]
       << "/ax" << ax << "/v2";
     return k.str();
@@ -1259,6 +1288,7 @@ gp_status autotune(gp_handle h, int realtime, int reps, const char *cache_path) 
             for (int sg : segs)
                 for (int lp : {4, 2, 1}) {
                     if (ax == 2 && lp != 1) continue;  // line groups apply to the strided axes only
+                    if (ax < 2 && lp == 1 && fp16(h)) continue;  // FP16 storage moves two or four lines
                     if (h->window[mode][ax] == 0 && sg != 0) continue;  // the exact solve has no segments
                     // skip limits that select the same group size as a larger one
                     if (ax < 2 && lp < 4) {
@@ -1331,10 +1361,11 @@ gp_status gp_nn_predict(gp_nn net, gp_handle h) {
     if (st != GP_OK) return st;
     const NNParams *P = nn_params(net);
     if (!P) return fail(h, GP_ERR_ARG, "NULL network");
+    if (fp16(h)) return fail(h, GP_ERR_STATE, "not for FP16 storage");
     const NNInstance I = make_nn_instance(h->n, h->d, h->w, h->g);
     GP_CK(h, nn_launch_predict(*P, I, h->buf[h->cur], h->prec == GP_F32, h->field == GP_COMPLEX, h->stream));
     FieldArgs a = handle_field_args(h);
-    GP_CK(h, launch_norm(h->prec == GP_F32 ? P_F32 : P_F64, h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
+    GP_CK(h, launch_norm(prec_of(h), h->field == GP_COMPLEX, a, kNormBlocks, h->stream));
     h->scale_pending = true;
     h->kick_pending = false;
     h->psi_lost = false;

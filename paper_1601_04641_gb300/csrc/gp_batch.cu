@@ -503,6 +503,7 @@ gp_status gp_batch_create(gp_batch *out, int n, const gp_grid *grids, const doub
     *out = nullptr;
     if (n < 1 || !grids || !dt || !gamma || !nu || !lambda || !g)
         return bfail(nullptr, GP_ERR_ARG, "need n >= 1 and all parameter arrays");
+    if (prec == GP_F16) return bfail(nullptr, GP_ERR_ARG, "the batched form has no FP16 storage");
     if (prec != GP_F64 && prec != GP_F32) return bfail(nullptr, GP_ERR_ARG, "unknown precision");
     if (field != GP_COMPLEX && field != GP_REAL) return bfail(nullptr, GP_ERR_ARG, "unknown field");
     for (int i = 0; i < n; ++i) {

@@ -9,7 +9,7 @@
 
 namespace gpcn {
 
-enum Prec { P_F64 = 0, P_F32 = 1 };
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2 };  // P_F16: FP16 storage, FP32 arithmetic (real fields, imaginary time)
 
 // The three arithmetic forms of a sweep:
 //  IMAG_REAL  imaginary time on a real field   (c real, coefficients real)
@@ -70,7 +70,7 @@ struct TmaMaps {
 // within 256 bytes (chunk = 64 bytes of nodes), and at least one chunk plus
 // the window plus two interior nodes.
 inline bool tma_z_fits(int elem_bytes, int W, int N, int n_seg, long long n_lines) {
-    if (elem_bytes != 4 && elem_bytes != 8) return false;
+    if (elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8) return false;
     const int chunk = 64 / elem_bytes;
     return W > 0 && (chunk + W) * 2 * elem_bytes <= 256 && n_seg == 1 && N - 2 >= chunk + W + 2 &&
            ((long long)N * elem_bytes) % 16 == 0 && n_lines > 0 && n_lines <= 0x7fffffffLL;

@@ -41,6 +41,8 @@
 // threads) whose last block writes the next renormalisation factor.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "gp_internal.h"
@@ -739,14 +741,55 @@ struct PImagRealQ {
     }
 };
 
+// FP16 storage of a real field in imaginary time (FP32 arithmetic): the
+// forms above with 2-byte elements in memory, widened on load and rounded
+// to nearest on store.  FImagRealH is the single-line form (its values are
+// FP32 in registers; StoreOf gives its memory element), PImagRealH the pair
+// and QImagRealH the four-line form.  There is no single-line strided form:
+// cp.async moves 4, 8 or 16 bytes, so the strided axes take pairs or quads.
+struct FImagRealH : FImagReal<float> {
+    using MemV = __half;
+    __device__ __forceinline__ static float load(MemV m) { return __half2float(m); }
+    __device__ __forceinline__ static MemV store(float v) { return __float2half_rn(v); }
+};
+struct __align__(4) Half2 { __half a, b; };
+struct __align__(8) Half4 { __half x, y, z, w; };
+struct PImagRealH : PImagRealF {
+    using F = FImagRealH;
+    using MemV = Half2;
+    // one packed conversion each way
+    __device__ __forceinline__ static V load(MemV m) { return __half22float2(__halves2half2(m.a, m.b)); }
+    __device__ __forceinline__ static MemV store(V v) {
+        const __half2 h = __float22half2_rn(v);
+        return MemV{__low2half(h), __high2half(h)};
+    }
+};
+struct QImagRealH : PImagRealQ {
+    using F = FImagRealH;
+    using MemV = Half4;
+    __device__ __forceinline__ static V load(MemV m) {
+        return V{__half22float2(__halves2half2(m.x, m.y)), __half22float2(__halves2half2(m.z, m.w))};
+    }
+    __device__ __forceinline__ static MemV store(V v) {
+        const __half2 a = __float22half2_rn(v.a), b = __float22half2_rn(v.b);
+        return MemV{__low2half(a), __high2half(a), __low2half(b), __high2half(b)};
+    }
+};
+// The memory element of a single-line form's field.
+template <class F> struct StoreOf { using type = typename F::V; };
+template <> struct StoreOf<FImagRealH> { using type = __half; };
+template <class F> using store_t = typename StoreOf<F>::type;
+
 // The paired form of a single-line form.
 template <class F> struct PairForm { using type = FPair<F>; };
 template <> struct PairForm<FRealTime<float>> { using type = PRealTimeF; };
 template <> struct PairForm<FImagReal<float>> { using type = PImagRealF; };
 template <> struct PairForm<FImagCplx<float>> { using type = PImagCplxF; };
+template <> struct PairForm<FImagRealH> { using type = PImagRealH; };
 // The four-line form of a single-line form, where there is one.
 template <class F> struct QuadForm { using type = void; };
 template <> struct QuadForm<FImagReal<float>> { using type = PImagRealQ; };
+template <> struct QuadForm<FImagRealH> { using type = QImagRealH; };
 template <class F> constexpr bool has_quad() { return !std::is_void<typename QuadForm<F>::type>::value; }
 
 // ------------------------------------------------------------------ reductions
@@ -1128,8 +1171,8 @@ __device__ __forceinline__ double lines_body(const SweepArgs &a, unsigned bx, un
     Acc<R> acc;
     if (L < a.n_lines) {
         const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
-        const MV *in = reinterpret_cast<const MV *>(static_cast<const typename F::V *>(a.psi) + off);
-        MV *out = reinterpret_cast<MV *>(static_cast<typename F::V *>(a.psi_out) + off);
+        const MV *in = reinterpret_cast<const MV *>(static_cast<const store_t<F> *>(a.psi) + off);
+        MV *out = reinterpret_cast<MV *>(static_cast<store_t<F> *>(a.psi_out) + off);
         const long long st = a.stride / LPT;  // stride in units of MV
         const int n = a.N - 2;
         const C *cp = static_cast<const C *>(a.cp);

@@ -60,12 +60,13 @@ template <typename E, int W> __host__ __device__ constexpr size_t tma_smem_bytes
     return 1024 + (size_t)kTmaWarps * tma_slots<E, W>() * (kTmaBoxBytes + 8);
 }
 
-// Forms the TMA kernel is built for: 4- or 8-byte elements, and a register
-// ring of B + W pair values within 256 bytes per thread (beyond that the
-// kernel spills; the per-thread copy form runs instead).
+// Forms the TMA kernel is built for: 2-, 4- or 8-byte elements (2: FP16
+// storage), and a register ring of B + W pair values within 256 bytes of
+// storage per thread (beyond that the kernel spills; the per-thread copy
+// form runs instead).
 template <class F, int W> constexpr bool tma_supported() {
-    using E = typename F::V;
-    if constexpr (sizeof(E) != 4 && sizeof(E) != 8) return false;
+    using E = store_t<F>;
+    if constexpr (sizeof(E) != 2 && sizeof(E) != 4 && sizeof(E) != 8) return false;
     else return (tma_chunk<E>() + W) * 2 * sizeof(E) <= 256;
 }
 
@@ -73,7 +74,7 @@ template <class F, int W> constexpr bool tma_supported() {
 // (one segment), rows that start on 16-byte boundaries, and lines of at
 // least one full chunk plus its window and two nodes.
 template <class F, int W> inline bool tma_usable(const SweepArgs &a) {
-    using E = typename F::V;
+    using E = store_t<F>;
     if constexpr (!tma_supported<F, W>()) {
         return false;
     } else {
@@ -124,7 +125,7 @@ template <typename E> struct __align__(2 * sizeof(E)) E2 { E x, y; };
 template <class F, typename R, int W>
 __device__ __forceinline__ double tma_body(const SweepArgs &a, const CUtensorMap *tin, const CUtensorMap *tout,
                                            unsigned char *wbase, unsigned bar0, int y0) {
-    using E = typename F::V;
+    using E = store_t<F>;
     using M = typename PairForm<F>::type;
     using V = typename M::V;
     using MV = typename M::MemV;
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) batch_tma_kernel(BatchDesc 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                             ~static_cast<uintptr_t>(1023));
-    constexpr int S = tma_slots<typename F::V, W>();
+    constexpr int S = tma_slots<store_t<F>, W>();
     const int q = find_instance(d, blockIdx.x);
     const SweepArgs a = d.args[q];
     const unsigned local = blockIdx.x - __ldg(d.first + q);
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) sweep_tma_kernel(SweepArgs 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                             ~static_cast<uintptr_t>(1023));
-    constexpr int S = tma_slots<typename F::V, W>();
+    constexpr int S = tma_slots<store_t<F>, W>();
     const int warp = threadIdx.x >> 5;
     const long long L0 = ((long long)blockIdx.x * kTmaWarps + warp) * kTmaRows;
     double v = 0.0;
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(kLineTmaWarps * 32) sweep_lines_tma_kernel(Swe
     }
     __syncwarp();
     const long long off = (L / a.inner) * a.outer_stride + (L % a.inner);
-    MV *out = reinterpret_cast<MV *>(static_cast<typename F::V *>(a.psi_out) + off);
+    MV *out = reinterpret_cast<MV *>(static_cast<store_t<F> *>(a.psi_out) + off);
     const long long st = a.stride / LPT;
     const int n = a.N - 2;
     const unsigned seg = blockIdx.y;
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(kLineTmaWarps * 32) sweep_lines_tma_kernel(Swe
     io.rp = reinterpret_cast<const MV *>(wb);
     io.ring_s = smem_u32(wb);
     io.bar0 = bar0;
-    io.cx = (int)(u0 * LPT * (long long)sizeof(typename F::V) / 4);
+    io.cx = (int)(u0 * LPT * (long long)sizeof(store_t<F>) / 4);
     io.cz = (int)o;
     io.lane = lane;
     io.out = out;

@@ -14,6 +14,7 @@ namespace {
 template <typename R, bool CPLX> struct Elem;
 template <typename R> struct Elem<R, false> {
     using V = R;
+    using T = R;  // arithmetic type
     __device__ __forceinline__ static double abs2(V v) { return (double)v * (double)v; }
     __device__ __forceinline__ static R abs2r(V v) { return v * v; }
     __device__ __forceinline__ static V from_real(double x) { return (R)x; }
@@ -25,6 +26,7 @@ template <typename R> struct Elem<R, false> {
 };
 template <typename R> struct Elem<R, true> {
     using V = cx<R>;
+    using T = R;
     __device__ __forceinline__ static double abs2(V v) {
         return (double)v.re * (double)v.re + (double)v.im * (double)v.im;
     }
@@ -34,6 +36,25 @@ template <typename R> struct Elem<R, true> {
     __device__ __forceinline__ static R diff2(V a, V b) {
         const R dre = a.re - b.re, dim = a.im - b.im;
         return dre * dre + dim * dim;
+    }
+};
+// FP16 storage of a real field: values widened to FP32 for all arithmetic.
+template <> struct Elem<__half, false> {
+    using V = __half;
+    using T = float;
+    __device__ __forceinline__ static double abs2(V v) {
+        const double x = (double)__half2float(v);
+        return x * x;
+    }
+    __device__ __forceinline__ static float abs2r(V v) {
+        const float x = __half2float(v);
+        return x * x;
+    }
+    __device__ __forceinline__ static V from_real(double x) { return __double2half(x); }
+    __device__ __forceinline__ static V scaled(V v, float s) { return __float2half_rn(__half2float(v) * s); }
+    __device__ __forceinline__ static float diff2(V a, V b) {
+        const float d = __half2float(a) - __half2float(b);
+        return d * d;
     }
 };
 
@@ -239,6 +260,7 @@ template <typename R, bool CPLX>
 __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned block, unsigned nblocks) {
     using E = Elem<R, CPLX>;
     using V = typename E::V;
+    using T = typename E::T;  // arithmetic
     const V *psi = static_cast<const V *>(a.psi);
     const long long plane = (long long)a.n[1] * a.n[2];
     const unsigned pblocks = (unsigned)((plane + kReduceThreads - 1) / kReduceThreads);
@@ -246,11 +268,11 @@ __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned bl
     const int i0 = (int)(block / pblocks) * kObsSeg;
     const int i1 = min(i0 + kObsSeg, a.n[0]);
     enum { S_RHO, S_X2, S_RHO2, S_LX, S_LY, S_LZ, S_N };
-    Acc<R> sum[S_N];
-    Acc<R> acc[9];
+    Acc<T> sum[S_N];
+    Acc<T> acc[9];
     if (L < plane && i0 < i1) {
         const int j = (int)(L / a.n[2]), k = (int)(L % a.n[2]);
-        const R x0 = (R)a.origin[0], dx = (R)a.d[0];
+        const T x0 = (T)a.origin[0], dx = (T)a.d[0];
         const bool has_y = j + 1 < a.n[1], has_z = k + 1 < a.n[2];
         V prev = i0 > 0 ? psi[(i0 - 1) * plane + L] : E::from_real(0.0);
         // chunks of 8 sites: all of a chunk's loads are issued before its sums
@@ -266,16 +288,16 @@ __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned bl
                     if (has_z) qz[u] = psi[off + 1];
                 }
             }
-            R part[S_N];
+            T part[S_N];
 #pragma unroll
-            for (int q = 0; q < S_N; ++q) part[q] = R(0);
-            const R fc0 = (R)c0;
+            for (int q = 0; q < S_N; ++q) part[q] = T(0);
+            const T fc0 = (T)c0;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int i = c0 + u;
                 if (i < i1) {
-                    const R rho = E::abs2r(p[u]);
-                    const R x = fma(fc0 + (R)u, dx, x0);
+                    const T rho = E::abs2r(p[u]);
+                    const T x = fma(fc0 + (T)u, dx, x0);
                     part[S_RHO] += rho;
                     part[S_X2] = fma(x * x, rho, part[S_X2]);
                     part[S_RHO2] = fma(rho, rho, part[S_RHO2]);
@@ -288,10 +310,10 @@ __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned bl
 #pragma unroll
             for (int q = 0; q < S_N; ++q) sum[q].add(part[q]);
         }
-        const R sc = (R)__ldg(a.scale);
-        const R s2 = sc * sc;
-        const R y = (R)(a.origin[1] + j * a.d[1]);
-        const R z = (R)(a.origin[2] + k * a.d[2]);
+        const T sc = (T)__ldg(a.scale);
+        const T s2 = sc * sc;
+        const T y = (T)(a.origin[1] + j * a.d[1]);
+        const T z = (T)(a.origin[2] + k * a.d[2]);
         acc[O_RHO] = acc_scaled(sum[S_RHO], s2);
         acc[O_X2] = acc_scaled(sum[S_X2], s2);
         acc[O_RHO2] = acc_scaled(sum[S_RHO2], s2 * s2);
@@ -300,11 +322,11 @@ __device__ __forceinline__ void observables_body(const FieldArgs &a, unsigned bl
         acc[O_LZ] = acc_scaled(sum[S_LZ], s2);
         acc[O_Y2] = acc_scaled(acc[O_RHO], y * y);
         acc[O_Z2] = acc_scaled(acc[O_RHO], z * z);
-        const R vyz = (R)a.half_w2[1] * y * y + (R)a.half_w2[2] * z * z;
-        acc[O_V] = acc_sum(acc_scaled(acc[O_X2], (R)a.half_w2[0]), acc_scaled(acc[O_RHO], vyz));
+        const T vyz = (T)a.half_w2[1] * y * y + (T)a.half_w2[2] * z * z;
+        acc[O_V] = acc_sum(acc_scaled(acc[O_X2], (T)a.half_w2[0]), acc_scaled(acc[O_RHO], vyz));
     }
     double bs[9];
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(T) == 4) {
         float ps[9], pc[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -817,7 +839,7 @@ __global__ void apply_scale_kernel(FieldArgs a, void *dst) {
     using E = Elem<R, CPLX>;
     const typename E::V *src = static_cast<const typename E::V *>(a.psi);
     typename E::V *out = static_cast<typename E::V *>(dst);
-    const R s = (R)__ldg(a.scale);
+    const typename E::T s = (typename E::T)__ldg(a.scale);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.sites; i += grid_stride())
         out[i] = E::scaled(src[i], s);
 }
@@ -859,6 +881,7 @@ cudaError_t dispatch_all(Prec p, bool cplx, int what, const FieldArgs &a, int bl
                          cudaStream_t s) {
     if (p == P_F64) return cplx ? dispatch<double, true>(what, a, blocks, dst, s)
                                 : dispatch<double, false>(what, a, blocks, dst, s);
+    if (p == P_F16) return cplx ? cudaErrorInvalidValue : dispatch<__half, false>(what, a, blocks, dst, s);
     return cplx ? dispatch<float, true>(what, a, blocks, dst, s)
                 : dispatch<float, false>(what, a, blocks, dst, s);
 }
@@ -876,6 +899,7 @@ void prepare_field_launches() {
 }
 
 cudaError_t launch_kick(Prec p, const FieldArgs &a, double kdt, void *dst, cudaStream_t s) {
+    if (p == P_F16) return cudaErrorInvalidValue;  // real time: complex fields only
     return p == P_F64 ? launch_kick_r<double>(a, kdt, dst, s) : launch_kick_r<float>(a, kdt, dst, s);
 }
 

@@ -29,7 +29,7 @@ static cudaError_t launch_tma_w(const SweepArgs &a, const TmaMaps &m, cudaStream
     if constexpr (tma_supported<F, W>()) {
         const long long rows = (long long)kTmaWarps * kTmaRows;
         const unsigned grid = (unsigned)((a.n_lines + rows - 1) / rows);
-        constexpr size_t smem = tma_smem_bytes<typename F::V, W>();
+        constexpr size_t smem = tma_smem_bytes<store_t<F>, W>();
         static bool attr = false;  // opt in once to more than 48 KB of dynamic shared memory
         if (!attr) {
             cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<F, R, W>,
@@ -44,10 +44,16 @@ static cudaError_t launch_tma_w(const SweepArgs &a, const TmaMaps &m, cudaStream
     }
 }
 
+// Forms whose memory element differs from their arithmetic type (FP16
+// storage) have only the TMA z sweep and the windowed strided sweeps with two
+// or four lines per thread.
+template <class F> constexpr bool narrow_store() { return !std::is_same<store_t<F>, typename F::V>::value; }
+
 template <class F, typename R, int W>
 static cudaError_t launch_contig_or_tma(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     if (L.tma && tma_usable<F, W>(a)) return launch_tma_w<F, R, W>(a, *L.tma, s);
-    return launch_contig_w<F, R, W>(a, s);
+    if constexpr (narrow_store<F>()) return cudaErrorInvalidValue;
+    else return launch_contig_w<F, R, W>(a, s);
 }
 
 template <class F, typename R>
@@ -79,7 +85,7 @@ static cudaError_t launch_lines_tma_wl(const SweepArgs &a, const TmaMaps &m, cud
 }
 
 template <class F, typename R, int W, int KIND, int LPT>
-static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+static cudaError_t launch_lines_wl_any(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
     using V = typename LinesPerThread<F, LPT>::M::MemV;
     if constexpr (W > 0 && KIND != K_Z) {
         if (L.lmaps) return launch_lines_tma_wl<F, R, W, KIND, LPT>(a, *L.lmaps, s);
@@ -97,6 +103,16 @@ static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cud
     }
     sweep_lines_kernel<F, R, W, KIND, LPT><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <class F, typename R, int W, int KIND, int LPT>
+static cudaError_t launch_lines_wl(const SweepLaunch &L, const SweepArgs &a, cudaStream_t s) {
+    using V = typename LinesPerThread<F, LPT>::M::MemV;
+    if constexpr (narrow_store<F>() && (W == 0 || sizeof(V) < 4 || KIND == K_Z)) {
+        return cudaErrorInvalidValue;
+    } else {
+        return launch_lines_wl_any<F, R, W, KIND, LPT>(L, a, s);
+    }
 }
 
 template <class F, typename R, int W, int KIND>

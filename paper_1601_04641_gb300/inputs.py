@@ -83,6 +83,17 @@ def imag_large_half() -> Problem:
                    name="imag 480x400x160, g 20, dt 0.1 d^2 (half-depth profiling case)", meta={})
 
 
+def imag_xl() -> Problem:
+    """The imaginary-time workload on a larger grid, 640x480x400 at d = 0.05
+    (trap (0.5, 1, 1.5), g = 20), at dt = d^2: the step of a schedule's
+    coarse level (ten times the fine dt), where the FP16 storage variant
+    runs.  At 640x480x400 an FP16 field (246 MB) exceeds the 129 MB L2; at
+    480x400x320 it would fit."""
+    p = imag_large()
+    return Problem((640, 480, 400), p.d, p.d[0] ** 2, p.omega, p.g,
+                   name="imag 640x480x400, g 20, dt d^2 (coarse level)", meta={})
+
+
 def sized_box(shape, omega, g, dt_factor=0.1) -> Problem:
     """Grid spacing that holds both the g = 0 Gaussian (6 oscillator lengths)
     and 1.3x the Thomas-Fermi radius in the half-box, per axis."""

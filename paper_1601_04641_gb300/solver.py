@@ -13,9 +13,10 @@ import numpy as np
 from . import _native as N
 
 _TORCH_DTYPES = {("f64", "complex"): "complex128", ("f32", "complex"): "complex64",
-                 ("f64", "real"): "float64", ("f32", "real"): "float32"}
+                 ("f64", "real"): "float64", ("f32", "real"): "float32", ("f16", "real"): "float16"}
 _NP_DTYPES = {("f64", "complex"): np.complex128, ("f32", "complex"): np.complex64,
-              ("f64", "real"): np.float64, ("f32", "real"): np.float32}
+              ("f64", "real"): np.float64, ("f32", "real"): np.float32, ("f16", "real"): np.float16}
+_PRECISIONS = {"f64": N.GP_F64, "f32": N.GP_F32, "f16": N.GP_F16}
 
 
 class GP:
@@ -23,7 +24,8 @@ class GP:
     anisotropic harmonic trap (imaginary or real time).
 
     shape: (nx, ny, nz); d: (dx, dy, dz); omega: (gamma, nu, lambda).
-    precision: "f64" or "f32" (element precision of psi; reductions are FP64);
+    precision: "f64", "f32" or "f16" (element precision of psi; reductions are
+    FP64; "f16" stores psi in half precision with FP32 arithmetic, real fields);
     field: "complex" or "real" (real allows imaginary time only).
     """
 
@@ -37,7 +39,7 @@ class GP:
         self.precision, self.field = precision, field
         key = (precision, field)
         if key not in _TORCH_DTYPES:
-            raise ValueError("precision must be f64/f32 and field complex/real")
+            raise ValueError("precision must be f64/f32 (or f16 with a real field) and field complex/real")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.np_dtype = _NP_DTYPES[key]
         with torch.cuda.device(self.device):
@@ -48,7 +50,7 @@ class GP:
             h = N.Handle()
             st = self.lib.gp_create_ext(ctypes.byref(h), grid, float(dt), float(omega[0]),
                                         float(omega[1]), float(omega[2]), float(g),
-                                        N.GP_F64 if precision == "f64" else N.GP_F32,
+                                        _PRECISIONS[precision],
                                         N.GP_COMPLEX if field == "complex" else N.GP_REAL,
                                         ctypes.c_void_p(self.stream.cuda_stream),
                                         ctypes.c_void_p(self.psi.data_ptr()),
@@ -267,7 +269,7 @@ class Batch:
                                           arr(p.omega[1] for p in self.problems),
                                           arr(p.omega[2] for p in self.problems),
                                           arr(p.g for p in self.problems),
-                                          N.GP_F64 if precision == "f64" else N.GP_F32,
+                                          _PRECISIONS[precision],
                                           N.GP_COMPLEX if field == "complex" else N.GP_REAL,
                                           ctypes.c_void_p(self.stream.cuda_stream))
             N.check(st, None, batch=True)

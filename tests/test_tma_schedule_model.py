@@ -188,11 +188,11 @@ def test_kernel_ring_depth_is_modelled():
 
 
 @pytest.mark.parametrize("ahead", [1, 2, 3, 4])
-@pytest.mark.parametrize("B", [8, 16])
+@pytest.mark.parametrize("B", [8, 16, 32])  # 64-byte box rows of 8-, 4- and 2-byte elements
 @pytest.mark.parametrize("W", [4, 8, 16])
 def test_tma_schedule_model(B, W, ahead):
     rng = np.random.default_rng(B * 100 + W)
-    step = 2 if B == 8 else 4                # rows must start on 16-byte boundaries
+    step = {8: 2, 16: 4, 32: 8}[B]           # rows must start on 16-byte boundaries
     for N in range(B + W + 4 + (-(B + W + 4)) % step, B + W + 4 + 4 * B + 2, step):
         psi = rng.standard_normal(N) + 1j * rng.standard_normal(N)
         psi[0], psi[-1] = 7.0, -5.0          # must not enter the solution
