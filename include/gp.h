@@ -300,8 +300,8 @@ gp_status gp_get_tma(gp_handle h, int *in_use);
 
 /* The x and y sweeps (strided axes) reading through tensor-memory-
  * accelerator boxes: `axes` is a mask, bit 0 for x and bit 1 for y, in both
- * modes; -1 (the default) takes x in imaginary time and neither axis in real
- * time.  An axis outside the mask reads through per-thread asynchronous
+ * modes; -1 (the default) takes x for real fields (imaginary time) and
+ * neither axis for complex fields.  An axis outside the mask reads through per-thread asynchronous
  * copies.  A
  * warp streams 32 adjacent line groups (1, 2 or 4 lines each, as
  * gp_set_lines_per_thread gives) in boxes of one chunk of nodes x 32 groups,
@@ -311,10 +311,11 @@ gp_status gp_get_tma(gp_handle h, int *in_use);
  * a line's node stride is a multiple of 16 bytes (ny * nz * element size
  * for x, nz * element size for y); elsewhere the other form runs.  Both
  * forms do the same arithmetic in the same order, so their results are
- * identical.  Measured on 480x400x320: it shortens the imaginary-time x
- * sweeps (FP32 real field 0.101 -> 0.096 ms, complex64 0.166 -> 0.164 ms),
- * lengthens the y sweeps (FP32 real 0.082 -> 0.086 ms) and the complex64
- * real-time x sweep (0.170 -> 0.173 ms).  gp_get_tma_lines gives the axes
+ * identical.  Measured inside full steps: it shortens the x sweep of real
+ * fields (FP32 on 480x400x320 0.1076 -> 0.1067 ms, FP16 on 640x480x400
+ * 0.371 -> 0.348 ms), and lengthens the complex64 x sweeps (imaginary time
+ * 0.1740 -> 0.1746, real time 0.170 -> 0.173 ms) and the y sweeps (FP32
+ * real 0.082 -> 0.086 ms in isolation).  gp_get_tma_lines gives the axes
  * that take it in either mode under the current settings (bit 0: x, bit 1:
  * y); GP_ERR_ARG for a mask outside -1..3. */
 gp_status gp_set_tma_lines(gp_handle h, int axes);

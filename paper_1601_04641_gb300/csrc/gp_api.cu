@@ -456,9 +456,14 @@ gp_status absent_stage(gp_handle h, int stage, bool realtime) {
 }
 
 // Axes whose sweeps read through TMA boxes in a mode (0 imaginary, 1 real
-// time): the mask set, or by default x in imaginary time only (the real-time
-// x sweep, bound by its kick arithmetic, measured 2 % slower that way).
-int tma_line_axes(gp_handle h, int mode) { return h->tma_lines >= 0 ? h->tma_lines : (mode == 0 ? 1 : 0); }
+// time): the mask set, or by default x for real fields (imaginary time).
+// Measured inside full steps on 480x400x320: FP32 real x 0.1067 against
+// 0.1076 ms, FP16 (640x480x400) 0.348 against 0.371; complex64 imaginary
+// x 0.1746 against 0.1740 and real-time x 0.173 against 0.170 (slower).
+int tma_line_axes(gp_handle h, int mode) {
+    if (h->tma_lines >= 0) return h->tma_lines;
+    return (mode == 0 && h->field == GP_REAL) ? 1 : 0;
+}
 
 // One stage of a step: 0 = kick + x sweep, 1 = y sweep, 2 = z sweep + norm.
 gp_status run_stage(gp_handle h, int stage, bool realtime) {

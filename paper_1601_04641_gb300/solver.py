@@ -208,7 +208,7 @@ class GP:
 
     def set_tma_lines(self, axes):
         """Axes (bit 0: x, bit 1: y) whose sweeps read through TMA boxes where the grid allows it;
-        -1 (default): x in imaginary time only."""
+        -1 (default): x for real fields (imaginary time), none for complex fields."""
         self._ck(self.lib.gp_set_tma_lines(self.h, int(axes)))
 
     def tma_lines_in_use(self):

@@ -125,15 +125,15 @@ def test_tma_lines_match_oracle(case):
 
 @pytest.mark.parametrize("field", ["real", "complex"])
 def test_tma_lines_axis_mask(field):
-    """The default reads x through TMA boxes in imaginary time only (a real
-    field has no real-time mode); a mask selects the axes in both modes;
-    masks outside -1..3 are refused."""
+    """The default reads x through TMA boxes for real fields only; a mask
+    selects the axes in both modes; masks outside -1..3 are refused."""
     from paper_1601_04641_gb300 import _native as N
     gp = make((20, 18, 64), 0.004, 12.0, "f32", field)
-    assert gp.tma_lines_in_use() == 1
+    default = 1 if field == "real" else 0
+    assert gp.tma_lines_in_use() == default
     for m in (0, 1, 2, 3, -1):
         gp.set_tma_lines(m)
-        assert gp.tma_lines_in_use() == (1 if m == -1 else m)
+        assert gp.tma_lines_in_use() == (default if m == -1 else m)
     for bad in (-2, 4):
         with pytest.raises(N.GPError) as e:
             gp.set_tma_lines(bad)
