@@ -14,6 +14,13 @@ Every function here is pinned by ``tests/test_oracle_pins.py`` against things
 other than itself: dense LU solves, the separable g = 0 fixed point, the
 continuum and Thomas-Fermi limits, the virial relation, unitarity in real
 time, and the O(dt) energy drift of first-order splitting.
+
+The ``axial_*`` functions are the axially symmetric (rho, z) variant
+(reading R21 in gp_oracle.c): arrays of shape ``(nx, nz)``, radial node i at
+rho = (i - 1/2) drho with node 0 a ghost and node nx-1 the boundary.  They are
+pinned by ``tests/test_oracle_axial.py``: the g = 0 continuum limit at second
+order, conservation of the cylindrical norm in real time, the virial
+relation, and the 3D Cartesian oracle's mu for gamma = nu.
 """
 from __future__ import annotations
 
@@ -60,6 +67,21 @@ def build_openmp(force: bool = False) -> str:
     return _compile(_OMP_PATH, ["-fopenmp"], force)
 
 
+_AXIAL = ("oracle_axial_gaussian", "oracle_axial_kick", "oracle_axial_sweep", "oracle_axial_step",
+          "oracle_axial_observables")
+
+
+def _set_axial_types(lib):
+    _i, _d = ctypes.c_int, ctypes.c_double
+    lib.oracle_axial_gaussian.argtypes = [_i, _i, _d, _d, _d, _d, _dp]
+    lib.oracle_axial_kick.argtypes = [_i, _i, _d, _d, _dp, _d, _d, _d, _d, _i]
+    lib.oracle_axial_sweep.argtypes = [_i, _i, _d, _d, _dp, _i, _d, _i]
+    lib.oracle_axial_step.argtypes = [_i, _i, _d, _d, _dp, _d, _d, _d, _d, _i, _i]
+    lib.oracle_axial_observables.argtypes = [_i, _i, _d, _d, _dp, _d, _d, _d, _dp]
+    for name in _AXIAL:
+        getattr(lib, name).restype = ctypes.c_int
+
+
 def _load():
     global _lib
     with _lock:
@@ -77,6 +99,7 @@ def _load():
             lib.oracle_observables.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_double, _dp]
             lib.oracle_step_strang.argtypes = [_ip, _dp, _dp, ctypes.c_double, _dp, ctypes.c_double,
                                                ctypes.c_int]
+            _set_axial_types(lib)
             for f in (lib.oracle_thomas, lib.oracle_gaussian, lib.oracle_kick,
                       lib.oracle_sweep, lib.oracle_renormalize, lib.oracle_step,
                       lib.oracle_observables, lib.oracle_step_strang):
@@ -100,7 +123,7 @@ class use_library:
             self.saved = _lib
             lib = ctypes.CDLL(self.path)
             for name in ("oracle_thomas", "oracle_gaussian", "oracle_kick", "oracle_sweep",
-                         "oracle_renormalize", "oracle_step", "oracle_observables", "oracle_step_strang"):
+                         "oracle_renormalize", "oracle_step", "oracle_observables", "oracle_step_strang") + _AXIAL:
                 getattr(lib, name).argtypes = getattr(self.saved, name).argtypes
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -266,3 +289,67 @@ def density_profiles(psi, d):
     rho = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
     return (rho.sum(axis=(1, 2)) * d[1] * d[2], rho.sum(axis=(0, 2)) * d[0] * d[2],
             rho.sum(axis=(0, 1)) * d[0] * d[1])
+
+
+# -------------------------------------------------------- axially symmetric (R21)
+def _axial_field(psi: np.ndarray) -> np.ndarray:
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous or psi.ndim != 2:
+        raise TypeError("axial fields are C-contiguous complex128 arrays of shape (nx, nz)")
+    return psi
+
+
+def axial_gaussian(nx, nz, drho, dz, gamma, lam) -> np.ndarray:
+    """The normalised g = 0 continuum ground state on the (rho, z) grid (R21)."""
+    psi = np.zeros((int(nx), int(nz)), dtype=np.complex128)
+    _check(_load().oracle_axial_gaussian(int(nx), int(nz), float(drho), float(dz), float(gamma), float(lam),
+                                         psi.ctypes.data_as(_dp)), "axial_gaussian")
+    return psi
+
+
+def axial_kick(psi, drho, dz, dt, gamma, lam, g, realtime) -> np.ndarray:
+    psi = _axial_field(psi)
+    _check(_load().oracle_axial_kick(psi.shape[0], psi.shape[1], float(drho), float(dz), psi.ctypes.data_as(_dp),
+                                     float(dt), float(gamma), float(lam), float(g), int(bool(realtime))),
+           "axial_kick")
+    return psi
+
+
+def axial_sweep(psi, drho, dz, axis, dt, realtime) -> np.ndarray:
+    """CN line solves along rho (axis 0) or z (axis 1), in place."""
+    psi = _axial_field(psi)
+    _check(_load().oracle_axial_sweep(psi.shape[0], psi.shape[1], float(drho), float(dz), psi.ctypes.data_as(_dp),
+                                      int(axis), float(dt), int(bool(realtime))), "axial_sweep")
+    return psi
+
+
+def axial_step(psi, drho, dz, dt, gamma, lam, g, realtime, nsteps=1) -> np.ndarray:
+    """In-place split-step CN steps of the axially symmetric equation (R21)."""
+    psi = _axial_field(psi)
+    _check(_load().oracle_axial_step(psi.shape[0], psi.shape[1], float(drho), float(dz), psi.ctypes.data_as(_dp),
+                                     float(dt), float(gamma), float(lam), float(g), int(bool(realtime)),
+                                     int(nsteps)), "axial_step")
+    return psi
+
+
+def axial_observables(psi, drho, dz, gamma, lam, g) -> dict:
+    psi = _axial_field(psi)
+    out = np.zeros(6, dtype=np.float64)
+    _check(_load().oracle_axial_observables(psi.shape[0], psi.shape[1], float(drho), float(dz),
+                                            psi.ctypes.data_as(_dp), float(gamma), float(lam), float(g),
+                                            out.ctypes.data_as(_dp)), "axial_observables")
+    return dict(zip(OBS_KEYS, (float(v) for v in out)))
+
+
+def axial_run_imag_until(psi, drho, dz, dt, gamma, lam, g, mu_tol, check_every=10, max_steps=200000):
+    """Imaginary time with the stop rule |mu(n) - mu(n-K)| < tol (R6).
+    Returns (steps taken, last mu)."""
+    mu_prev = axial_observables(psi, drho, dz, gamma, lam, g)["mu"]
+    steps = 0
+    while steps < max_steps:
+        axial_step(psi, drho, dz, dt, gamma, lam, g, False, check_every)
+        steps += check_every
+        mu = axial_observables(psi, drho, dz, gamma, lam, g)["mu"]
+        if abs(mu - mu_prev) < mu_tol:
+            return steps, mu
+        mu_prev = mu
+    return steps, mu_prev

@@ -453,3 +453,206 @@ int oracle_observables(const int n[3], const double d[3], const double *psi_ri,
     out[5] = sqrt(dv * s_z2 / norm);
     return ORACLE_OK;
 }
+
+/* ====================================================================
+ * Axially symmetric condensates (reading R21), the (rho, z) program variant
+ * of the predecessor package.  With gamma = nu the trap is symmetric about
+ * the z axis and the ground state (no circulation) depends on (rho, z) only:
+ *     i dpsi/dt = [-(1/2)((1/rho) d/drho (rho d/drho) + d^2/dz^2) + V + g|psi|^2] psi,
+ *     V = (gamma^2 rho^2 + lambda^2 z^2) / 2,   int 2 pi rho |psi|^2 drho dz = 1.
+ * Grid: psi[i][k] (k stride 1), nx nodes along rho and nz along z.  Radial
+ * node i = 1..nx-2 sits at rho_i = (i - 1/2) drho (cell centres, so no node
+ * lies on the axis); node 0 is a ghost that nothing couples to and node
+ * nx-1, at rho = (nx - 3/2) drho, is the Dirichlet boundary (psi = 0).  The
+ * z nodes are those of R2/R3.  The radial operator is the finite-volume
+ * (1/rho) d/drho (rho d/drho):
+ *     L psi_i = [rho_{i+1/2} (psi_{i+1} - psi_i) - rho_{i-1/2} (psi_i - psi_{i-1})] / (rho_i drho^2),
+ * rho_{i+-1/2} = rho_i +- drho/2, so rho_{1/2} = 0: the axis carries no flux
+ * (the symmetry condition).  It is symmetric in the cylindrical inner product
+ * sum 2 pi rho_i drho dz phi* psi, so the CN radial sweep conserves that
+ * norm in real time.  With wl_i = rho_{i-1/2}/rho_i, wr_i = rho_{i+1/2}/rho_i
+ * and c as in the header, the radial CN equation at node i is
+ *     -c wl_i phi[i-1] + (1 + c (wl_i + wr_i)) phi[i] - c wr_i phi[i+1]
+ *         = c wl_i psi[i-1] + (1 - c (wl_i + wr_i)) psi[i] + c wr_i psi[i+1].
+ * A step is kick, radial sweep, z sweep, then (imaginary time) the
+ * renormalisation in the cylindrical measure (R5).  Observables: the
+ * measure w_i = 2 pi rho_i drho dz; radial links at rho_{i+1/2} weighted
+ * 2 pi rho_{i+1/2} dz / drho, z links weighted 2 pi rho_i drho / dz (the
+ * discrete Rayleigh quotient of this operator, R4); rms_x = rms_y =
+ * sqrt(<rho^2> / 2).
+ * ==================================================================== */
+
+static int axial_grid_ok(int nx, int nz, double drho, double dz)
+{
+    return nx >= 3 && nz >= 3 && isfinite(drho) && drho > 0.0 && isfinite(dz) && dz > 0.0;
+}
+
+static double axial_rho(int i, double drho) { return (i - 0.5) * drho; }
+
+/* Cylindrical weight 2 pi rho_i drho dz of interior radial node i. */
+static double axial_w(int i, double drho, double dz) { return 2.0 * M_PI * axial_rho(i, drho) * drho * dz; }
+
+static int axial_interior(int nx, int nz, int i, int k) { return i >= 1 && i <= nx - 2 && k >= 1 && k <= nz - 2; }
+
+static double axial_norm(int nx, int nz, double drho, double dz, const cplx *psi)
+{
+    double sum = 0.0;
+    for (int i = 1; i <= nx - 2; i++)
+        for (int k = 0; k < nz; k++) {
+            cplx p = psi[(size_t)i * nz + k];
+            sum += axial_w(i, drho, dz) * creal(p * conj(p));
+        }
+    return sum;
+}
+
+/* The continuum g = 0 ground state (gamma/pi)^(1/2) (lambda/pi)^(1/4)
+ * exp(-(gamma rho^2 + lambda z^2)/2) at the interior nodes, zero elsewhere,
+ * normalised in the cylindrical measure. */
+int oracle_axial_gaussian(int nx, int nz, double drho, double dz, double gamma, double lambda, double *psi_ri)
+{
+    if (!psi_ri || !axial_grid_ok(nx, nz, drho, dz) || !(gamma > 0.0) || !(lambda > 0.0))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    for (int i = 0; i < nx; i++)
+        for (int k = 0; k < nz; k++) {
+            double v = 0.0;
+            if (axial_interior(nx, nz, i, k)) {
+                double r = axial_rho(i, drho), z = node_coord(k, nz, dz);
+                v = sqrt(gamma / M_PI) * pow(lambda / M_PI, 0.25) * exp(-0.5 * (gamma * r * r + lambda * z * z));
+            }
+            psi[(size_t)i * nz + k] = v;
+        }
+    double scale = 1.0 / sqrt(axial_norm(nx, nz, drho, dz, psi));
+    for (size_t s = 0; s < (size_t)nx * nz; s++)
+        psi[s] *= scale;
+    return ORACLE_OK;
+}
+
+/* Kick at every interior node with rho = |psi|^2 before the step:
+ * exp(-dt (V + g rho)) (imaginary time) or exp(-i dt (V + g rho)). */
+int oracle_axial_kick(int nx, int nz, double drho, double dz, double *psi_ri, double dt, double gamma,
+                      double lambda, double g, int realtime)
+{
+    if (!psi_ri || !axial_grid_ok(nx, nz, drho, dz) || !isfinite(dt))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    for (int i = 1; i <= nx - 2; i++)
+        for (int k = 1; k <= nz - 2; k++) {
+            size_t s = (size_t)i * nz + k;
+            double r = axial_rho(i, drho), z = node_coord(k, nz, dz);
+            double v = 0.5 * (gamma * gamma * r * r + lambda * lambda * z * z);
+            double arg = dt * (v + g * creal(psi[s] * conj(psi[s])));
+            psi[s] = psi[s] * (realtime ? cexp(-I * arg) : exp(-arg));
+        }
+    return ORACLE_OK;
+}
+
+/* CN line solves along rho (axis 0: the radial equation above, for every z
+ * line k = 1..nz-2) or z (axis 1: the Cartesian equation of the header, for
+ * every radial node i = 1..nx-2).  Boundary and ghost nodes are written 0. */
+int oracle_axial_sweep(int nx, int nz, double drho, double dz, double *psi_ri, int axis, double dt, int realtime)
+{
+    if (!psi_ri || !axial_grid_ok(nx, nz, drho, dz) || (axis != 0 && axis != 1) || !isfinite(dt))
+        return ORACLE_EARG;
+    cplx *psi = (cplx *)psi_ri;
+    const double h = axis == 0 ? drho : dz;
+    const cplx c = realtime ? I * dt / (4.0 * h * h) : dt / (4.0 * h * h);
+    const int len = (axis == 0 ? nx : nz) - 2, lines = axis == 0 ? nz : nx;
+    cplx *sub = malloc((size_t)len * sizeof(cplx)), *diag = malloc((size_t)len * sizeof(cplx));
+    cplx *sup = malloc((size_t)len * sizeof(cplx)), *rhs = malloc((size_t)len * sizeof(cplx));
+    cplx *x = malloc((size_t)len * sizeof(cplx));
+    int rc = (sub && diag && sup && rhs && x) ? ORACLE_OK : ORACLE_ENOMEM;
+    for (int l = 1; l <= lines - 2 && rc == ORACLE_OK; l++) {
+        /* node m (1..len) of this line */
+        size_t base = axis == 0 ? (size_t)l : (size_t)l * nz;
+        size_t stride = axis == 0 ? (size_t)nz : 1;
+        for (int m = 1; m <= len; m++) {
+            double wl = 1.0, wr = 1.0;
+            if (axis == 0) {
+                double r = axial_rho(m, drho);
+                wl = (r - 0.5 * drho) / r;
+                wr = (r + 0.5 * drho) / r;
+            }
+            cplx pm = m > 1 ? psi[base + (size_t)(m - 1) * stride] : 0.0;  /* ghost / boundary node: 0 */
+            cplx p0 = psi[base + (size_t)m * stride];
+            cplx pp = m < len ? psi[base + (size_t)(m + 1) * stride] : 0.0;
+            sub[m - 1] = -c * wl;
+            diag[m - 1] = 1.0 + c * (wl + wr);
+            sup[m - 1] = -c * wr;
+            rhs[m - 1] = c * wl * pm + (1.0 - c * (wl + wr)) * p0 + c * wr * pp;
+        }
+        rc = thomas_solve(len, sub, diag, sup, rhs, x);
+        if (rc != ORACLE_OK)
+            break;
+        psi[base] = 0.0;
+        for (int m = 1; m <= len; m++)
+            psi[base + (size_t)m * stride] = x[m - 1];
+        psi[base + (size_t)(len + 1) * stride] = 0.0;
+    }
+    free(sub);
+    free(diag);
+    free(sup);
+    free(rhs);
+    free(x);
+    return rc;
+}
+
+int oracle_axial_step(int nx, int nz, double drho, double dz, double *psi_ri, double dt, double gamma,
+                      double lambda, double g, int realtime, int nsteps)
+{
+    if (nsteps < 0)
+        return ORACLE_EARG;
+    for (int s = 0; s < nsteps; s++) {
+        int rc = oracle_axial_kick(nx, nz, drho, dz, psi_ri, dt, gamma, lambda, g, realtime);
+        for (int axis = 0; axis < 2 && rc == ORACLE_OK; axis++)
+            rc = oracle_axial_sweep(nx, nz, drho, dz, psi_ri, axis, dt, realtime);
+        if (rc == ORACLE_OK && !realtime) {
+            cplx *psi = (cplx *)psi_ri;
+            double nrm = axial_norm(nx, nz, drho, dz, psi);
+            if (!(nrm > 0.0) || !isfinite(nrm))
+                return ORACLE_EARG;
+            for (size_t q = 0; q < (size_t)nx * nz; q++)
+                psi[q] /= sqrt(nrm);
+        }
+        if (rc != ORACLE_OK)
+            return rc;
+    }
+    return ORACLE_OK;
+}
+
+/* out = {norm, mu, energy, rms_x, rms_y, rms_z} (rms_x = rms_y). */
+int oracle_axial_observables(int nx, int nz, double drho, double dz, const double *psi_ri, double gamma,
+                             double lambda, double g, double out[6])
+{
+    if (!psi_ri || !out || !axial_grid_ok(nx, nz, drho, dz))
+        return ORACLE_EARG;
+    const cplx *psi = (const cplx *)psi_ri;
+    double enorm = 0.0, epot = 0.0, eint = 0.0, r2 = 0.0, z2 = 0.0, ekin = 0.0;
+    for (int i = 1; i <= nx - 2; i++)
+        for (int k = 0; k < nz; k++) {
+            cplx p = psi[(size_t)i * nz + k];
+            double rho = creal(p * conj(p));
+            double r = axial_rho(i, drho), z = node_coord(k, nz, dz), w = axial_w(i, drho, dz);
+            enorm += w * rho;
+            epot += w * 0.5 * (gamma * gamma * r * r + lambda * lambda * z * z) * rho;
+            eint += w * rho * rho;
+            r2 += w * r * r * rho;
+            z2 += w * z * z * rho;
+            /* radial link to node i+1 (the last one reaches the boundary node) */
+            cplx dr = psi[(size_t)(i + 1) * nz + k] - p;
+            ekin += 0.5 * 2.0 * M_PI * (r + 0.5 * drho) * dz / drho * creal(dr * conj(dr));
+            if (k + 1 < nz) {
+                cplx dzp = psi[(size_t)i * nz + k + 1] - p;
+                ekin += 0.5 * 2.0 * M_PI * r * drho / dz * creal(dzp * conj(dzp));
+            }
+        }
+    if (!(enorm > 0.0))
+        return ORACLE_EARG;
+    out[0] = enorm;
+    out[1] = (ekin + epot + g * eint) / enorm;
+    out[2] = (ekin + epot + 0.5 * g * eint) / enorm;
+    out[3] = sqrt(0.5 * r2 / enorm);
+    out[4] = out[3];
+    out[5] = sqrt(z2 / enorm);
+    return ORACLE_OK;
+}
