@@ -549,6 +549,40 @@ const char *gp_nn_last_error(gp_nn net);
  * NULL. */
 const char *gp_last_error(gp_handle h);
 
+/* ---- axially symmetric condensates ----
+ * psi(rho, z) for a trap with gamma = nu: the (rho, z) program variant of
+ * the predecessor package the paper's programs extend.  The equation is the
+ * 3D one (i dpsi/dt = [-(1/2) lap + V + g |psi|^2] psi, V = (gamma^2 rho^2 +
+ * lambda^2 z^2) / 2, int 2 pi rho |psi|^2 drho dz = 1) for states without
+ * circulation.  Grid psi[i][k] (k, along z, has stride 1; a C array of
+ * shape (nx, nz)): radial node i = 1..nx-2 at rho = (i - 1/2) drho, node 0 a
+ * ghost (read as 0, written 0), node nx-1 the Dirichlet boundary; z nodes
+ * z_k = (k - (nz-1)/2) dz with psi = 0 at k = 0 and nz-1.  The radial line
+ * solve is the CN step of the finite-volume operator (1/rho) d/drho (rho
+ * d/drho) with face radii rho_{i +- 1/2} (no flux through the axis); a step
+ * is kick, radial solves, z solves, and in imaginary time the
+ * renormalisation in the cylindrical measure 2 pi rho drho dz.  Observables
+ * are the discrete Rayleigh quotient of this operator; gp_obs.rms_x and
+ * rms_y are both sqrt(<rho^2> / 2).  FP64 or FP32 fields (arithmetic in
+ * the field's precision, sums in FP64), real (imaginary time only) or
+ * complex.  gp_axial_create: nx, nz >= 3; drho, dz, dt, gamma, lambda > 0;
+ * GP_ERR_ARG otherwise, GP_ERR_NOMEM if device memory runs out.  psi
+ * buffers of set/get hold nx * nz elements (host or device, as on_device
+ * says; the caller owns them).  gp_axial_run_imag_until: the stop rule
+ * |mu(n) - mu(n - check_every)| < mu_tol, at most max_steps steps. */
+typedef struct gp_axial_s *gp_axial;
+gp_status gp_axial_create(gp_axial *out, int nx, int nz, double drho, double dz, double dt, double gamma,
+                          double lambda, double g, gp_precision prec, gp_field field, void *cuda_stream);
+void gp_axial_destroy(gp_axial a);
+const char *gp_axial_last_error(gp_axial a);
+gp_status gp_axial_init_gaussian(gp_axial a);
+gp_status gp_axial_set_psi(gp_axial a, const void *psi, int on_device);
+gp_status gp_axial_get_psi(gp_axial a, void *psi, int on_device);
+gp_status gp_axial_step_imag(gp_axial a, int nsteps);
+gp_status gp_axial_step_real(gp_axial a, int nsteps);
+gp_status gp_axial_observables(gp_axial a, gp_obs *out);
+gp_status gp_axial_run_imag_until(gp_axial a, double mu_tol, int check_every, int max_steps, int *steps_taken);
+
 /* ---- failure-detection self-tests (no counterpart in the paper) ----
  * gp_selftest_bounded_wait launches one warp on the given stream that waits,
  * with the bounded mbarrier wait the TMA sweep uses, on an mbarrier whose

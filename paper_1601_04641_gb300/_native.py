@@ -87,6 +87,16 @@ SIGNATURES = {
                              ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d),
                              _i, _i, _vp]),
     "gp_batch_destroy": (None, [Handle]),
+    "gp_axial_create": (_i, [ctypes.POINTER(Handle), _i, _i, _d, _d, _d, _d, _d, _d, _i, _i, _vp]),
+    "gp_axial_destroy": (None, [Handle]),
+    "gp_axial_last_error": (ctypes.c_char_p, [Handle]),
+    "gp_axial_init_gaussian": (_i, [Handle]),
+    "gp_axial_set_psi": (_i, [Handle, _vp, _i]),
+    "gp_axial_get_psi": (_i, [Handle, _vp, _i]),
+    "gp_axial_step_imag": (_i, [Handle, _i]),
+    "gp_axial_step_real": (_i, [Handle, _i]),
+    "gp_axial_observables": (_i, [Handle, ctypes.POINTER(Obs)]),
+    "gp_axial_run_imag_until": (_i, [Handle, _d, _i, _i, ctypes.POINTER(_i)]),
     "gp_batch_init_gaussian": (_i, [Handle]),
     "gp_batch_set_psi": (_i, [Handle, _i, _vp, _i]),
     "gp_batch_get_psi": (_i, [Handle, _i, _vp, _i]),
@@ -150,10 +160,12 @@ def load():
     return _lib
 
 
-def check(status, handle=None, batch=False, nn=False):
+def check(status, handle=None, batch=False, nn=False, axial=False):
     if status != GP_OK:
         lib = load()
-        if nn:
+        if axial:
+            msg = lib.gp_axial_last_error(handle)
+        elif nn:
             msg = lib.gp_nn_last_error(handle)
         elif batch:
             msg = lib.gp_batch_last_error(handle)

@@ -407,3 +407,74 @@ def ground_state(shape, d, dt, omega, g, tol=1e-10, device=None, max_steps=20000
     return psi, {"fp32_schedule_steps": n32, "fp32_s": t1 - t0, "mu_fp32": mu32,
                  "fp64_steps": n64, "fp64_s": t2 - t1, "mu": mu_prev, "last_dmu": dmu, "tol": tol,
                  "converged": dmu < tol}
+
+
+class AxialGP:
+    """Axially symmetric condensate psi(rho, z) (trap gamma = nu, lambda):
+    a C array of shape (nx, nz); radial node i at rho = (i - 1/2) drho (node 0
+    a ghost, node nx-1 the boundary), z nodes centred.  See gp_axial_create."""
+
+    def __init__(self, nx, nz, drho, dz, dt, gamma, lam, g, precision="f64", field="complex", device=None):
+        import torch
+        self._torch = torch
+        self.lib = N.load()
+        self.shape = (int(nx), int(nz))
+        key = (precision, field)
+        if key not in _NP_DTYPES or precision == "f16":
+            raise ValueError("precision must be f64/f32 and field complex/real")
+        self.np_dtype = _NP_DTYPES[key]
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            h = N.Handle()
+            st = self.lib.gp_axial_create(ctypes.byref(h), int(nx), int(nz), float(drho), float(dz), float(dt),
+                                          float(gamma), float(lam), float(g), _PRECISIONS[precision],
+                                          N.GP_COMPLEX if field == "complex" else N.GP_REAL,
+                                          ctypes.c_void_p(self.stream.cuda_stream))
+            N.check(st, None, axial=True)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gp_axial_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        N.check(st, self.h, axial=True)
+
+    def init_gaussian(self):
+        self._ck(self.lib.gp_axial_init_gaussian(self.h))
+
+    def set_psi(self, arr):
+        a = np.ascontiguousarray(np.asarray(arr), dtype=self.np_dtype)
+        if a.shape != self.shape:
+            raise ValueError("psi must have shape %s" % (self.shape,))
+        self._ck(self.lib.gp_axial_set_psi(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def get_psi(self):
+        out = np.empty(self.shape, dtype=self.np_dtype)
+        self._ck(self.lib.gp_axial_get_psi(self.h, out.ctypes.data_as(ctypes.c_void_p), 0))
+        return out
+
+    def step_imag(self, n=1):
+        self._ck(self.lib.gp_axial_step_imag(self.h, int(n)))
+
+    def step_real(self, n=1):
+        self._ck(self.lib.gp_axial_step_real(self.h, int(n)))
+
+    def observables(self):
+        o = N.Obs()
+        self._ck(self.lib.gp_axial_observables(self.h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k in ("norm", "mu", "energy", "rms_x", "rms_y", "rms_z", "step", "t")}
+
+    def run_imag_until(self, mu_tol, check_every=10, max_steps=200000):
+        taken = ctypes.c_int(0)
+        self._ck(self.lib.gp_axial_run_imag_until(self.h, float(mu_tol), int(check_every), int(max_steps),
+                                                  ctypes.byref(taken)))
+        return taken.value
