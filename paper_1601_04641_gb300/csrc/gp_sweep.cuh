@@ -1115,11 +1115,22 @@ template <class F, class M, typename R, int B, int KIND> struct ColumnIO {
     Hooks<F, M, R, KIND> hk;
     __device__ __forceinline__ void issue() {
         const int pb = s0 + issued * B;
+        // the chunk's B ring rows are consecutive: (pb + e - s0) mod RL =
+        // ((issued B) mod RL) + e, since RL is a multiple of B
+        MV *slot = ring + ((issued * B) & (RL - 1)) * T;
+        if (pb >= 0 && pb + B <= n) {
+            // the whole chunk inside the line (every chunk but a line's
+            // first and last): no per-element range test or select
+            const MV *g = in + (long long)(pb + 1) * st;
 #pragma unroll
-        for (int e = 0; e < B; ++e) {
-            const int p = pb + e;
-            const bool ok = p >= 0 && p < n;
-            cp_async<sizeof(MV)>(ring + ((p - s0) & (RL - 1)) * T, ok ? in + (long long)(p + 1) * st : in, ok);
+            for (int e = 0; e < B; ++e) cp_async<sizeof(MV)>(slot + e * T, g + e * st, true);
+        } else {
+#pragma unroll
+            for (int e = 0; e < B; ++e) {
+                const int p = pb + e;
+                const bool ok = p >= 0 && p < n;
+                cp_async<sizeof(MV)>(slot + e * T, ok ? in + (long long)(p + 1) * st : in, ok);
+            }
         }
         cp_async_commit();
         ++issued;
