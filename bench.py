@@ -67,9 +67,9 @@ FP64_PEAK_GFLOPS = 1250.0
 NCU_TRAFFIC = {
     # ncu --set full of the 480x400x160 half-depth case (profiles/), scaled x2
     # by sites to a full 480x400x320 launch: (read + write) bytes per launch
-    ("real_large", "zsweep_norm"): (2 * (246.279936e6 + 200.308736e6), "28b8942c626c9eb2"),
-    ("real_large", "kick_xsweep"): (2 * (257.200128e6 + 193.952256e6), "28b8942c626c9eb2"),
-    ("real_large", "ysweep"): (2 * (250.594816e6 + 193.361920e6), "28b8942c626c9eb2"),
+    ("real_large", "zsweep_norm"): (2 * (246.269440e6 + 200.813568e6), "e8585e1feeacb572"),
+    ("real_large", "kick_xsweep"): (2 * (257.253120e6 + 193.859584e6), "e8585e1feeacb572"),
+    ("real_large", "ysweep"): (2 * (253.209088e6 + 193.392128e6), "e8585e1feeacb572"),
 }
 
 
