@@ -483,7 +483,11 @@ gp_status gp_axial_create(gp_axial *out, int nx, int nz, double drho, double dz,
     if (field != GP_COMPLEX && field != GP_REAL) return afail(nullptr, GP_ERR_ARG, "unknown field");
     gp_axial a = new (std::nothrow) gp_axial_s();
     if (!a) return afail(nullptr, GP_ERR_NOMEM, "host allocation failed");
-    cudaGetDevice(&a->device);
+    if (cudaGetDevice(&a->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete a;
+        return afail(nullptr, GP_ERR_CUDA, "no CUDA device");
+    }
     a->nx = nx;
     a->nz = nz;
     a->drho = drho;

@@ -94,3 +94,75 @@ def test_valid_create_without_gpu_reports_cuda_error(lib):
         lib.gp_destroy(h)
     else:
         assert st in (N.GP_ERR_CUDA, N.GP_ERR_NOMEM)
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.parametrize("nz, field", [(64, N.GP_COMPLEX), (60, N.GP_REAL), (48, N.GP_REAL)])
+def test_fp16_storage_refusals_on_the_host(lib, nz, field):
+    """FP16 storage holds real fields only, on z rows of whole 16-byte units
+    (nz a multiple of 8) long enough for a chunk and the widest window."""
+    st, h = _create(lib, nz=nz, prec=N.GP_F16, field=field)
+    assert st == N.GP_ERR_ARG
+    assert not h.value
+    assert lib.gp_last_error(None)
+
+
+def test_fp16_storage_valid_arguments_pass_the_host_checks(lib):
+    st, h = _create(lib, nz=64, prec=N.GP_F16, field=N.GP_REAL)
+    if _has_gpu():
+        assert st == N.GP_OK
+        lib.gp_destroy(h)
+    else:
+        assert st in (N.GP_ERR_CUDA, N.GP_ERR_NOMEM)
+
+
+def _axial_create(lib, **kw):
+    args = dict(nx=16, nz=24, drho=0.2, dz=0.2, dt=1e-3, gamma=1.0, lam=2.0, g=5.0,
+                prec=N.GP_F64, field=N.GP_COMPLEX)
+    args.update(kw)
+    h = N.Handle()
+    st = lib.gp_axial_create(ctypes.byref(h), args["nx"], args["nz"], args["drho"], args["dz"], args["dt"],
+                             args["gamma"], args["lam"], args["g"], args["prec"], args["field"], None)
+    return st, h
+
+
+@pytest.mark.parametrize("bad", [dict(nx=2), dict(nz=2), dict(drho=0.0), dict(dz=-0.1),
+                                 dict(dt=float("nan")), dict(gamma=0.0), dict(lam=float("inf")),
+                                 dict(g=float("nan")), dict(prec=N.GP_F16), dict(prec=5), dict(field=3)])
+def test_axial_bad_arguments_are_rejected_on_the_host(lib, bad):
+    st, h = _axial_create(lib, **bad)
+    assert st == N.GP_ERR_ARG
+    assert not h.value
+    assert lib.gp_axial_last_error(None)
+
+
+def test_axial_null_handle_and_out_pointers(lib):
+    grid_args = (16, 24, 0.2, 0.2, 1e-3, 1.0, 2.0, 5.0, N.GP_F64, N.GP_COMPLEX, None)
+    assert lib.gp_axial_create(None, *grid_args) == N.GP_ERR_ARG
+    for call in (lambda: lib.gp_axial_init_gaussian(None),
+                 lambda: lib.gp_axial_set_psi(None, None, 0),
+                 lambda: lib.gp_axial_get_psi(None, None, 0),
+                 lambda: lib.gp_axial_step_imag(None, 1),
+                 lambda: lib.gp_axial_step_real(None, 1),
+                 lambda: lib.gp_axial_observables(None, None),
+                 lambda: lib.gp_axial_run_imag_until(None, 1e-6, 10, 100, None)):
+        assert call() == N.GP_ERR_ARG
+    lib.gp_axial_destroy(None)
+    assert b"NULL" in lib.gp_axial_last_error(None)
+
+
+def test_axial_valid_create_without_gpu_reports_cuda_error(lib):
+    st, h = _axial_create(lib)
+    if _has_gpu():
+        assert st == N.GP_OK
+        lib.gp_axial_destroy(h)
+    else:
+        assert st == N.GP_ERR_CUDA
+        assert not h.value
