@@ -89,6 +89,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def guarded(fn):
+    """The result of one secondary section of the JSON line, or {"error":
+    message} if it raised: a failing section is reported in the line instead
+    of losing the headline figures measured before it."""
+    try:
+        return fn()
+    except Exception as e:  # reported in the line
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -880,58 +890,69 @@ def run_ours(args):
                   if track else None},
     }
     res["gp"].close()
+
+    def also_workload(name):
+        """One secondary workload: its step time and per-kernel HBM fractions."""
+        r2 = time_workload(torch, name, args.also_steps, 3, local)
+        el2 = timed_region(torch, r2, args.also_steps, None)
+        kb2 = kernel_breakdown(torch, r2, min(args.also_steps, 50))
+        p2 = r2["problem"]
+        elem2 = {"f16": 4, "f32": 8, "f64": 16}[r2["prec"]] // (2 if r2["field"] == "real" else 1)
+        bytes2 = 2 * elem2 * p2.sites  # algorithmic bytes per sweep launch
+        if r2["prec"] == "f64" and r2["field"] == "complex" and r2["realtime"]:
+            # FP64 is bound by the FP64 units, not by HBM: flops against the FP64 peak
+            flops = p2.sites * (FP64_FLOPS_STEP_REALTIME + FP64_FLOPS_OBSERVABLES / TRACK_EVERY)
+            gflops = flops * args.also_steps / el2 / 1e9
+            alu = {"bound": "alu", "flops_per_site_step": flops / p2.sites,
+                   "achieved_gflops": gflops, "peak_gflops": FP64_PEAK_GFLOPS,
+                   "peak_source": "recipe nominal FP64", "alu_frac": gflops / FP64_PEAK_GFLOPS}
+        else:
+            alu = None
+        out = {"workload": p2.name, "grid": list(p2.shape),
+               "psi": {(2, "real"): "float16", (4, "real"): "float32", (8, "real"): "float64",
+                       (8, "complex"): "complex64",
+                       (16, "complex"): "complex128"}[(elem2, r2["field"])],
+               "time": "real" if r2["realtime"] else "imaginary",
+               "value": p2.sites * args.also_steps / el2,
+               "ms_per_step": 1e3 * el2 / args.also_steps, "dtype": r2["prec"],
+               "kernel_ms": {k: 1e3 * v for k, v in kb2.items()},
+               "kernel_hbm_frac": {k: bytes2 / v / 1e9 / peak for k, v in kb2.items()},
+               "step_hbm_frac": 3 * bytes2 * args.also_steps / el2 / 1e9 / peak}
+        if alu:
+            out["fp64_roofline"] = alu
+        if r2["realtime"]:
+            _, info = ground_state_of(torch, p2, local)
+            out["start"] = {"mu": info["mu"], "last_dmu": info["last_dmu"]}
+        o2 = r2["gp"].observables()
+        out["mu"] = o2["mu"]
+        r2["gp"].close()
+        return out
+
     if args.also and world == 1:
-        also = {}
-        for name in args.also.split(","):
-            if name and name != args.workload:
-                r2 = time_workload(torch, name, args.also_steps, 3, local)
-                el2 = timed_region(torch, r2, args.also_steps, None)
-                kb2 = kernel_breakdown(torch, r2, min(args.also_steps, 50))
-                p2 = r2["problem"]
-                elem2 = {"f16": 4, "f32": 8, "f64": 16}[r2["prec"]] // (2 if r2["field"] == "real" else 1)
-                bytes2 = 2 * elem2 * p2.sites  # algorithmic bytes per sweep launch
-                if r2["prec"] == "f64" and r2["field"] == "complex" and r2["realtime"]:
-                    # FP64 is bound by the FP64 units, not by HBM: flops against the FP64 peak
-                    flops = p2.sites * (FP64_FLOPS_STEP_REALTIME + FP64_FLOPS_OBSERVABLES / TRACK_EVERY)
-                    gflops = flops * args.also_steps / el2 / 1e9
-                    alu = {"bound": "alu", "flops_per_site_step": flops / p2.sites,
-                           "achieved_gflops": gflops, "peak_gflops": FP64_PEAK_GFLOPS,
-                           "peak_source": "recipe nominal FP64", "alu_frac": gflops / FP64_PEAK_GFLOPS}
-                else:
-                    alu = None
-                also[name] = {"workload": p2.name, "grid": list(p2.shape),
-                              "psi": {(2, "real"): "float16", (4, "real"): "float32", (8, "real"): "float64",
-                                      (8, "complex"): "complex64",
-                                      (16, "complex"): "complex128"}[(elem2, r2["field"])],
-                              "time": "real" if r2["realtime"] else "imaginary",
-                              "value": p2.sites * args.also_steps / el2,
-                              "ms_per_step": 1e3 * el2 / args.also_steps, "dtype": r2["prec"],
-                              "kernel_ms": {k: 1e3 * v for k, v in kb2.items()},
-                              "kernel_hbm_frac": {k: bytes2 / v / 1e9 / peak for k, v in kb2.items()},
-                              "step_hbm_frac": 3 * bytes2 * args.also_steps / el2 / 1e9 / peak}
-                if alu:
-                    also[name]["fp64_roofline"] = alu
-                if r2["realtime"]:
-                    _, info = ground_state_of(torch, p2, local)
-                    also[name]["start"] = {"mu": info["mu"], "last_dmu": info["last_dmu"]}
-                o2 = r2["gp"].observables()
-                also[name]["mu"] = o2["mu"]
-                r2["gp"].close()
-        line["also"] = also
+        line["also"] = {name: guarded(lambda: also_workload(name))
+                        for name in args.also.split(",") if name and name != args.workload}
+    # single-rank sections are guarded; the sharded one is not (a rank that
+    # skipped its collectives would leave the others waiting)
     if args.precision and world == 1:
-        line["precision_vs_fp64"] = precision_vs_fp64(torch, local, 500)
+        line["precision_vs_fp64"] = guarded(lambda: precision_vs_fp64(torch, local, 500))
     if args.strang and world == 1:
-        line["symmetric_splitting"] = symmetric_splitting(torch, local, min(args.steps, 500), args.warmup)
+        line["symmetric_splitting"] = guarded(
+            lambda: symmetric_splitting(torch, local, min(args.steps, 500), args.warmup))
     mustar64 = bar64 = None
     if args.gs and world == 1:
-        line["time_to_ground_state"], mustar64, bar64 = time_to_ground_state(torch, local, args.gs, 1e-6, peak)
+        out = guarded(lambda: time_to_ground_state(torch, local, args.gs, 1e-6, peak))
+        if isinstance(out, tuple):
+            line["time_to_ground_state"], mustar64, bar64 = out
+        else:
+            line["time_to_ground_state"] = out
     elif args.gs:
         line["time_to_ground_state"] = time_to_ground_state_sharded(torch, local, args.gs, 1e-6, rank, world, dist)
     if args.ws_train and world == 1:
-        line["warm_start"] = warm_start(torch, local, args.ws_train, args.ws_held, args.ws_steps,
-                                        mustar64 if args.gs == 64 else None, bar64 if args.gs == 64 else None)
+        line["warm_start"] = guarded(
+            lambda: warm_start(torch, local, args.ws_train, args.ws_held, args.ws_steps,
+                               mustar64 if args.gs == 64 else None, bar64 if args.gs == 64 else None))
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(p, res["realtime"], args.cpu_budget)
+        line["cpu_baseline"] = guarded(lambda: cpu_baseline(p, res["realtime"], args.cpu_budget))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
