@@ -37,7 +37,8 @@ def fake_workload(torch, name, steps, warmup, dev):
     if name == "bad_workload":
         raise RuntimeError("planted failure in a secondary workload")
     p = types.SimpleNamespace(name=name, shape=(8, 8, 8), sites=512, dt=1e-3, g=1.0, omega=(1.0, 1.0, 1.0))
-    return {"problem": p, "gp": FakeGP(), "prec": "f32", "field": "complex", "realtime": True}
+    prec = "f64" if name == "f64_workload" else "f32"
+    return {"problem": p, "gp": FakeGP(), "prec": prec, "field": "complex", "realtime": True}
 
 
 class FakeClocks:
@@ -87,7 +88,7 @@ def test_failing_sections_do_not_lose_the_line(monkeypatch, capsys, tgs_fails):
     monkeypatch.setattr(bench, "cpu_baseline", lambda p, realtime, budget: {"value": 1.0, "cores": 1})
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     monkeypatch.delenv("RANK", raising=False)
-    args = types.SimpleNamespace(workload="real_large", steps=20, warmup=3, also="good_workload,bad_workload",
+    args = types.SimpleNamespace(workload="real_large", steps=20, warmup=3, also="good_workload,bad_workload,f64_workload",
                                  also_steps=10, precision=1, strang=1, gs=64, ws_train=5, ws_held=2,
                                  ws_steps=1, no_cpu=False, cpu_budget=1.0)
     assert bench.run_ours(args) == 0
@@ -106,4 +107,7 @@ def test_failing_sections_do_not_lose_the_line(monkeypatch, capsys, tgs_fails):
     assert line["also"]["bad_workload"] == {"error": "RuntimeError: planted failure in a secondary workload"}
     good = line["also"]["good_workload"]
     assert good["ms_per_step"] == pytest.approx(1.0) and good["mu"] == 3.0 and good["start"]["mu"] == 3.0
+    f64 = line["also"]["f64_workload"]
+    assert f64["psi"] == "complex128" and f64["fp64_roofline"]["bound"] == "alu"
+    assert "fp64_roofline" not in good
     assert line["cpu_baseline"] == {"value": 1.0, "cores": 1}
