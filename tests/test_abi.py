@@ -166,3 +166,41 @@ def test_axial_valid_create_without_gpu_reports_cuda_error(lib):
     else:
         assert st == N.GP_ERR_CUDA
         assert not h.value
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "gp.h"
+int main(void) {
+    gp_handle h = 0;
+    gp_grid grid = {48, 40, 32, 0.1, 0.1, 0.1};
+    gp_status st = gp_create(&h, grid, 1e-3, 0.5, 1.0, 1.5, 20.0, GP_F32, GP_COMPLEX, NULL);
+    gp_axial a = 0;
+    gp_status sa = gp_axial_create(&a, 16, 24, 0.2, 0.2, 1e-3, 1.0, 2.0, 5.0, GP_F64, GP_REAL, NULL);
+    gp_status bad = gp_create(&h, grid, -1.0, 0.5, 1.0, 1.5, 20.0, GP_F32, GP_COMPLEX, NULL);
+    if (st == GP_OK) gp_destroy(h);
+    if (sa == GP_OK) gp_axial_destroy(a);
+    printf("%d %d %d\n", (int)st, (int)sa, (int)bad);
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """A C99 client (pedantic, warnings as errors) includes gp.h, links
+    libgpcn.so and gets statuses back (no GPU here: GP_ERR_CUDA)."""
+    build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(N.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lgpcn",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=120).stdout.split()
+    st, sa, bad = (int(x) for x in out)
+    assert bad == N.GP_ERR_ARG
+    if _has_gpu():
+        assert st == N.GP_OK and sa == N.GP_OK
+    else:
+        assert st == N.GP_ERR_CUDA and sa == N.GP_ERR_CUDA
