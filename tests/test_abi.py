@@ -204,3 +204,29 @@ def test_header_is_plain_c_and_links(tmp_path):
         assert st == N.GP_OK and sa == N.GP_OK
     else:
         assert st == N.GP_ERR_CUDA and sa == N.GP_ERR_CUDA
+
+
+def test_last_error_without_handle_is_per_thread(lib):
+    """gp_last_error(NULL) reports the calling thread's last failure: two
+    threads failing with different messages at the same time each read back
+    their own (ctypes releases the interpreter lock during the calls)."""
+    import threading
+    cases = {"dt": dict(dt=-1.0), "spacing": dict(dx=0.0)}
+    wrong = []
+    barrier = threading.Barrier(len(cases))
+
+    def worker(key):
+        barrier.wait()
+        for _ in range(2000):
+            st, _ = _create(lib, **cases[key])
+            msg = lib.gp_last_error(None).decode()
+            if st != N.GP_ERR_ARG or key not in msg:
+                wrong.append((key, st, msg))
+                return
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in cases]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not wrong, wrong[:3]
