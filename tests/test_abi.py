@@ -230,3 +230,43 @@ def test_last_error_without_handle_is_per_thread(lib):
     for t in threads:
         t.join()
     assert not wrong, wrong[:3]
+
+
+def _batch_create(lib, n=3, bad=None, prec=N.GP_F32, field=N.GP_COMPLEX):
+    """gp_batch_create on n small instances; `bad` = (instance, key, value)
+    overrides one parameter of one instance."""
+    grids = (N.Grid * n)(*[N.Grid(12 + i, 10, 9, 0.2, 0.2, 0.25) for i in range(n)])
+    arr = {k: [v] * n for k, v in dict(dt=1e-3, gamma=1.0, nu=1.2, lam=1.5, g=5.0).items()}
+    if bad:
+        i, key, value = bad
+        if key in arr:
+            arr[key][i] = value
+        else:
+            setattr(grids[i], key, value)
+    c = {k: (ctypes.c_double * n)(*v) for k, v in arr.items()}
+    h = N.Handle()
+    st = lib.gp_batch_create(ctypes.byref(h), n, grids, c["dt"], c["gamma"], c["nu"], c["lam"], c["g"],
+                             prec, field, None)
+    return st, h
+
+
+@pytest.mark.parametrize("bad", [(0, "nx", 2), (2, "nz", 1), (1, "dy", 0.0), (2, "dz", float("nan")),
+                                 (1, "dt", -1e-3), (0, "g", float("inf")), (2, "gamma", -1.0),
+                                 (1, "lam", float("nan"))])
+def test_batch_bad_instance_is_rejected_on_the_host(lib, bad):
+    st, h = _batch_create(lib, bad=bad)
+    assert st == N.GP_ERR_ARG
+    assert not h.value
+    assert ("instance %d" % bad[0]).encode() in lib.gp_batch_last_error(None)
+
+
+def test_batch_refusals_and_valid_create_without_gpu(lib):
+    for kw in (dict(prec=N.GP_F16), dict(prec=9), dict(field=4), dict(n=0)):
+        st, h = _batch_create(lib, **kw)
+        assert st == N.GP_ERR_ARG and not h.value, kw
+    st, h = _batch_create(lib)
+    if _has_gpu():
+        assert st == N.GP_OK
+        lib.gp_batch_destroy(h)
+    else:
+        assert st == N.GP_ERR_CUDA and not h.value
