@@ -286,11 +286,12 @@ gp_status gp_get_lines_per_thread(gp_handle h, int mode, int lines[3]);
 /* The z sweep (stride-1 axis) through tensor-memory-accelerator tiles: one
  * bulk tensor copy per 64 lines x 64 bytes, two lines per thread (1, the
  * default), or through per-thread asynchronous copies (0).  The TMA form is
- * taken where the rows allow it: 4- or 8-byte elements, nz * element size a
- * multiple of 16 bytes, a window > 0 with (chunk + window) pair values in
- * at most 256 bytes (chunk = 64 bytes of nodes: every window for FP32 real
- * fields, windows 4 and 8 for 8-byte elements), whole lines, and nz - 2 at
- * least one chunk plus the window plus 2; elsewhere the other form runs.
+ * taken where the rows allow it: 2-, 4- or 8-byte elements, nz * element
+ * size a multiple of 16 bytes, a window > 0 with (chunk + window) pair
+ * values in at most 256 bytes (chunk = 64 bytes of nodes: every window for
+ * FP16 and FP32 real fields, windows 4 and 8 for 8-byte elements), whole
+ * lines, and nz - 2 at least one chunk plus the window plus 2; elsewhere
+ * the other form runs (GP_F16 handles take only the TMA form).
  * The arithmetic per line is the same in both.  gp_get_tma reports whether
  * the z sweep of imaginary time, or (complex fields) of real time, takes the
  * TMA form under the current settings: selected, tensor maps encoded for the
@@ -301,12 +302,11 @@ gp_status gp_get_tma(gp_handle h, int *in_use);
 /* The x and y sweeps (strided axes) reading through tensor-memory-
  * accelerator boxes: `axes` is a mask, bit 0 for x and bit 1 for y, in both
  * modes; -1 (the default) takes x for real fields (imaginary time) and
- * neither axis for complex fields.  An axis outside the mask reads through per-thread asynchronous
- * copies.  A
- * warp streams 32 adjacent line groups (1, 2 or 4 lines each, as
- * gp_set_lines_per_thread gives) in boxes of one chunk of nodes x 32 groups,
- * one bulk tensor copy each; the last warp of a plane (x) or of a row of
- * a plane (y) may be partial.  Results are stored by the threads in both
+ * neither axis for complex fields.  An axis outside the mask reads through
+ * per-thread asynchronous copies.  A warp streams 32 adjacent line groups
+ * (1, 2 or 4 lines each, as gp_set_lines_per_thread gives) in boxes of one
+ * chunk of nodes x 32 groups, one bulk tensor copy each; the last warp of a
+ * plane (x) or of a row of a plane (y) may be partial.  Results are stored by the threads in both
  * forms.  The TMA form is taken where a windowed solve runs (window > 0) and
  * a line's node stride is a multiple of 16 bytes (ny * nz * element size
  * for x, nz * element size for y); elsewhere the other form runs.  Both
@@ -428,13 +428,14 @@ gp_status gp_observables_noalloc(const void *dev_psi, gp_grid grid, gp_precision
 /* ------------------------------------------------------------------ batch
  * Many independent condensates -- each with its own grid, spacings, dt,
  * trap and g (the paper's programs run one condensate each) -- advanced in
- * imaginary time together: each step is one launch per sweep covering all
- * active instances (two on a strided axis at window 4 with complex64 fields:
- * instances whose lines pair up in memory advance line pairs; two on the z
- * axis when some instances' rows fit the TMA form of gp_set_tma and others
- * do not), with per-instance arguments, norm partials and counters; blocks of steps are
- * replayed from CUDA graphs, and
- * gp_batch_run_imag_until drops converged instances from the launches.  All
+ * imaginary time together: each step is one launch per sweep and stream
+ * group (gp_batch_set_streams) covering that group's active instances (two
+ * on a strided axis at window 4 with complex64 fields: instances whose
+ * lines pair up in memory advance line pairs; two on the z axis when some
+ * instances' rows fit the TMA form of gp_set_tma and others do not), with
+ * per-instance arguments, norm partials and counters; blocks of steps are
+ * replayed from CUDA graphs, and gp_batch_run_imag_until drops converged
+ * instances from the launches.  All
  * instances share one precision and field; each axis uses one window for the
  * whole batch (the largest of the instances' smallest admissible windows;
  * the exact solve in FP64).  psi of instance i has the layout above. */
@@ -565,8 +566,9 @@ const char *gp_last_error(gp_handle h);
  * are the discrete Rayleigh quotient of this operator; gp_obs.rms_x and
  * rms_y are both sqrt(<rho^2> / 2).  FP64 or FP32 fields (arithmetic in
  * the field's precision, sums in FP64), real (imaginary time only) or
- * complex.  gp_axial_create: nx, nz >= 3; drho, dz, dt, gamma, lambda > 0;
- * GP_ERR_ARG otherwise, GP_ERR_NOMEM if device memory runs out.  psi
+ * complex.  gp_axial_create: nx, nz >= 3; drho, dz, dt, gamma, lambda > 0,
+ * g finite, prec GP_F64 or GP_F32; GP_ERR_ARG otherwise, GP_ERR_CUDA
+ * without a CUDA device, GP_ERR_NOMEM if device memory runs out.  psi
  * buffers of set/get hold nx * nz elements (host or device, as on_device
  * says; the caller owns them).  gp_axial_run_imag_until: the stop rule
  * |mu(n) - mu(n - check_every)| < mu_tol, at most max_steps steps. */
